@@ -1,0 +1,349 @@
+"""Benchmark of the CheFSI hot path on one GB300 (or N independent replicas).
+
+One step = one CheFSI iteration over the whole subspace of the workload: the
+degree-m Chebyshev filter Y = p_m(H) X (FP32, column blocks), Cholesky-QR, Rayleigh-Ritz
+and the density of the occupied states, on a synthetic H-passivated Si nanocluster.
+The metric is Gpoint*vec/s = n_points * k * m / step time / 1e9 (one unit is one grid
+point x one vector x one degree step).
+
+Output: one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead
+(the only other place that runs oracle/ besides the cpu_baseline leg).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Chebyshev filter Gpoint*vec/s (CheFSI step: filter + Cholesky-QR + Rayleigh-Ritz + density)"
+UNIT = "Gpoint*vec/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="kscf", choices=["kscf", "reference"])
+    p.add_argument("--workload", default="si353h196")
+    p.add_argument("--block", type=int, default=0, help="filter column block (0 = workload default)")
+    p.add_argument("--brick", type=int, default=8)
+    p.add_argument("--mode", default="auto", choices=["auto", "native", "tensor"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU seconds of the oracle sample")
+    return p.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def setup_dist(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle (CPU) legs
+def oracle_step_sample(w, cpu_seconds: float):
+    """Time the FP64 CPU oracle on a bounded sample of the workload: one CheFSI step
+    (filter, Cholesky-QR, Rayleigh-Ritz, density) on the first k_s columns."""
+    from oracle.system import cluster_hamiltonian
+    from oracle import chefsi as orc
+    from workloads import pseudo_params, random_block_lex
+    pos, z = w.atoms()
+    OH = cluster_hamiltonian(pos, z, pseudo_params(), w.radius, w.h)
+    b = orc.spectral_upper_bound(OH)
+    # calibrate the column count on a 4-column filter
+    X = random_block_lex(1, OH.n, 4)
+    t0 = time.perf_counter()
+    orc.chebyshev_filter(OH, X, w.degree, -1.0, b, -30.0)
+    per_col = (time.perf_counter() - t0) / 4
+    ks = int(max(4, min(w.k, cpu_seconds / max(per_col, 1e-6))))
+    X0 = random_block_lex(1, OH.n, ks)
+    X, _ = orc.cholesky_qr(X0, OH.h3)
+    lam, X, _ = orc.rayleigh_ritz(OH, X, OH.h3)
+    t0 = time.perf_counter()
+    Y = orc.chebyshev_filter(OH, X, w.degree, lam[-1], b, lam[0])
+    X, _ = orc.cholesky_qr(Y, OH.h3)
+    lam, X, _ = orc.rayleigh_ritz(OH, X, OH.h3)
+    orc.density(X, np.full(min(ks, 4), 2.0))
+    dt = time.perf_counter() - t0
+    units = OH.n * ks * w.degree
+    return units / dt / 1e9, {"n_points": OH.n, "k_sample": ks, "seconds": dt}
+
+
+def cpu_threads() -> int:
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    world, rank, _ = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0
+    if rank != 0:
+        return
+    from workloads import workload
+    w = workload(args.workload)
+    vals = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        v, info = oracle_step_sample(w, args.cpu_seconds / 3)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    sample = (f"one CheFSI step of the FP64 CPU oracle on the first {info['k_sample']} of {w.k} columns "
+              f"({info['n_points']} points, degree {w.degree})")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": info["seconds"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_kscf(args):
+    import torch
+
+    from paper_2303_00790_gb300 import kscf
+    from workloads import n_occupied, pseudo_params, workload
+
+    world, rank, local = setup_dist(args)
+    assert torch.cuda.is_available(), "the kscf arm needs a CUDA device"
+    w = workload(args.workload)
+    block = args.block or min(w.block, 128)
+    mode = {"auto": kscf.KSCF_GEMM_NATIVE, "native": kscf.KSCF_GEMM_NATIVE, "tensor": kscf.KSCF_GEMM_TENSOR}[args.mode]
+    pos, z = w.atoms()
+    species = pseudo_params()
+    grid, H = kscf.build_cluster(pos, z, species, w.radius, w.h, brick=args.brick)
+    n_points, n_slots = grid.info["n_points"], grid.info["n_slots"]
+    k, m = w.k, w.degree
+    nocc = n_occupied(z)
+    dt = torch.float32
+    X = torch.empty((n_slots, k), dtype=dt, device="cuda")
+    kscf.kscf_random_subspace(H, X, seed=1 + rank)
+    rho = torch.empty(n_slots, dtype=torch.float64, device="cuda")
+    lo, b = kscf.kscf_spectral_bounds(H)
+    wf = torch.empty(kscf.kscf_workspace_size(H, kscf.KSCF_OP_FILTER, k, kscf.KSCF_F32, 0, block),
+                     dtype=torch.uint8, device="cuda")
+    wo = torch.empty(kscf.kscf_workspace_size(H, kscf.KSCF_OP_ORTHO, k, kscf.KSCF_F32, mode, 0),
+                     dtype=torch.uint8, device="cuda")
+    wr = torch.empty(kscf.kscf_workspace_size(H, kscf.KSCF_OP_RR, k, kscf.KSCF_F32, mode, 0),
+                     dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    kscf.kscf_orthonormalize(H, X, mode=mode, work=wo)
+    lam = kscf.kscf_rayleigh_ritz(H, X, mode=mode, work=wr)
+    state = {"lam": lam}
+    ev_f = []
+
+    def step(timed: bool):
+        lam = state["lam"]
+        if timed:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        kscf.kscf_chebyshev_filter(H, X, m, lam[-1], b, lam[0], block=block, work=wf)
+        if timed:
+            e1.record(stream)
+            ev_f.append((e0, e1))
+        kscf.kscf_orthonormalize(H, X, mode=mode, work=wo)
+        state["lam"] = kscf.kscf_rayleigh_ritz(H, X, mode=mode, work=wr)
+        kscf.kscf_density(H, X, nocc, rho=rho)
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = kscf.kscf_launch_counter()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    launches = kscf.kscf_launch_counter() - launches0
+    ms = t0.elapsed_time(t1) / args.steps
+    ms = max_over_ranks(ms, world)
+    filt_ms = statistics.mean([a.elapsed_time(c) for a, c in ev_f])
+    units = n_points * k * m
+    value = world * units / (ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel: the fused filter step (one launch = one degree
+    # step of one column block); algorithmic bytes = 12 B per point*vec (read Y_{j-1},
+    # read Y_{j-2}, write Y_j in FP32).  Its duration is the filter time over its
+    # m * ceil(k/block) degree-step launches (the small projector-gather launches
+    # inside are counted in the time).
+    n_launch_steps = m * ((k + block - 1) // block)
+    step_ms = filt_ms / n_launch_steps
+    alg_bytes = 12.0 * n_points * block
+    peak, peak_src = load_peaks()
+    achieved = alg_bytes / (step_ms * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get(f"{w.name}:{block}:{args.brick}")
+        except Exception:
+            traffic = None
+
+    # end-to-end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.empty((n_slots, k), dtype=dt, pin_memory=True)
+        Xh.copy_(X)
+        outh = torch.empty((n_slots, k), dtype=dt, pin_memory=True)
+        torch.cuda.synchronize()
+        barrier(world)
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        nE = max(1, min(args.steps, 3))
+        for _ in range(nE):
+            X.copy_(Xh, non_blocking=True)
+            step(False)
+            outh.copy_(X, non_blocking=True)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = max_over_ranks(s0.elapsed_time(s1) / nE, world)
+        e2e = {"value": world * units / (e_ms * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size()),
+               "d2h_bytes_per_step": int(outh.numel() * outh.element_size() + 8 * k)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, info = oracle_step_sample(w, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+               "sample": (f"one CheFSI step of the FP64 CPU oracle on the first {info['k_sample']} of {k} columns "
+                          f"({info['n_points']} points, degree {m}), {info['seconds']:.1f} s")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w.name, "n_points": n_points, "n_slots": n_slots, "k": k, "degree": m,
+                           "block": block, "brick": args.brick,
+                           "gemm": "tensor" if mode == kscf.KSCF_GEMM_TENSOR else "native",
+                           "parallelism": f"replicas{world}" if world > 1 else "single",
+                           "l2": f"inputs larger than L2 (X = {X.numel() * 4 / 2**20:.0f} MiB)"},
+                "filter": {"ms": filt_ms, "gpvs": units / (filt_ms * 1e-3) / 1e9},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
+                             "kernel": "cheb_step (fused stencil+V+KB+recurrence), per degree-step launch",
+                             "alg_bytes_per_launch": alg_bytes, "launch_ms": step_ms},
+                "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_kscf(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * kscf.h -- C ABI of the GB300 (sm_103a) CheFSI hot path for real-space Kohn-Sham DFT.
+ *
+ * Method: Chebyshev-filtered subspace iteration (CheFSI) on a high-order
+ * finite-difference Hamiltonian over a spherical Dirichlet grid whose points are
+ * stored in blockwise Hilbert space-filling-curve order (arXiv 2303.00790: Abstract;
+ * CheFSI paragraph before Table I; SFC paragraph after Table I; Computational details).
+ *
+ * Conventions for every entry point
+ *   - Return value: KSCF_OK (0) or a negative KSCF_ERR_* code; kscf_last_error()
+ *     returns a thread-local message describing the last failure on this thread.
+ *   - Units: Hartree atomic units (bohr, Hartree).
+ *   - Handles (kscf_grid, kscf_ham) are owned by the library; free them with the
+ *     matching *_free call.  A kscf_ham keeps a reference to device memory only, not to
+ *     the kscf_grid, so the grid may be freed after kscf_build_hamiltonian.
+ *   - Device arrays (X, rho, work, ...) are owned by the caller.  `stream` is a
+ *     cudaStream_t passed as void* (NULL = legacy default stream).  Calls are
+ *     asynchronous on `stream` unless stated otherwise.
+ *   - Wavefunction blocks X are "slot-major": row s (0 <= s < n_slots) holds the k
+ *     vector values of grid slot s contiguously, row stride `ld` elements (ld >= k).
+ *     Slots are brick_rank * b^3 + (lz*b + ly)*b + lx with bricks in Hilbert order.
+ *     Rows of slots outside the domain (padding of boundary bricks) are zero on
+ *     output; the library zeroes them on input where a stencil reads them.
+ *   - dtype: KSCF_F64 (double) or KSCF_F32 (float) for X and the filter arithmetic.
+ *   - Inner products use the grid weight h^3: <u, v> = h^3 sum_s u_s v_s.
+ *   - Device work buffers must be at least the size kscf_workspace_size() reports for
+ *     the same (op, k, dtype, mode, block); a smaller buffer gives KSCF_ERR_WORKSPACE
+ *     before any launch.  Work buffers must be 256-byte aligned.
+ */
+#ifndef KSCF_H
+#define KSCF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define KSCF_OK               0
+#define KSCF_ERR_INVALID     -1   /* bad argument (null pointer, size, bounds, dtype) */
+#define KSCF_ERR_CUDA        -2   /* a CUDA / cuSOLVER call failed */
+#define KSCF_ERR_WORKSPACE   -3   /* work buffer smaller than kscf_workspace_size */
+#define KSCF_ERR_NOT_SPD     -4   /* Gram matrix not positive definite (rank-deficient X) */
+#define KSCF_ERR_NONFINITE   -5   /* NaN/Inf found in an input or result */
+#define KSCF_ERR_NO_CONVERGE -6   /* dense eigensolver did not converge */
+#define KSCF_ERR_UNSUPPORTED -7   /* combination not built (e.g. bf16 mode with F64 X) */
+#define KSCF_ERR_HOST_ALLOC  -8   /* host memory allocation failed */
+
+/* ---- element types ---- */
+#define KSCF_F64 0
+#define KSCF_F32 1
+
+/* ---- Gram / projection GEMM modes (orthonormalize, rayleigh_ritz) ---- */
+#define KSCF_GEMM_NATIVE 0   /* CUDA-core GEMM in the dtype of X; FP32 X: FP32 products with FP64
+                                sums of partial sums over at most 256 rows */
+#define KSCF_GEMM_TENSOR 1   /* tensor cores (tcgen05), F32 X only: every FP32 operand is split into
+                                three bf16 pieces x = x1 + x2 + x3 and the six products x1y1, x1y2,
+                                x2y1, x1y3, x2y2, x3y1 are accumulated in FP32 over chunks of rows,
+                                chunk sums added in FP64 */
+
+/* ---- operations for kscf_workspace_size ---- */
+#define KSCF_OP_APPLY   0
+#define KSCF_OP_FILTER  1
+#define KSCF_OP_ORTHO   2
+#define KSCF_OP_RR      3
+
+typedef struct kscf_grid kscf_grid;
+typedef struct kscf_ham kscf_ham;
+
+/* An atom: position (bohr) and element number (14 = Si, 1 = H, ...). */
+typedef struct kscf_atom {
+  double x, y, z;
+  int32_t z_number;
+  int32_t reserved;
+} kscf_atom;
+
+/* Synthetic pseudopotential of one element (stand-in for the paper's norm-conserving
+ * Troullier-Martins potentials in Kleinman-Bylander form, Computational details):
+ *   local     v(r) = -z_valence erf(r/r_c)/r + a_gauss exp(-r^2/r_gauss^2)
+ *             (v(0) = -2 z_valence/(r_c sqrt(pi)) + a_gauss)
+ *   projectors (n_proj = 4): s = exp(-r^2/(2 r_p^2)), p_m = (x_m/r_p) exp(-r^2/(2 r_p^2)),
+ *             zero beyond r_cut; energies e_s (s) and e_p (p_x, p_y, p_z).
+ *   n_proj = 0 means no nonlocal part. */
+typedef struct kscf_species {
+  int32_t z_number;
+  int32_t n_proj;      /* 0 or 4 */
+  double z_valence, r_c, a_gauss, r_gauss;
+  double e_s, e_p, r_p, r_cut;
+} kscf_species;
+
+typedef struct kscf_grid_info {
+  int64_t n_points;    /* grid points inside the domain */
+  int64_t n_slots;     /* rows of X = n_bricks * brick^3 */
+  int64_t n_bricks;
+  int32_t brick;       /* brick edge b (8 or 16) */
+  int32_t lo[3];       /* smallest (i, j, k) over the domain */
+  int32_t extent[3];   /* bounding-box extent in points */
+  int32_t reserved;
+  double h;            /* grid spacing (bohr) */
+  double center[3];    /* grid point (0,0,0) position (bohr) */
+} kscf_grid_info;
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* kscf_last_error(void);
+
+/* Number of CUDA kernels this library has launched since it was loaded (all threads;
+ * kernels launched inside cuSOLVER are not counted).  For launch accounting. */
+uint64_t kscf_launch_counter(void);
+
+/* ---------------------------------------------------------------------------------
+ * Grid (host only).  Spherical domain: points center + h*(i,j,k) with
+ * i^2 + j^2 + k^2 <= radius^2/h^2 + 1e-9 (zero Dirichlet outside; the paper treats
+ * aperiodic clusters without a supercell, Intro).  Points are grouped into b^3
+ * bricks of the bounding box; bricks holding no point are dropped; the kept bricks
+ * are ordered along a 3D Hilbert curve of their brick coordinates (blockwise Hilbert
+ * SFC ordering, SFC paragraph after Table I), points inside a brick in x-fastest
+ * order.  brick must be 8 or 16.  *out receives a new handle. */
+int kscf_build_grid(const double center[3], double radius, double h, int brick, kscf_grid** out);
+
+/* Box domain 0 <= i < nx, 0 <= j < ny, 0 <= k < nz (closed-form tests).  Same layout. */
+int kscf_build_grid_box(int nx, int ny, int nz, double h, int brick, kscf_grid** out);
+
+int kscf_grid_get_info(const kscf_grid* grid, kscf_grid_info* info);
+
+/* Copies the slot tables to caller host arrays (either may be NULL):
+ *   lex_of_slot[n_slots]   lexicographic index (k slowest, i fastest) of the point in
+ *                          each slot, -1 for padding slots;
+ *   ijk_of_slot[3*n_slots] integer coordinates (i, j, k) of each slot (padding slots
+ *                          hold the coordinates they would have). */
+int kscf_grid_slots(const kscf_grid* grid, int64_t* lex_of_slot, int32_t* ijk_of_slot);
+
+int kscf_grid_free(kscf_grid* grid);
+
+/* ---------------------------------------------------------------------------------
+ * Hamiltonian H = -1/2 Lap_h + V_loc + V_NL at fixed potential (Intro: high-order
+ * finite differences in real space; Computational details: KB pseudopotentials).
+ * Lap_h: order-12 central differences, 6 neighbours per side along each axis.
+ * V_loc(p) = sum over all atoms of the species' local term (no truncation).
+ * V_NL y = sum_i chi_i E_i h^3 <chi_i, y> over the atoms' projectors.
+ * Builds the tables on the host, evaluates V_loc on the current CUDA device and
+ * uploads everything; synchronous.  atoms/species are read only during the call. */
+int kscf_build_hamiltonian(const kscf_grid* grid, const kscf_atom* atoms, int n_atoms,
+                           const kscf_species* species, int n_species, kscf_ham** out);
+
+int kscf_ham_free(kscf_ham* ham);
+
+/* Copies the grid info of the grid the Hamiltonian was built on. */
+int kscf_ham_grid_info(const kscf_ham* ham, kscf_grid_info* info);
+
+/* Replace V_loc by v_slots (device, n_slots doubles, slot order; padding entries are
+ * ignored).  Used for self-consistent updates and special potentials. */
+int kscf_set_potential(kscf_ham* ham, const double* v_slots, void* stream);
+
+/* Copy V_loc (device, n_slots doubles, zero in padding slots) to v_slots. */
+int kscf_get_potential(const kscf_ham* ham, double* v_slots, void* stream);
+
+/* Bounds of the spectrum (host doubles; synchronous):
+ *   upper = 3/(2h^2) (|w_0| + 2 sum_k |w_k|) + max V_loc
+ *           + max_i sum_j sqrt(E+_i E+_j) h^3 |<chi_i, chi_j>|   (Weyl + Gershgorin)
+ *   lower = min V_loc - max_i sum_j sqrt(E-_i E-_j) h^3 |<chi_i, chi_j>|
+ * with E+ = max(E, 0), E- = max(-E, 0).  upper is the filter's upper bound b. */
+int kscf_spectral_bounds(const kscf_ham* ham, double* lower, double* upper);
+
+/* Bytes of device work buffer needed by `op` for k vectors of `dtype` in GEMM `mode`,
+ * streaming `block` columns at a time (0 = all k). */
+int kscf_workspace_size(const kscf_ham* ham, int op, int k, int dtype, int mode, int block,
+                        size_t* bytes);
+
+/* HY = H Y for k vectors (Y and HY: n_slots x k, row strides ld_y, ld_hy; must not
+ * overlap).  Padding rows of Y are zeroed first. */
+int kscf_hamiltonian_apply(const kscf_ham* ham, void* Y, int64_t ld_y, void* HY, int64_t ld_hy,
+                           int k, int dtype, void* work, size_t work_bytes, void* stream);
+
+/* In place X <- p_m(H) X: the degree-m scaled Chebyshev filter (CheFSI paragraph;
+ * Zhou, Saad, Tiago & Chelikowsky 2006).  With e = (b-a)/2, c = (b+a)/2,
+ * sigma_1 = e/(a0-c), tau = 2/sigma_1:
+ *   Y_1 = (sigma_1/e)(H X - c X)
+ *   Y_j = (2 sigma_j/e)(H Y_{j-1} - c Y_{j-1}) - sigma_{j-1} sigma_j Y_{j-2},
+ *   sigma_j = 1/(tau - sigma_{j-1}),  j = 2..m;   X <- Y_m.
+ * Requires a0 < a < b, degree >= 1.  Columns are processed `block` at a time
+ * (0 = all k); the result does not depend on block. */
+int kscf_chebyshev_filter(const kscf_ham* ham, void* X, int64_t ld, int k, int degree,
+                          double a, double b, double a0, int dtype, int block,
+                          void* work, size_t work_bytes, void* stream);
+
+/* In place Cholesky-QR (orthonormalisation step of CheFSI):
+ *   S = h^3 X^T X (k x k, FP64 sums), S = R^T R (FP64 Cholesky), X <- X R^-1,
+ * so that h^3 X^T X = I.  For F32 X the step is repeated once (CholeskyQR2,
+ * Yamamoto et al. 2015), the second rotation applied as X + X (R2^-1 - I).  Returns KSCF_ERR_NOT_SPD if the Cholesky factorisation
+ * fails (X rank-deficient); X is then left unchanged.  Synchronises on `stream` to
+ * read the factorisation status. */
+int kscf_orthonormalize(const kscf_ham* ham, void* X, int64_t ld, int k, int dtype, int mode,
+                        void* work, size_t work_bytes, void* stream);
+
+/* In place Rayleigh-Ritz (CheFSI paragraph): HX = H X, Hs = h^3 X^T (HX) symmetrised
+ * (FP64 k x k), Hs = Q Lambda Q^T (FP64 symmetric eigensolver, ascending),
+ * X <- X Q.  Requires h^3 X^T X = I on entry.  eigvals_host (k doubles) receives
+ * Lambda; synchronous on `stream`. */
+int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int k, int dtype, int mode,
+                       double* eigvals_host, void* work, size_t work_bytes, void* stream);
+
+/* rho[s] = sum_{i < n_occ} f_i X[s][i]^2 in FP64 (electron density of the occupied
+ * states; the density evolves together with the subspace, CheFSI paragraph).
+ * occ: device array of n_occ occupations, or NULL for f_i = 2 (spin-degenerate).
+ * rho: device, n_slots doubles. */
+int kscf_density(const kscf_ham* ham, const void* X, int64_t ld, int n_occ, int dtype,
+                 const double* occ, double* rho, void* stream);
+
+/* Initial subspace: X[s][j] = N(0,1) sample number (lex_of_slot[s] * k + j) of the
+ * counter-based generator (SplitMix64 finaliser keyed by seed, Box-Muller pairs; the
+ * definition is in the implementation's comments), 0 in padding rows.  The values do
+ * not depend on the slot order, so any layout sees the same X0. */
+int kscf_random_subspace(const kscf_ham* ham, void* X, int64_t ld, int k, int dtype,
+                         uint64_t seed, void* stream);
+
+/* Hilbert index of brick coordinates (x, y, z) on the 2^bits cube, as used to order the
+ * bricks (Skilling 2004 transpose algorithm; bits interleaved most significant first,
+ * x first).  Pure host function, exported for tests of the ordering. */
+uint64_t kscf_hilbert_index3(uint32_t x, uint32_t y, uint32_t z, int bits);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KSCF_H */

@@ -1,0 +1,491 @@
+// C ABI drivers of the CheFSI hot path: Hamiltonian apply, Chebyshev filter,
+// Cholesky-QR, Rayleigh-Ritz, density and the initial subspace (arXiv 2303.00790,
+// CheFSI paragraph).  The k x k FP64 factorisations call cuSOLVER.
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "kscf_internal.h"
+
+using namespace kscf;
+
+namespace kscf {
+cudaError_t launch_gram_tc(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t rows, int m, int n,
+                           double scale, double* C, int64_t ldc, bool accumulate, void* work, size_t work_bytes,
+                           cudaStream_t st);
+cudaError_t launch_rotate_tc(const float* A, int64_t lda, const double* Q, int64_t ldq, int64_t rows, int kin,
+                             int kout, bool add_identity_input, float* out, int64_t ldo, void* work,
+                             size_t work_bytes, cudaStream_t st);
+size_t gram_tc_work_bytes(int64_t rows, int m, int n);
+size_t rotate_tc_work_bytes(int64_t rows, int kin, int kout);
+bool tc_available();
+}  // namespace kscf
+
+namespace {
+
+// ---- per-device cuSOLVER handles ----
+std::mutex g_mu;
+std::vector<cusolverDnHandle_t> g_handles;
+
+int solver_handle(cusolverDnHandle_t* out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    set_error("cudaGetDevice failed");
+    return KSCF_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  if ((int)g_handles.size() <= dev) g_handles.resize(dev + 1, nullptr);
+  if (!g_handles[dev]) {
+    if (cusolverDnCreate(&g_handles[dev]) != CUSOLVER_STATUS_SUCCESS) {
+      set_error("cusolverDnCreate failed");
+      return KSCF_ERR_CUDA;
+    }
+  }
+  *out = g_handles[dev];
+  return KSCF_OK;
+}
+
+#define SOLVER_TRY(expr)                                                              \
+  do {                                                                                \
+    cusolverStatus_t _s = (expr);                                                     \
+    if (_s != CUSOLVER_STATUS_SUCCESS) {                                              \
+      set_error("%s failed with cuSOLVER status %d (%s:%d)", #expr, (int)_s, __FILE__, \
+                __LINE__);                                                            \
+      return KSCF_ERR_CUDA;                                                           \
+    }                                                                                 \
+  } while (0)
+
+size_t esize(int dtype) { return dtype == KSCF_F64 ? 8 : 4; }
+
+int check_common(const kscf_ham* ham, const void* X, int64_t ld, int k, int dtype, const char* who) {
+  if (!ham || !X) {
+    set_error("%s: null argument", who);
+    return KSCF_ERR_INVALID;
+  }
+  if (dtype != KSCF_F64 && dtype != KSCF_F32) {
+    set_error("%s: dtype must be KSCF_F64 or KSCF_F32", who);
+    return KSCF_ERR_INVALID;
+  }
+  if (k < 1 || ld < k) {
+    set_error("%s: need k >= 1 and ld >= k (k=%d, ld=%lld)", who, k, (long long)ld);
+    return KSCF_ERR_INVALID;
+  }
+  return KSCF_OK;
+}
+
+int block_width(int k, int block) { return (block <= 0 || block > k) ? k : block; }
+
+// Carves aligned pieces out of the caller's work buffer.
+struct Carver {
+  char* base;
+  size_t used = 0;
+  explicit Carver(void* b) : base((char*)b) {}
+  void* take(size_t bytes) {
+    void* p = base ? base + used : nullptr;
+    used += kscf_align256(bytes);
+    return p;
+  }
+};
+
+// rows per panel of the in-place rotation (panel buffer = rows x k)
+int64_t panel_rows(int64_t n_slots, int k, int dtype) {
+  const size_t target = (size_t)256 << 20;
+  int64_t r = (int64_t)(target / ((size_t)k * esize(dtype)));
+  r = std::max<int64_t>(r, 512);
+  r = (r / 512) * 512;
+  return std::min<int64_t>(r, n_slots);
+}
+
+struct OrthoPlan {
+  size_t S, Rinv, info, lwork_bytes, host_bytes, panel, tc;
+  int64_t prows;
+};
+
+int ortho_plan(const Ham& H, int k, int dtype, int mode, OrthoPlan* p) {
+  cusolverDnHandle_t hs;
+  int rc = solver_handle(&hs);
+  if (rc) return rc;
+  int lw_potrf = 0;
+  SOLVER_TRY(cusolverDnDpotrf_bufferSize(hs, CUBLAS_FILL_MODE_UPPER, k, nullptr, k, &lw_potrf));
+  size_t dev_tr = 0, host_tr = 0;
+  SOLVER_TRY(cusolverDnXtrtri_bufferSize(hs, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, k, CUDA_R_64F,
+                                         nullptr, k, &dev_tr, &host_tr));
+  p->S = (size_t)k * k * 8;
+  p->Rinv = (size_t)k * k * esize(dtype);
+  p->info = 256;
+  p->lwork_bytes = std::max((size_t)lw_potrf * 8, dev_tr) + 256;
+  p->host_bytes = host_tr;
+  p->prows = panel_rows(H.grid.n_slots, k, dtype);
+  p->panel = (size_t)p->prows * k * esize(dtype);
+  p->tc = 0;
+  if (mode == KSCF_GEMM_TENSOR)
+    p->tc = std::max(gram_tc_work_bytes(H.grid.n_slots, k, k), rotate_tc_work_bytes(p->prows, k, k));
+  return KSCF_OK;
+}
+
+size_t ortho_bytes(const OrthoPlan& p) {
+  return kscf_align256(p.S) + kscf_align256(p.Rinv) + kscf_align256(p.info) + kscf_align256(p.lwork_bytes) +
+         kscf_align256(p.panel) + kscf_align256(p.tc);
+}
+
+struct RRPlan {
+  size_t hxb, coef, Hs, W, Q, info, lwork_bytes, panel, tc;
+  int64_t prows;
+  int w;
+};
+
+int rr_plan(const Ham& H, int k, int dtype, int mode, int block, RRPlan* p) {
+  cusolverDnHandle_t hs;
+  int rc = solver_handle(&hs);
+  if (rc) return rc;
+  int lw = 0;
+  SOLVER_TRY(cusolverDnDsyevd_bufferSize(hs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, k, nullptr, k,
+                                         nullptr, &lw));
+  p->w = block_width(k, block);
+  p->hxb = (size_t)H.grid.n_slots * p->w * esize(dtype);
+  p->coef = (size_t)std::max(H.n_kb, 1) * 4 * p->w * esize(dtype);
+  p->Hs = (size_t)k * k * 8;
+  p->W = (size_t)k * 8;
+  p->Q = (size_t)k * k * esize(dtype);
+  p->info = 256;
+  p->lwork_bytes = (size_t)lw * 8 + 256;
+  p->prows = panel_rows(H.grid.n_slots, k, dtype);
+  p->panel = (size_t)p->prows * k * esize(dtype);
+  p->tc = 0;
+  if (mode == KSCF_GEMM_TENSOR)
+    p->tc = std::max(gram_tc_work_bytes(H.grid.n_slots, k, p->w), rotate_tc_work_bytes(p->prows, k, k));
+  return KSCF_OK;
+}
+
+size_t rr_bytes(const RRPlan& p) {
+  return kscf_align256(p.hxb) + kscf_align256(p.coef) + kscf_align256(p.Hs) + kscf_align256(p.W) +
+         kscf_align256(p.Q) + kscf_align256(p.info) + kscf_align256(p.lwork_bytes) + kscf_align256(p.panel) +
+         kscf_align256(p.tc);
+}
+
+size_t filter_bytes(const Ham& H, int k, int dtype, int block) {
+  const int w = block_width(k, block);
+  return kscf_align256((size_t)H.grid.n_slots * w * esize(dtype)) +
+         kscf_align256((size_t)std::max(H.n_kb, 1) * 4 * w * esize(dtype));
+}
+
+size_t apply_bytes(const Ham& H, int k, int dtype) {
+  return kscf_align256((size_t)std::max(H.n_kb, 1) * 4 * k * esize(dtype));
+}
+
+int check_work(void* work, size_t have, size_t need, const char* who) {
+  if (have < need || (need > 0 && !work)) {
+    set_error("%s: work buffer of %zu bytes, need %zu", who, have, need);
+    return KSCF_ERR_WORKSPACE;
+  }
+  if (((uintptr_t)work & 255) != 0) {
+    set_error("%s: work buffer must be 256-byte aligned", who);
+    return KSCF_ERR_INVALID;
+  }
+  return KSCF_OK;
+}
+
+int check_mode(int dtype, int mode, const char* who) {
+  if (mode != KSCF_GEMM_NATIVE && mode != KSCF_GEMM_TENSOR) {
+    set_error("%s: unknown GEMM mode %d", who, mode);
+    return KSCF_ERR_INVALID;
+  }
+  if (mode == KSCF_GEMM_TENSOR && dtype != KSCF_F32) {
+    set_error("%s: tensor-core mode needs F32 X", who);
+    return KSCF_ERR_UNSUPPORTED;
+  }
+  return KSCF_OK;
+}
+
+// X <- X Qm (Qm column-major k x k in the dtype of X for the native path, FP64 for the
+// tensor path) in row panels through the panel buffer.
+int rotate_inplace(void* X, int64_t ld, int64_t rows, int k, int dtype, int mode, const void* Qm, const double* Q64,
+                   bool near_identity, void* panel, int64_t prows, void* tcwork, size_t tcbytes, cudaStream_t st) {
+  const size_t es = esize(dtype);
+  for (int64_t r0 = 0; r0 < rows; r0 += prows) {
+    const int64_t nr = std::min(prows, rows - r0);
+    char* Xr = (char*)X + (size_t)r0 * ld * es;
+    if (mode == KSCF_GEMM_TENSOR) {
+      KSCF_CUDA_TRY(launch_rotate_tc((const float*)Xr, ld, Q64, k, nr, k, k, near_identity, (float*)panel, k,
+                                     tcwork, tcbytes, st));
+    } else {
+      KSCF_CUDA_TRY(launch_rotate_native(Xr, ld, Qm, k, nr, k, k, dtype, panel, k, st));
+    }
+    KSCF_CUDA_TRY(launch_copy_cols(panel, k, Xr, ld, nr, k, dtype, st));
+  }
+  return KSCF_OK;
+}
+
+int gram(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t rows, int m, int n, int dtype, int mode,
+         double scale, double* C, int64_t ldc, void* tcwork, size_t tcbytes, cudaStream_t st) {
+  if (mode == KSCF_GEMM_TENSOR) {
+    KSCF_CUDA_TRY(launch_gram_tc((const float*)A, lda, (const float*)B, ldb, rows, m, n, scale, C, ldc, false,
+                                 tcwork, tcbytes, st));
+  } else {
+    KSCF_CUDA_TRY(launch_gram_native(A, lda, B, ldb, rows, m, n, dtype, scale, C, ldc, false, st));
+  }
+  return KSCF_OK;
+}
+
+// One Cholesky-QR pass: S = h^3 X^T X, S = R^T R, X <- X R^-1.
+int cholqr_pass(const Ham& H, void* X, int64_t ld, int k, int dtype, int mode, const OrthoPlan& p, Carver& cv,
+                bool second_pass, cudaStream_t st) {
+  cusolverDnHandle_t hs;
+  int rc = solver_handle(&hs);
+  if (rc) return rc;
+  SOLVER_TRY(cusolverDnSetStream(hs, st));
+  Carver c = cv;
+  double* S = (double*)c.take(p.S);
+  void* Rinv = c.take(p.Rinv);
+  int* info = (int*)c.take(p.info);
+  void* lwork = c.take(p.lwork_bytes);
+  void* panel = c.take(p.panel);
+  void* tcw = c.take(p.tc);
+  const double h3 = H.grid.h * H.grid.h * H.grid.h;
+  const int64_t rows = H.grid.n_slots;
+  rc = gram(X, ld, X, ld, rows, k, k, dtype, mode, h3, S, k, tcw, p.tc, st);
+  if (rc) return rc;
+  SOLVER_TRY(cusolverDnDpotrf(hs, CUBLAS_FILL_MODE_UPPER, k, S, k, (double*)lwork, (int)(p.lwork_bytes / 8 - 32),
+                              info));
+  int hinfo = 0;
+  KSCF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  KSCF_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hinfo != 0) {
+    set_error("Cholesky-QR: Gram matrix not positive definite (potrf info %d%s)", hinfo,
+              second_pass ? ", second pass" : "");
+    return KSCF_ERR_NOT_SPD;
+  }
+  std::vector<char> hostw(std::max<size_t>(p.host_bytes, 1));
+  SOLVER_TRY(cusolverDnXtrtri(hs, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, k, CUDA_R_64F, S, k, lwork,
+                              p.lwork_bytes - 256, hostw.data(), p.host_bytes, info));
+  // S now holds R^-1 in its upper triangle; zero the rest (and convert for the native path)
+  KSCF_CUDA_TRY(launch_upper_to_dtype(S, k, KSCF_F64, S, st));
+  if (mode != KSCF_GEMM_TENSOR) KSCF_CUDA_TRY(launch_upper_to_dtype(S, k, dtype, Rinv, st));
+  rc = rotate_inplace(X, ld, rows, k, dtype, mode, Rinv, S, second_pass, panel, p.prows, tcw, p.tc, st);
+  if (rc) return rc;
+  // the trtri status is read together with the next synchronisation
+  KSCF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  KSCF_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hinfo != 0) {
+    set_error("Cholesky-QR: triangular inverse failed (info %d)", hinfo);
+    return KSCF_ERR_NOT_SPD;
+  }
+  return KSCF_OK;
+}
+
+}  // namespace
+
+extern "C" int kscf_workspace_size(const kscf_ham* ham, int op, int k, int dtype, int mode, int block,
+                                   size_t* bytes) {
+  if (!ham || !bytes || k < 1 || (dtype != KSCF_F64 && dtype != KSCF_F32)) {
+    set_error("kscf_workspace_size: invalid argument");
+    return KSCF_ERR_INVALID;
+  }
+  const Ham& H = ham->h;
+  switch (op) {
+    case KSCF_OP_APPLY:
+      *bytes = apply_bytes(H, k, dtype);
+      return KSCF_OK;
+    case KSCF_OP_FILTER:
+      *bytes = filter_bytes(H, k, dtype, block);
+      return KSCF_OK;
+    case KSCF_OP_ORTHO: {
+      int rc = check_mode(dtype, mode, "kscf_workspace_size");
+      if (rc) return rc;
+      OrthoPlan p;
+      rc = ortho_plan(H, k, dtype, mode, &p);
+      if (rc) return rc;
+      *bytes = ortho_bytes(p);
+      return KSCF_OK;
+    }
+    case KSCF_OP_RR: {
+      int rc = check_mode(dtype, mode, "kscf_workspace_size");
+      if (rc) return rc;
+      RRPlan p;
+      rc = rr_plan(H, k, dtype, mode, block, &p);
+      if (rc) return rc;
+      *bytes = rr_bytes(p);
+      return KSCF_OK;
+    }
+  }
+  set_error("kscf_workspace_size: unknown op %d", op);
+  return KSCF_ERR_INVALID;
+}
+
+extern "C" int kscf_hamiltonian_apply(const kscf_ham* ham, void* Y, int64_t ld_y, void* HY, int64_t ld_hy, int k,
+                                      int dtype, void* work, size_t work_bytes, void* stream) {
+  int rc = check_common(ham, Y, ld_y, k, dtype, "kscf_hamiltonian_apply");
+  if (rc) return rc;
+  if (!HY || ld_hy < k) {
+    set_error("kscf_hamiltonian_apply: bad output");
+    return KSCF_ERR_INVALID;
+  }
+  const Ham& H = ham->h;
+  rc = check_work(work, work_bytes, apply_bytes(H, k, dtype), "kscf_hamiltonian_apply");
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  KSCF_CUDA_TRY(launch_zero_rows(H, Y, ld_y, k, dtype, st));
+  KSCF_CUDA_TRY(launch_kb_gather(H, Y, ld_y, k, dtype, work, st));
+  KSCF_CUDA_TRY(launch_cheb_step(H, Y, ld_y, nullptr, 0, HY, ld_hy, k, dtype, 1.0, 0.0, 0.0, work, st));
+  return KSCF_OK;
+}
+
+extern "C" int kscf_chebyshev_filter(const kscf_ham* ham, void* X, int64_t ld, int k, int degree, double a,
+                                     double b, double a0, int dtype, int block, void* work, size_t work_bytes,
+                                     void* stream) {
+  int rc = check_common(ham, X, ld, k, dtype, "kscf_chebyshev_filter");
+  if (rc) return rc;
+  if (degree < 1 || !(a0 < a) || !(a < b) || !std::isfinite(a) || !std::isfinite(b) || !std::isfinite(a0)) {
+    set_error("kscf_chebyshev_filter: need degree >= 1 and finite a0 < a < b");
+    return KSCF_ERR_INVALID;
+  }
+  const Ham& H = ham->h;
+  rc = check_work(work, work_bytes, filter_bytes(H, k, dtype, block), "kscf_chebyshev_filter");
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int w = block_width(k, block);
+  const size_t es = esize(dtype);
+  Carver cv(work);
+  void* buf = cv.take((size_t)H.grid.n_slots * w * es);
+  void* coef = cv.take((size_t)std::max(H.n_kb, 1) * 4 * w * es);
+  const double e = (b - a) / 2.0, c = (b + a) / 2.0;
+  const double sigma1 = e / (a0 - c), tau = 2.0 / sigma1;
+  KSCF_CUDA_TRY(launch_zero_rows(H, X, ld, k, dtype, st));
+  for (int c0 = 0; c0 < k; c0 += w) {
+    const int wb = std::min(w, k - c0);
+    char* Xb = (char*)X + (size_t)c0 * es;
+    // Y_1 = (sigma_1/e)(H X - c X)   -> buf
+    KSCF_CUDA_TRY(launch_kb_gather(H, Xb, ld, wb, dtype, coef, st));
+    KSCF_CUDA_TRY(launch_cheb_step(H, Xb, ld, nullptr, 0, buf, wb, wb, dtype, sigma1 / e, 0.0, c, coef, st));
+    void* cur = buf;
+    int64_t ld_cur = wb;
+    void* prv = Xb;
+    int64_t ld_prv = ld;
+    double sigma = sigma1;
+    for (int j = 2; j <= degree; j++) {
+      const double sigma_new = 1.0 / (tau - sigma);
+      KSCF_CUDA_TRY(launch_kb_gather(H, cur, ld_cur, wb, dtype, coef, st));
+      // Y_j overwrites Y_{j-2} in place (each element is read before it is written)
+      KSCF_CUDA_TRY(launch_cheb_step(H, cur, ld_cur, prv, ld_prv, prv, ld_prv, wb, dtype, 2.0 * sigma_new / e,
+                                     -sigma * sigma_new, c, coef, st));
+      std::swap(cur, prv);
+      std::swap(ld_cur, ld_prv);
+      sigma = sigma_new;
+    }
+    if (cur != (void*)Xb) KSCF_CUDA_TRY(launch_copy_cols(cur, ld_cur, Xb, ld, H.grid.n_slots, wb, dtype, st));
+  }
+  return KSCF_OK;
+}
+
+extern "C" int kscf_orthonormalize(const kscf_ham* ham, void* X, int64_t ld, int k, int dtype, int mode, void* work,
+                                   size_t work_bytes, void* stream) {
+  int rc = check_common(ham, X, ld, k, dtype, "kscf_orthonormalize");
+  if (rc) return rc;
+  rc = check_mode(dtype, mode, "kscf_orthonormalize");
+  if (rc) return rc;
+  const Ham& H = ham->h;
+  OrthoPlan p;
+  rc = ortho_plan(H, k, dtype, mode, &p);
+  if (rc) return rc;
+  rc = check_work(work, work_bytes, ortho_bytes(p), "kscf_orthonormalize");
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  KSCF_CUDA_TRY(launch_zero_rows(H, X, ld, k, dtype, st));
+  Carver cv(work);
+  rc = cholqr_pass(H, X, ld, k, dtype, mode, p, cv, false, st);
+  if (rc) return rc;
+  if (dtype == KSCF_F32) rc = cholqr_pass(H, X, ld, k, dtype, mode, p, cv, true, st);
+  return rc;
+}
+
+extern "C" int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int k, int dtype, int mode,
+                                  double* eigvals_host, void* work, size_t work_bytes, void* stream) {
+  int rc = check_common(ham, X, ld, k, dtype, "kscf_rayleigh_ritz");
+  if (rc) return rc;
+  rc = check_mode(dtype, mode, "kscf_rayleigh_ritz");
+  if (rc) return rc;
+  if (!eigvals_host) {
+    set_error("kscf_rayleigh_ritz: null eigvals_host");
+    return KSCF_ERR_INVALID;
+  }
+  const Ham& H = ham->h;
+  // block width of the H X stream: bounded so that the N x w buffer stays modest
+  int block = k;
+  {
+    const size_t cap = (size_t)1 << 30;
+    const size_t per_col = (size_t)H.grid.n_slots * esize(dtype);
+    if ((size_t)k * per_col > cap) block = std::max<int>(32, (int)(cap / per_col) / 32 * 32);
+  }
+  RRPlan p;
+  rc = rr_plan(H, k, dtype, mode, block, &p);
+  if (rc) return rc;
+  rc = check_work(work, work_bytes, rr_bytes(p), "kscf_rayleigh_ritz");
+  if (rc) return rc;
+  cusolverDnHandle_t hs;
+  rc = solver_handle(&hs);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  SOLVER_TRY(cusolverDnSetStream(hs, st));
+  Carver cv(work);
+  void* hxb = cv.take(p.hxb);
+  void* coef = cv.take(p.coef);
+  double* Hs = (double*)cv.take(p.Hs);
+  double* W = (double*)cv.take(p.W);
+  void* Qm = cv.take(p.Q);
+  int* info = (int*)cv.take(p.info);
+  double* lwork = (double*)cv.take(p.lwork_bytes);
+  void* panel = cv.take(p.panel);
+  void* tcw = cv.take(p.tc);
+  const size_t es = esize(dtype);
+  const double h3 = H.grid.h * H.grid.h * H.grid.h;
+  const int64_t rows = H.grid.n_slots;
+  KSCF_CUDA_TRY(launch_zero_rows(H, X, ld, k, dtype, st));
+  for (int c0 = 0; c0 < k; c0 += p.w) {
+    const int wb = std::min(p.w, k - c0);
+    char* Xb = (char*)X + (size_t)c0 * es;
+    KSCF_CUDA_TRY(launch_kb_gather(H, Xb, ld, wb, dtype, coef, st));
+    KSCF_CUDA_TRY(launch_cheb_step(H, Xb, ld, nullptr, 0, hxb, wb, wb, dtype, 1.0, 0.0, 0.0, coef, st));
+    // Hs[:, c0:c0+wb] = h^3 X^T (H X_b)
+    rc = gram(X, ld, hxb, wb, rows, k, wb, dtype, mode, h3, Hs + (size_t)c0 * k, k, tcw, p.tc, st);
+    if (rc) return rc;
+  }
+  KSCF_CUDA_TRY(launch_symmetrize(Hs, k, k, st));
+  SOLVER_TRY(cusolverDnDsyevd(hs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, k, Hs, k, W, lwork,
+                              (int)(p.lwork_bytes / 8 - 32), info));
+  if (mode != KSCF_GEMM_TENSOR) KSCF_CUDA_TRY(launch_f64_to_dtype(Hs, (int64_t)k * k, dtype, Qm, st));
+  int hinfo = 0;
+  KSCF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  KSCF_CUDA_TRY(cudaMemcpyAsync(eigvals_host, W, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+  KSCF_CUDA_TRY(cudaStreamSynchronize(st));
+  if (hinfo != 0) {
+    set_error("kscf_rayleigh_ritz: symmetric eigensolver failed (info %d)", hinfo);
+    return hinfo > 0 ? KSCF_ERR_NO_CONVERGE : KSCF_ERR_INVALID;
+  }
+  for (int i = 0; i < k; i++)
+    if (!std::isfinite(eigvals_host[i])) {
+      set_error("kscf_rayleigh_ritz: non-finite Ritz value");
+      return KSCF_ERR_NONFINITE;
+    }
+  return rotate_inplace(X, ld, rows, k, dtype, mode, Qm, Hs, false, panel, p.prows, tcw, p.tc, st);
+}
+
+extern "C" int kscf_density(const kscf_ham* ham, const void* X, int64_t ld, int n_occ, int dtype, const double* occ,
+                            double* rho, void* stream) {
+  if (!ham || !X || !rho || n_occ < 0 || ld < n_occ || (dtype != KSCF_F64 && dtype != KSCF_F32)) {
+    set_error("kscf_density: invalid argument");
+    return KSCF_ERR_INVALID;
+  }
+  KSCF_CUDA_TRY(launch_density(ham->h, X, ld, n_occ, dtype, occ, rho, (cudaStream_t)stream));
+  return KSCF_OK;
+}
+
+extern "C" int kscf_random_subspace(const kscf_ham* ham, void* X, int64_t ld, int k, int dtype, uint64_t seed,
+                                    void* stream) {
+  int rc = check_common(ham, X, ld, k, dtype, "kscf_random_subspace");
+  if (rc) return rc;
+  KSCF_CUDA_TRY(launch_random(ham->h, X, ld, k, dtype, seed, (cudaStream_t)stream));
+  return KSCF_OK;
+}

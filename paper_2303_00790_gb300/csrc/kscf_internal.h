@@ -1,0 +1,134 @@
+// Internal structures shared by the translation units of libkscf.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/kscf.h"
+
+namespace kscf {
+
+// thread-local error message
+void set_error(const char* fmt, ...);
+// counts kernel launches made by this library (all threads)
+void count_launch();
+
+struct Grid {
+  double h = 0.0;
+  double center[3] = {0, 0, 0};
+  int B = 8;                       // brick edge
+  int lo[3] = {0, 0, 0};           // smallest (i,j,k)
+  int ext[3] = {0, 0, 0};          // bounding-box extent in points
+  int nb[3] = {0, 0, 0};           // bricks per axis over the bounding box
+  int64_t n_points = 0, n_bricks = 0, n_slots = 0;
+  std::vector<int32_t> brick_xyz;     // 3 per kept brick (brick coordinates)
+  std::vector<int32_t> brick_of_box;  // nb0*nb1*nb2 -> brick rank or -1
+  std::vector<int32_t> nbr;           // 6 per brick: -x,+x,-y,+y,-z,+z ranks or -1
+  std::vector<int64_t> lex_of_slot;   // n_slots, -1 for padding
+  std::vector<uint8_t> mask;          // n_slots, 1 inside the domain
+
+  // slot of integer point (i,j,k) or -1 when outside the bounding box / dropped brick
+  int64_t slot_of(int i, int j, int k) const {
+    int x = i - lo[0], y = j - lo[1], z = k - lo[2];
+    if (x < 0 || y < 0 || z < 0 || x >= nb[0] * B || y >= nb[1] * B || z >= nb[2] * B) return -1;
+    int bx = x / B, by = y / B, bz = z / B;
+    int32_t r = brick_of_box[((int64_t)bz * nb[1] + by) * nb[0] + bx];
+    if (r < 0) return -1;
+    return (int64_t)r * B * B * B + ((int64_t)(z - bz * B) * B + (y - by * B)) * B + (x - bx * B);
+  }
+  void slot_ijk(int64_t s, int* ijk) const {
+    int64_t r = s / ((int64_t)B * B * B);
+    int li = (int)(s % ((int64_t)B * B * B));
+    ijk[0] = lo[0] + brick_xyz[3 * r + 0] * B + li % B;
+    ijk[1] = lo[1] + brick_xyz[3 * r + 1] * B + (li / B) % B;
+    ijk[2] = lo[2] + brick_xyz[3 * r + 2] * B + li / (B * B);
+  }
+};
+
+// Device-side tables of the Hamiltonian.
+struct Ham {
+  Grid grid;                       // host copy of the grid tables
+  int M = 6;
+  double stencil[7];               // -1/2 h^-2 w_k (k = 0..6); the centre uses 3*stencil[0]
+  int device = 0;
+  // device arrays
+  int32_t* d_nbr = nullptr;        // n_bricks*6
+  uint8_t* d_mask = nullptr;       // n_slots
+  int64_t* d_lex = nullptr;        // n_slots
+  int64_t* d_pad = nullptr;        // padding slots
+  int64_t n_pad = 0;
+  double* d_v64 = nullptr;         // n_slots
+  float* d_v32 = nullptr;          // n_slots
+  // KB tables
+  int n_kb = 0;                    // atoms with projectors
+  int64_t n_kb_entries = 0;
+  int64_t* d_kb_atom_ptr = nullptr;   // n_kb+1, entries per atom
+  int64_t* d_kb_atom_slot = nullptr;  // entry -> slot
+  double* d_kb_atom_chi64 = nullptr;  // entry*4
+  float* d_kb_atom_chi32 = nullptr;
+  int64_t* d_kb_slot_ptr = nullptr;   // n_slots+1, entries per slot
+  int32_t* d_kb_slot_atom = nullptr;  // entry -> kb atom
+  double* d_kb_slot_chi64 = nullptr;  // entry*4
+  float* d_kb_slot_chi32 = nullptr;
+  double* d_kb_energy = nullptr;      // n_kb*4: E_l * h^3
+  double kb_upper = 0.0, kb_lower = 0.0;  // Gershgorin bounds of V_NL
+  int max_slot_entries = 0;
+};
+
+// ---- launchers (filter.cu) ----
+cudaError_t launch_zero_rows(const Ham& H, void* X, int64_t ld, int k, int dtype, cudaStream_t st);
+cudaError_t launch_kb_gather(const Ham& H, const void* Y, int64_t ld, int w, int dtype, void* coef,
+                             cudaStream_t st);
+cudaError_t launch_cheb_step(const Ham& H, const void* in, int64_t ld_in, const void* prev,
+                             int64_t ld_prev, void* out, int64_t ld_out, int w, int dtype,
+                             double alpha, double beta, double c, const void* coef, cudaStream_t st);
+cudaError_t launch_copy_cols(const void* src, int64_t ld_src, void* dst, int64_t ld_dst, int64_t rows,
+                             int w, int dtype, cudaStream_t st);
+
+// ---- launchers (setup.cu) ----
+cudaError_t launch_vloc(const Ham& H, const double* d_xyz /*n_slots*3*/, const double* d_atoms /*n*8*/,
+                        int n_atoms, cudaStream_t st);
+cudaError_t launch_v_to_f32(const Ham& H, cudaStream_t st);
+cudaError_t launch_random(const Ham& H, void* X, int64_t ld, int k, int dtype, uint64_t seed,
+                          cudaStream_t st);
+cudaError_t launch_density(const Ham& H, const void* X, int64_t ld, int n_occ, int dtype,
+                           const double* occ, double* rho, cudaStream_t st);
+cudaError_t launch_minmax_v(const Ham& H, double* d_out2, cudaStream_t st);
+cudaError_t launch_mask_v(const Ham& H, const double* src, double* dst, cudaStream_t st);
+
+// ---- launchers (gemm.cu) ----
+// C[i + j*ldc] (+)= scale * sum_r A[r*lda + i] * B[r*ldb + j], i < m, j < n, r < rows.
+cudaError_t launch_gram_native(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t rows,
+                               int m, int n, int dtype, double scale, double* C, int64_t ldc,
+                               bool accumulate, cudaStream_t st);
+// out[r*ldo + j] = sum_i A[r*lda + i] * Q[i + j*ldq]  (Q column-major, dtype of A)
+cudaError_t launch_rotate_native(const void* A, int64_t lda, const void* Q, int64_t ldq, int64_t rows,
+                                 int kin, int kout, int dtype, void* out, int64_t ldo, cudaStream_t st);
+cudaError_t launch_symmetrize(double* C, int k, int64_t ldc, cudaStream_t st);
+cudaError_t launch_upper_to_dtype(const double* R, int k, int dtype, void* out, cudaStream_t st);
+cudaError_t launch_f64_to_dtype(const double* src, int64_t n, int dtype, void* out, cudaStream_t st);
+
+}  // namespace kscf
+
+struct kscf_grid {
+  kscf::Grid g;
+};
+struct kscf_ham {
+  kscf::Ham h;
+};
+
+#define KSCF_CUDA_TRY(expr)                                                         \
+  do {                                                                              \
+    cudaError_t _e = (expr);                                                        \
+    if (_e != cudaSuccess) {                                                        \
+      kscf::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e),      \
+                      __FILE__, __LINE__);                                          \
+      return KSCF_ERR_CUDA;                                                         \
+    }                                                                               \
+  } while (0)
+
+inline size_t kscf_align256(size_t x) { return (x + 255) & ~(size_t)255; }

@@ -1,0 +1,329 @@
+"""Thin ctypes binding of libkscf (include/kscf.h).
+
+Argument marshalling only: every computation runs in the CUDA library.  Device
+arrays are torch tensors (PyTorch provides device memory and streams); their raw
+pointers and the current stream are passed through the C ABI.  There is no CPU
+fallback: if libkscf.so cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkscf.so")
+
+KSCF_OK = 0
+KSCF_ERR_INVALID = -1
+KSCF_ERR_CUDA = -2
+KSCF_ERR_WORKSPACE = -3
+KSCF_ERR_NOT_SPD = -4
+KSCF_ERR_NONFINITE = -5
+KSCF_ERR_NO_CONVERGE = -6
+KSCF_ERR_UNSUPPORTED = -7
+KSCF_ERR_HOST_ALLOC = -8
+KSCF_F64, KSCF_F32 = 0, 1
+KSCF_GEMM_NATIVE, KSCF_GEMM_TENSOR = 0, 1
+KSCF_OP_APPLY, KSCF_OP_FILTER, KSCF_OP_ORTHO, KSCF_OP_RR = 0, 1, 2, 3
+
+
+class KscfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"kscf error {code}: {msg}")
+        self.code = code
+
+
+class kscf_atom(C.Structure):
+    _fields_ = [("x", C.c_double), ("y", C.c_double), ("z", C.c_double),
+                ("z_number", C.c_int32), ("reserved", C.c_int32)]
+
+
+class kscf_species(C.Structure):
+    _fields_ = [("z_number", C.c_int32), ("n_proj", C.c_int32),
+                ("z_valence", C.c_double), ("r_c", C.c_double), ("a_gauss", C.c_double),
+                ("r_gauss", C.c_double), ("e_s", C.c_double), ("e_p", C.c_double),
+                ("r_p", C.c_double), ("r_cut", C.c_double)]
+
+
+class kscf_grid_info(C.Structure):
+    _fields_ = [("n_points", C.c_int64), ("n_slots", C.c_int64), ("n_bricks", C.c_int64),
+                ("brick", C.c_int32), ("lo", C.c_int32 * 3), ("extent", C.c_int32 * 3),
+                ("reserved", C.c_int32), ("h", C.c_double), ("center", C.c_double * 3)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libkscf.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    return C.CDLL(LIB_PATH)
+
+
+lib = _load()
+_vp, _i32, _i64, _d, _sz = C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_size_t
+_sigs = {
+    "kscf_last_error": ([], C.c_char_p),
+    "kscf_launch_counter": ([], C.c_uint64),
+    "kscf_build_grid": ([C.POINTER(_d), _d, _d, _i32, C.POINTER(_vp)], _i32),
+    "kscf_build_grid_box": ([_i32, _i32, _i32, _d, _i32, C.POINTER(_vp)], _i32),
+    "kscf_grid_get_info": ([_vp, C.POINTER(kscf_grid_info)], _i32),
+    "kscf_grid_slots": ([_vp, _vp, _vp], _i32),
+    "kscf_grid_free": ([_vp], _i32),
+    "kscf_build_hamiltonian": ([_vp, C.POINTER(kscf_atom), _i32, C.POINTER(kscf_species), _i32,
+                                C.POINTER(_vp)], _i32),
+    "kscf_ham_free": ([_vp], _i32),
+    "kscf_ham_grid_info": ([_vp, C.POINTER(kscf_grid_info)], _i32),
+    "kscf_set_potential": ([_vp, _vp, _vp], _i32),
+    "kscf_get_potential": ([_vp, _vp, _vp], _i32),
+    "kscf_spectral_bounds": ([_vp, C.POINTER(_d), C.POINTER(_d)], _i32),
+    "kscf_workspace_size": ([_vp, _i32, _i32, _i32, _i32, _i32, C.POINTER(_sz)], _i32),
+    "kscf_hamiltonian_apply": ([_vp, _vp, _i64, _vp, _i64, _i32, _i32, _vp, _sz, _vp], _i32),
+    "kscf_chebyshev_filter": ([_vp, _vp, _i64, _i32, _i32, _d, _d, _d, _i32, _i32, _vp, _sz, _vp], _i32),
+    "kscf_orthonormalize": ([_vp, _vp, _i64, _i32, _i32, _i32, _vp, _sz, _vp], _i32),
+    "kscf_rayleigh_ritz": ([_vp, _vp, _i64, _i32, _i32, _i32, C.POINTER(_d), _vp, _sz, _vp], _i32),
+    "kscf_density": ([_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp], _i32),
+    "kscf_random_subspace": ([_vp, _vp, _i64, _i32, _i32, C.c_uint64, _vp], _i32),
+    "kscf_hilbert_index3": ([C.c_uint32, C.c_uint32, C.c_uint32, _i32], C.c_uint64),
+}
+for _name, (_args, _res) in _sigs.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+EXPORTED = tuple(_sigs)
+
+
+def _check(code: int):
+    if code != KSCF_OK:
+        raise KscfError(code, lib.kscf_last_error().decode(errors="replace"))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float64:
+        return KSCF_F64
+    if t.dtype == torch.float32:
+        return KSCF_F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _rows(t, k: int):
+    if not t.is_cuda or t.dim() != 2 or t.stride(1) != 1 or t.shape[1] < k:
+        raise ValueError("X must be a 2-D CUDA tensor with unit column stride")
+    return t.stride(0)
+
+
+def _work(ham, op, k, dtype, mode=0, block=0, work=None):
+    need = kscf_workspace_size(ham, op, k, dtype, mode, block)
+    if work is None:
+        torch = _torch()
+        work = torch.empty(max(need, 256), dtype=torch.uint8, device="cuda")
+    return work, need
+
+
+# ------------------------------------------------------------------ grid
+def kscf_build_grid(center, radius: float, h: float, brick: int = 8):
+    c = (C.c_double * 3)(*[float(x) for x in center])
+    out = C.c_void_p()
+    _check(lib.kscf_build_grid(c, float(radius), float(h), int(brick), C.byref(out)))
+    return Grid(out)
+
+
+def kscf_build_grid_box(nx: int, ny: int, nz: int, h: float, brick: int = 8):
+    out = C.c_void_p()
+    _check(lib.kscf_build_grid_box(nx, ny, nz, float(h), int(brick), C.byref(out)))
+    return Grid(out)
+
+
+def _info_dict(info: kscf_grid_info) -> dict:
+    return {"n_points": info.n_points, "n_slots": info.n_slots, "n_bricks": info.n_bricks,
+            "brick": info.brick, "lo": tuple(info.lo), "extent": tuple(info.extent), "h": info.h,
+            "center": tuple(info.center)}
+
+
+class Grid:
+    def __init__(self, handle):
+        self.handle = handle
+        info = kscf_grid_info()
+        _check(lib.kscf_grid_get_info(handle, C.byref(info)))
+        self.info = _info_dict(info)
+
+    def slots(self):
+        """(lex_of_slot int64 (n_slots,), ijk_of_slot int32 (n_slots, 3))"""
+        n = self.info["n_slots"]
+        lex = np.empty(n, dtype=np.int64)
+        ijk = np.empty((n, 3), dtype=np.int32)
+        _check(lib.kscf_grid_slots(self.handle, lex.ctypes.data_as(C.c_void_p), ijk.ctypes.data_as(C.c_void_p)))
+        return lex, ijk
+
+    def free(self):
+        if self.handle:
+            lib.kscf_grid_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ Hamiltonian
+def species_array(species):
+    arr = (kscf_species * len(species))()
+    for i, s in enumerate(species):
+        arr[i] = kscf_species(int(s["z_number"]), int(s["n_proj"]), float(s["z_valence"]), float(s["r_c"]),
+                              float(s["a_gauss"]), float(s["r_gauss"]), float(s["e_s"]), float(s["e_p"]),
+                              float(s["r_p"]), float(s["r_cut"]))
+    return arr
+
+
+def atom_array(pos, z):
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    arr = (kscf_atom * max(len(pos), 1))()
+    for i in range(len(pos)):
+        arr[i] = kscf_atom(float(pos[i, 0]), float(pos[i, 1]), float(pos[i, 2]), int(z[i]), 0)
+    return arr, len(pos)
+
+
+def kscf_build_hamiltonian(grid: Grid, atom_pos, atom_z, species):
+    atoms, n = atom_array(atom_pos, atom_z)
+    sp = species_array(species)
+    out = C.c_void_p()
+    _check(lib.kscf_build_hamiltonian(grid.handle, atoms, n, sp, len(species), C.byref(out)))
+    return Hamiltonian(out)
+
+
+class Hamiltonian:
+    def __init__(self, handle):
+        self.handle = handle
+        info = kscf_grid_info()
+        _check(lib.kscf_ham_grid_info(handle, C.byref(info)))
+        self.info = _info_dict(info)
+        self.n_slots = self.info["n_slots"]
+        self.h3 = self.info["h"] ** 3
+
+    def free(self):
+        if self.handle:
+            lib.kscf_ham_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def kscf_spectral_bounds(ham: Hamiltonian):
+    lo, hi = C.c_double(), C.c_double()
+    _check(lib.kscf_spectral_bounds(ham.handle, C.byref(lo), C.byref(hi)))
+    return lo.value, hi.value
+
+
+def kscf_set_potential(ham: Hamiltonian, v_slots, stream=None):
+    torch = _torch()
+    assert v_slots.is_cuda and v_slots.dtype == torch.float64 and v_slots.numel() >= ham.n_slots
+    _check(lib.kscf_set_potential(ham.handle, C.c_void_p(v_slots.data_ptr()), _stream(stream)))
+
+
+def kscf_get_potential(ham: Hamiltonian, stream=None):
+    torch = _torch()
+    v = torch.empty(ham.n_slots, dtype=torch.float64, device="cuda")
+    _check(lib.kscf_get_potential(ham.handle, C.c_void_p(v.data_ptr()), _stream(stream)))
+    return v
+
+
+def kscf_workspace_size(ham: Hamiltonian, op: int, k: int, dtype: int, mode: int = 0, block: int = 0) -> int:
+    n = C.c_size_t()
+    _check(lib.kscf_workspace_size(ham.handle, op, k, dtype, mode, block, C.byref(n)))
+    return n.value
+
+
+# ------------------------------------------------------------------ hot path
+def kscf_hamiltonian_apply(ham: Hamiltonian, Y, HY, k: int | None = None, work=None, stream=None):
+    k = Y.shape[1] if k is None else k
+    dt = _dtype_code(Y)
+    work, need = _work(ham, KSCF_OP_APPLY, k, dt, work=work)
+    _check(lib.kscf_hamiltonian_apply(ham.handle, C.c_void_p(Y.data_ptr()), _rows(Y, k), C.c_void_p(HY.data_ptr()),
+                                      _rows(HY, k), k, dt, C.c_void_p(work.data_ptr()), work.numel(),
+                                      _stream(stream)))
+    return HY
+
+
+def kscf_chebyshev_filter(ham: Hamiltonian, X, degree: int, a: float, b: float, a0: float, k: int | None = None,
+                          block: int = 0, work=None, stream=None):
+    k = X.shape[1] if k is None else k
+    dt = _dtype_code(X)
+    work, need = _work(ham, KSCF_OP_FILTER, k, dt, block=block, work=work)
+    _check(lib.kscf_chebyshev_filter(ham.handle, C.c_void_p(X.data_ptr()), _rows(X, k), k, degree, a, b, a0, dt,
+                                     block, C.c_void_p(work.data_ptr()), work.numel(), _stream(stream)))
+    return X
+
+
+def kscf_orthonormalize(ham: Hamiltonian, X, mode: int = KSCF_GEMM_NATIVE, k: int | None = None, work=None,
+                        stream=None):
+    k = X.shape[1] if k is None else k
+    dt = _dtype_code(X)
+    work, need = _work(ham, KSCF_OP_ORTHO, k, dt, mode=mode, work=work)
+    _check(lib.kscf_orthonormalize(ham.handle, C.c_void_p(X.data_ptr()), _rows(X, k), k, dt, mode,
+                                   C.c_void_p(work.data_ptr()), work.numel(), _stream(stream)))
+    return X
+
+
+def kscf_rayleigh_ritz(ham: Hamiltonian, X, mode: int = KSCF_GEMM_NATIVE, k: int | None = None, work=None,
+                       stream=None):
+    k = X.shape[1] if k is None else k
+    dt = _dtype_code(X)
+    work, need = _work(ham, KSCF_OP_RR, k, dt, mode=mode, work=work)
+    lam = np.empty(k, dtype=np.float64)
+    _check(lib.kscf_rayleigh_ritz(ham.handle, C.c_void_p(X.data_ptr()), _rows(X, k), k, dt, mode,
+                                  lam.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(work.data_ptr()),
+                                  work.numel(), _stream(stream)))
+    return lam
+
+
+def kscf_density(ham: Hamiltonian, X, n_occ: int, occ=None, rho=None, stream=None):
+    torch = _torch()
+    if rho is None:
+        rho = torch.empty(ham.n_slots, dtype=torch.float64, device="cuda")
+    occ_ptr = C.c_void_p(occ.data_ptr()) if occ is not None else C.c_void_p(0)
+    _check(lib.kscf_density(ham.handle, C.c_void_p(X.data_ptr()), _rows(X, n_occ), n_occ, _dtype_code(X), occ_ptr,
+                            C.c_void_p(rho.data_ptr()), _stream(stream)))
+    return rho
+
+
+def kscf_random_subspace(ham: Hamiltonian, X, seed: int, k: int | None = None, stream=None):
+    k = X.shape[1] if k is None else k
+    _check(lib.kscf_random_subspace(ham.handle, C.c_void_p(X.data_ptr()), _rows(X, k), k, _dtype_code(X),
+                                    int(seed), _stream(stream)))
+    return X
+
+
+def kscf_launch_counter() -> int:
+    return int(lib.kscf_launch_counter())
+
+
+def kscf_hilbert_index3(x: int, y: int, z: int, bits: int) -> int:
+    return int(lib.kscf_hilbert_index3(x, y, z, bits))
+
+
+# ------------------------------------------------------------------ convenience
+def build_cluster(atom_pos, atom_z, species, radius: float, h: float, brick: int = 8, center=None):
+    """Grid (centred on atom 0 unless `center`) and Hamiltonian for a cluster."""
+    c = np.asarray(atom_pos, dtype=np.float64)[0] if center is None else center
+    g = kscf_build_grid(c, radius, h, brick)
+    H = kscf_build_hamiltonian(g, atom_pos, atom_z, species)
+    return g, H

@@ -1,0 +1,220 @@
+"""GPU parity: every C-ABI call against the FP64 CPU oracle on the same seeded inputs.
+
+Tolerances (derived from the arithmetic):
+  FP64 paths: one H-apply sums ~45 terms of size <= |V| + 3*7.07/(2h^2) ~ 50 |y|, so
+    rounding-order differences are <= ~1e-14 relative to max|Hy|; through the filter,
+    Cholesky-QR and Rayleigh-Ritz they stay below 1e-10 relative.
+  FP32 filter/apply: unit roundoff 6e-8 times the same ~45-term sums -> ~3e-6 of max|Hy|
+    per step; the scaled recurrence keeps |Y_j| ~ |X| so m steps stay below 1e-4 of the
+    column maximum.
+"""
+import numpy as np
+import pytest
+
+from helpers import from_slots, small_cluster, subspace_gap, to_slots
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def kscf():
+    from paper_2303_00790_gb300.build import build
+    build()
+    from paper_2303_00790_gb300 import kscf as mod
+    return mod
+
+
+@pytest.fixture(scope="module", params=[8, 16])
+def system(request, kscf, species):
+    from oracle.system import cluster_hamiltonian
+    pos, z = small_cluster()
+    R, h = 9.0, 0.7
+    g, H = kscf.build_cluster(pos, z, species, R, h, brick=request.param)
+    OH = cluster_hamiltonian(pos, z, species, R, h)
+    lex, ijk = g.slots()
+    return {"g": g, "H": H, "OH": OH, "lex": lex, "n": g.info["n_points"], "brick": request.param}
+
+
+def dev(a, dtype=torch.float64):
+    return torch.tensor(a, dtype=dtype, device="cuda")
+
+
+def test_potential_matches_oracle(kscf, system):
+    V = kscf.kscf_get_potential(system["H"]).cpu().numpy()
+    Vl = from_slots(V, system["lex"], system["n"])
+    ref = system["OH"].V
+    assert np.max(np.abs(Vl - ref)) <= 1e-13 * np.max(np.abs(ref))
+    assert np.all(V[system["lex"] < 0] == 0)
+
+
+def test_spectral_bounds_match_oracle(kscf, system):
+    from oracle.chefsi import spectral_upper_bound
+    lo, hi = kscf.kscf_spectral_bounds(system["H"])
+    ref = spectral_upper_bound(system["OH"])
+    assert abs(hi - ref) <= 1e-12 * abs(ref)
+    assert lo <= system["OH"].V.min() + 1e-12
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 1e-5)])
+def test_apply_matches_oracle(kscf, system, dtype, tol):
+    from workloads import random_block_lex
+    k = 13
+    Y = random_block_lex(7, system["n"], k)
+    if dtype == torch.float32:
+        Y = Y.astype(np.float32).astype(np.float64)
+    Yd = dev(to_slots(Y, system["lex"]), dtype)
+    HYd = torch.full_like(Yd, 12345.0)
+    kscf.kscf_hamiltonian_apply(system["H"], Yd, HYd)
+    HY = HYd.double().cpu().numpy()
+    ref = system["OH"].apply(Y)
+    got = from_slots(HY, system["lex"], system["n"])
+    assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
+    assert np.all(HY[system["lex"] < 0] == 0)
+
+
+@pytest.mark.parametrize("dtype,tol,degree,block", [
+    (torch.float64, 1e-11, 10, 0), (torch.float64, 1e-11, 7, 5), (torch.float64, 1e-11, 1, 0),
+    (torch.float32, 1e-4, 10, 0), (torch.float32, 1e-4, 9, 8)])
+def test_filter_matches_oracle(kscf, system, dtype, tol, degree, block):
+    from oracle.chefsi import chebyshev_filter, spectral_upper_bound
+    from workloads import random_block_lex
+    k = 19
+    X = random_block_lex(3, system["n"], k)
+    if dtype == torch.float32:
+        X = X.astype(np.float32).astype(np.float64)
+    b = spectral_upper_bound(system["OH"])
+    a, a0 = -0.5, -9.0
+    Xd = dev(to_slots(X, system["lex"]), dtype)
+    kscf.kscf_chebyshev_filter(system["H"], Xd, degree, a, b, a0, block=block)
+    got = from_slots(Xd.double().cpu().numpy(), system["lex"], system["n"])
+    ref = chebyshev_filter(system["OH"], X, degree, a, b, a0)
+    colmax = np.max(np.abs(ref), axis=0)
+    assert np.all(np.max(np.abs(got - ref), axis=0) <= tol * colmax)
+
+
+def test_filter_strided_columns(kscf, system):
+    """X as a column slice of a wider array (ld > k): other columns untouched."""
+    from oracle.chefsi import chebyshev_filter, spectral_upper_bound
+    from workloads import random_block_lex
+    X = random_block_lex(5, system["n"], 6)
+    full = dev(to_slots(np.concatenate([X, np.ones((system["n"], 3))], 1), system["lex"]))
+    view = full[:, :6]
+    b = spectral_upper_bound(system["OH"])
+    kscf.kscf_chebyshev_filter(system["H"], view, 4, 0.0, b, -9.0, block=4)
+    got = full.cpu().numpy()
+    ref = chebyshev_filter(system["OH"], X, 4, 0.0, b, -9.0)
+    live = system["lex"] >= 0
+    assert np.allclose(got[live, 6:], 1.0)
+    g = from_slots(got[:, :6], system["lex"], system["n"])
+    assert np.max(np.abs(g - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+def test_orthonormalize_matches_oracle(kscf, system):
+    from oracle.chefsi import cholesky_qr
+    from workloads import random_block_lex
+    k = 24
+    X = random_block_lex(9, system["n"], k) + 0.5 * random_block_lex(10, system["n"], 1)
+    Xd = dev(to_slots(X, system["lex"]))
+    kscf.kscf_orthonormalize(system["H"], Xd)
+    got = from_slots(Xd.cpu().numpy(), system["lex"], system["n"])
+    ref, _ = cholesky_qr(X, system["OH"].h3)
+    assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
+    h3 = system["OH"].h3
+    assert np.max(np.abs(h3 * got.T @ got - np.eye(k))) < 1e-12
+
+
+def test_orthonormalize_f32_is_orthonormal(kscf, system):
+    from workloads import random_block_lex
+    k = 24
+    X = random_block_lex(9, system["n"], k)
+    Xd = dev(to_slots(X, system["lex"]), torch.float32)
+    kscf.kscf_orthonormalize(system["H"], Xd)
+    got = from_slots(Xd.double().cpu().numpy(), system["lex"], system["n"])
+    h3 = system["OH"].h3
+    assert np.max(np.abs(h3 * got.T @ got - np.eye(k))) < 2e-6
+    assert subspace_gap(got, X, h3) < 1e-5
+
+
+def test_rayleigh_ritz_matches_oracle(kscf, system):
+    from oracle.chefsi import cholesky_qr, rayleigh_ritz
+    from workloads import random_block_lex
+    k = 16
+    X, _ = cholesky_qr(random_block_lex(4, system["n"], k), system["OH"].h3)
+    Xd = dev(to_slots(X, system["lex"]))
+    lam = kscf.kscf_rayleigh_ritz(system["H"], Xd)
+    ref_lam, ref_X, _ = rayleigh_ritz(system["OH"], X, system["OH"].h3)
+    assert np.max(np.abs(lam - ref_lam)) <= 1e-11 * np.max(np.abs(ref_lam))
+    got = from_slots(Xd.cpu().numpy(), system["lex"], system["n"])
+    # eigenvectors up to sign (random subspace: simple Ritz values)
+    sgn = np.sign(np.sum(got * ref_X, axis=0))
+    assert np.max(np.abs(got * sgn - ref_X)) <= 1e-8 * np.max(np.abs(ref_X))
+
+
+def test_density_matches_oracle(kscf, system):
+    from oracle.chefsi import density
+    from workloads import random_block_lex
+    k, nocc = 11, 7
+    X = random_block_lex(12, system["n"], k)
+    occ = np.linspace(2.0, 0.5, nocc)
+    Xd = dev(to_slots(X, system["lex"]))
+    rho = kscf.kscf_density(system["H"], Xd, nocc, occ=dev(occ)).cpu().numpy()
+    ref = density(X, occ)
+    assert np.max(np.abs(from_slots(rho, system["lex"], system["n"]) - ref)) <= 1e-13 * ref.max()
+    rho2 = kscf.kscf_density(system["H"], Xd.float(), nocc).cpu().numpy()
+    ref2 = density(X.astype(np.float32).astype(np.float64), np.full(nocc, 2.0))
+    assert np.max(np.abs(from_slots(rho2, system["lex"], system["n"]) - ref2)) <= 1e-12 * ref2.max()
+
+
+def test_random_subspace_matches_generator(kscf, system):
+    from workloads import random_block_lex
+    k = 9
+    Xd = torch.full((system["g"].info["n_slots"], k + 2), 7.0, dtype=torch.float64, device="cuda")
+    kscf.kscf_random_subspace(system["H"], Xd[:, :k], seed=77)
+    got = Xd.cpu().numpy()
+    ref = random_block_lex(77, system["n"], k)
+    assert np.max(np.abs(from_slots(got[:, :k], system["lex"], system["n"]) - ref)) < 1e-13
+    assert np.all(got[system["lex"] < 0, :k] == 0) and np.all(got[:, k:] == 7.0)
+
+
+def test_chefsi_iterations_match_oracle(kscf, system):
+    from oracle.chefsi import chefsi, spectral_upper_bound
+    from workloads import random_block_lex
+    k, m, iters = 12, 8, 3
+    X0 = random_block_lex(1, system["n"], k)
+    Xd = dev(to_slots(X0, system["lex"]))
+    _, b = kscf.kscf_spectral_bounds(system["H"])
+    kscf.kscf_orthonormalize(system["H"], Xd)
+    lam = kscf.kscf_rayleigh_ritz(system["H"], Xd)
+    for _ in range(iters):
+        kscf.kscf_chebyshev_filter(system["H"], Xd, m, lam[-1], b, lam[0])
+        kscf.kscf_orthonormalize(system["H"], Xd)
+        lam = kscf.kscf_rayleigh_ritz(system["H"], Xd)
+    ref = chefsi(system["OH"], X0, m, iters, b=spectral_upper_bound(system["OH"]))
+    assert np.max(np.abs(lam - ref["lam"])) <= 1e-10 * np.max(np.abs(ref["lam"]))
+
+
+def test_error_paths(kscf, system):
+    H = system["H"]
+    X = torch.zeros((system["g"].info["n_slots"], 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(kscf.KscfError) as e:
+        kscf.kscf_chebyshev_filter(H, X, 4, 2.0, 1.0, 0.0)           # a >= b
+    assert e.value.code == kscf.KSCF_ERR_INVALID
+    with pytest.raises(kscf.KscfError) as e:
+        kscf.kscf_chebyshev_filter(H, X, 4, 1.0, 2.0, 0.0, work=torch.empty(64, dtype=torch.uint8, device="cuda"))
+    assert e.value.code == kscf.KSCF_ERR_WORKSPACE
+    # duplicated columns: rank-deficient Gram -> not SPD, X unchanged
+    from workloads import random_block_lex
+    col = random_block_lex(2, system["n"], 1)
+    Xd = dev(to_slots(np.concatenate([col, col, col * 2, col], 1), system["lex"]))
+    before = Xd.clone()
+    with pytest.raises(kscf.KscfError) as e:
+        kscf.kscf_orthonormalize(H, Xd)
+    assert e.value.code == kscf.KSCF_ERR_NOT_SPD
+    assert torch.equal(before, Xd)
+    with pytest.raises(kscf.KscfError) as e:
+        kscf.kscf_orthonormalize(H, X, mode=kscf.KSCF_GEMM_TENSOR)    # tensor mode needs F32
+    assert e.value.code == kscf.KSCF_ERR_UNSUPPORTED
