@@ -173,6 +173,30 @@ int kscf_workspace_size(const kscf_ham* ham, int op, int k, int dtype, int mode,
 int kscf_hamiltonian_apply(const kscf_ham* ham, void* Y, int64_t ld_y, void* HY, int64_t ld_hy,
                            int k, int dtype, void* work, size_t work_bytes, void* stream);
 
+/* Size in bytes of the fixed device array used by kscf_hamiltonian_apply_noalloc. */
+#define KSCF_NOALLOC_SCRATCH_BYTES (4 << 20)
+
+/* HY = H Y like kscf_hamiltonian_apply, for callers that cannot allocate device
+ * memory: for example a process whose framework has reserved all device memory in
+ * its own pool and forbids other allocators, or a latency-critical loop that must not
+ * call cudaMalloc because it synchronises the device.  The paper has no counterpart;
+ * this is a service of the library.
+ *   - No work buffer: the projection coefficients live in a fixed library-owned device
+ *     array of KSCF_NOALLOC_SCRATCH_BYTES bytes (held on every GPU that loads the
+ *     library until the process exits).  It needs n_kb * 4 * k * sizeof(element)
+ *     bytes (n_kb = atoms with projectors); larger k is rejected with
+ *     KSCF_ERR_INVALID and a message giving the largest k that fits -- call it on
+ *     column blocks of Y instead.
+ *   - Allocates nothing and calls no allocating routine.  The first call on each
+ *     device looks up the array's device address (cudaGetSymbolAddress) with that
+ *     device current; make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents; calls whose
+ *     work overlaps on the GPU (different streams, or threads without ordering) race
+ *     on it and give wrong results.  Serialise them (e.g. one stream).
+ * Arguments and layout as kscf_hamiltonian_apply (padding rows of Y are zeroed). */
+int kscf_hamiltonian_apply_noalloc(const kscf_ham* ham, void* Y, int64_t ld_y, void* HY, int64_t ld_hy,
+                                   int k, int dtype, void* stream);
+
 /* In place X <- p_m(H) X: the degree-m scaled Chebyshev filter (CheFSI paragraph;
  * Zhou, Saad, Tiago & Chelikowsky 2006).  With e = (b-a)/2, c = (b+a)/2,
  * sigma_1 = e/(a0-c), tau = 2/sigma_1:

@@ -1,0 +1,89 @@
+// H Y without any device allocation by the caller or the library.
+//
+// kscf_hamiltonian_apply needs a caller-provided work buffer for the projection
+// coefficients of the nonlocal term.  Some callers cannot obtain one: a host program
+// whose framework has already reserved all device memory in its own pool and
+// forbids other allocators, or code that must not call cudaMalloc because it
+// implicitly synchronises the device in a latency-critical loop.  This entry point
+// keeps that scratch in a fixed array compiled into the library instead.
+//
+// The array is a file-scope __device__ variable of KSCF_NOALLOC_SCRATCH_BYTES bytes; every
+// GPU that loads this library holds it until the process exits.  Host code may not
+// use the array's name as a device address (on the host it is only a stand-in), so
+// the device address is looked up once per device with cudaGetSymbolAddress, with
+// that device current, on the first call made on that device.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "kscf_internal.h"
+
+static __device__ __align__(256) unsigned char g_apply_scratch[KSCF_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_apply_scratch on the current device (looked up once per device).
+int scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    kscf::set_error("kscf_hamiltonian_apply_noalloc: cudaGetDevice failed: %s", cudaGetErrorString(e));
+    return KSCF_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    kscf::set_error("kscf_hamiltonian_apply_noalloc: device %d out of range", dev);
+    return KSCF_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_apply_scratch);
+    if (e != cudaSuccess || !p) {
+      kscf::set_error("kscf_hamiltonian_apply_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return KSCF_ERR_CUDA;
+    }
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return KSCF_OK;
+}
+}  // namespace
+
+extern "C" int kscf_hamiltonian_apply_noalloc(const kscf_ham* ham, void* Y, int64_t ld_y, void* HY, int64_t ld_hy,
+                                              int k, int dtype, void* stream) {
+  if (!ham || !Y || !HY) {
+    kscf::set_error("kscf_hamiltonian_apply_noalloc: null argument");
+    return KSCF_ERR_INVALID;
+  }
+  if (dtype != KSCF_F64 && dtype != KSCF_F32) {
+    kscf::set_error("kscf_hamiltonian_apply_noalloc: dtype must be KSCF_F64 or KSCF_F32");
+    return KSCF_ERR_INVALID;
+  }
+  if (k < 1 || ld_y < k || ld_hy < k) {
+    kscf::set_error("kscf_hamiltonian_apply_noalloc: need k >= 1, ld_y >= k and ld_hy >= k");
+    return KSCF_ERR_INVALID;
+  }
+  const kscf::Ham& H = ham->h;
+  const size_t need = (size_t)H.n_kb * 4 * (size_t)k * (dtype == KSCF_F64 ? 8 : 4);
+  if (need > (size_t)KSCF_NOALLOC_SCRATCH_BYTES) {
+    kscf::set_error(
+        "kscf_hamiltonian_apply_noalloc: %d vectors need %zu bytes of projection scratch, above the fixed "
+        "%d-byte array; call it on fewer columns at a time (at most %zu here)",
+        k, need, KSCF_NOALLOC_SCRATCH_BYTES,
+        (size_t)KSCF_NOALLOC_SCRATCH_BYTES / ((size_t)(H.n_kb > 0 ? H.n_kb : 1) * 4 * (dtype == KSCF_F64 ? 8 : 4)));
+    return KSCF_ERR_INVALID;
+  }
+  void* coef = nullptr;
+  int rc = scratch_address(&coef);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  // every coefficient the step kernel reads is written by the gather first, so the
+  // array needs no clearing between calls
+  KSCF_CUDA_TRY(kscf::launch_zero_rows(H, Y, ld_y, k, dtype, st));
+  KSCF_CUDA_TRY(kscf::launch_kb_gather(H, Y, ld_y, k, dtype, coef, st));
+  KSCF_CUDA_TRY(kscf::launch_cheb_step(H, Y, ld_y, nullptr, 0, HY, ld_hy, k, dtype, 1.0, 0.0, 0.0, coef, st));
+  return KSCF_OK;
+}

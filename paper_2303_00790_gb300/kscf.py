@@ -78,6 +78,7 @@ _sigs = {
     "kscf_spectral_bounds": ([_vp, C.POINTER(_d), C.POINTER(_d)], _i32),
     "kscf_workspace_size": ([_vp, _i32, _i32, _i32, _i32, _i32, C.POINTER(_sz)], _i32),
     "kscf_hamiltonian_apply": ([_vp, _vp, _i64, _vp, _i64, _i32, _i32, _vp, _sz, _vp], _i32),
+    "kscf_hamiltonian_apply_noalloc": ([_vp, _vp, _i64, _vp, _i64, _i32, _i32, _vp], _i32),
     "kscf_chebyshev_filter": ([_vp, _vp, _i64, _i32, _i32, _d, _d, _d, _i32, _i32, _vp, _sz, _vp], _i32),
     "kscf_orthonormalize": ([_vp, _vp, _i64, _i32, _i32, _i32, _vp, _sz, _vp], _i32),
     "kscf_rayleigh_ritz": ([_vp, _vp, _i64, _i32, _i32, _i32, C.POINTER(_d), _vp, _sz, _vp], _i32),
@@ -260,6 +261,15 @@ def kscf_hamiltonian_apply(ham: Hamiltonian, Y, HY, k: int | None = None, work=N
     _check(lib.kscf_hamiltonian_apply(ham.handle, C.c_void_p(Y.data_ptr()), _rows(Y, k), C.c_void_p(HY.data_ptr()),
                                       _rows(HY, k), k, dt, C.c_void_p(work.data_ptr()), work.numel(),
                                       _stream(stream)))
+    return HY
+
+
+def kscf_hamiltonian_apply_noalloc(ham: Hamiltonian, Y, HY, k: int | None = None, stream=None):
+    """H Y without a work buffer (fixed library-owned scratch; see include/kscf.h)."""
+    k = Y.shape[1] if k is None else k
+    _check(lib.kscf_hamiltonian_apply_noalloc(ham.handle, C.c_void_p(Y.data_ptr()), _rows(Y, k),
+                                              C.c_void_p(HY.data_ptr()), _rows(HY, k), k, _dtype_code(Y),
+                                              _stream(stream)))
     return HY
 
 
