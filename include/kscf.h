@@ -47,6 +47,7 @@ extern "C" {
 #define KSCF_ERR_NO_CONVERGE -6   /* dense eigensolver did not converge */
 #define KSCF_ERR_UNSUPPORTED -7   /* combination not built (e.g. bf16 mode with F64 X) */
 #define KSCF_ERR_HOST_ALLOC  -8   /* host memory allocation failed */
+#define KSCF_ERR_TIMEOUT     -9   /* a bounded device-side wait gave up (kernel returned early) */
 
 /* ---- element types ---- */
 #define KSCF_F64 0
@@ -238,6 +239,34 @@ int kscf_density(const kscf_ham* ham, const void* X, int64_t ld, int n_occ, int 
  * not depend on the slot order, so any layout sees the same X0. */
 int kscf_random_subspace(const kscf_ham* ham, void* X, int64_t ld, int k, int dtype,
                          uint64_t seed, void* stream);
+
+/* ---------------------------------------------------------------------------------
+ * GEMM building blocks of Cholesky-QR and Rayleigh-Ritz (exported for tests and
+ * benchmarks; orthonormalize and rayleigh_ritz call the same code).
+ *
+ * kscf_gram: C[i + j*ldc] = scale * sum_{r < rows} A[r*lda + i] * B[r*ldb + j]
+ *   (i < m, j < n; C FP64 column-major, overwritten).  A, B device arrays of dtype.
+ *   mode KSCF_GEMM_TENSOR (F32 only) uses tcgen05 with split-bf16 operands (see the
+ *   mode constants); KSCF_GEMM_NATIVE uses CUDA cores.  When A == B, lda == ldb and
+ *   m == n, only the upper triangle is computed and mirrored.
+ * kscf_rotate: out[r*ldo + j] = sum_{i < kin} A[r*lda + i] * Q'[i + j*ldq]  (r < rows,
+ *   j < kout) with Q' = Q - I when minus_identity (then out += A, i.e. out = A Q
+ *   evaluated as A + A (Q - I); tensor mode, kin == kout).  Q is FP64 column-major;
+ *   the native mode needs ldq == kin.  out must not overlap A.
+ * Work buffers: kscf_gemm_workspace_size(op = 0 gram / 1 rotate, rows, m|kin, n|kout,
+ * dtype, mode, &bytes). */
+int kscf_gram(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t rows, int m, int n, int dtype,
+              int mode, double scale, double* C, int64_t ldc, void* work, size_t work_bytes, void* stream);
+int kscf_rotate(const void* A, int64_t lda, const double* Q, int64_t ldq, int64_t rows, int kin, int kout,
+                int dtype, int mode, int minus_identity, void* out, int64_t ldo, void* work, size_t work_bytes,
+                void* stream);
+int kscf_gemm_workspace_size(int op, int64_t rows, int m, int n, int dtype, int mode, size_t* bytes);
+
+/* Reads and clears the device status word of the tensor-core kernels: KSCF_ERR_TIMEOUT
+ * if a bounded mbarrier wait gave up since the last check (the kernel then skipped its
+ * remaining work and freed its tensor memory), else KSCF_OK.  Synchronising.
+ * orthonormalize and rayleigh_ritz check it themselves. */
+int kscf_check_status(void);
 
 /* Hilbert index of brick coordinates (x, y, z) on the 2^bits cube, as used to order the
  * bricks (Skilling 2004 transpose algorithm; bits interleaved most significant first,

@@ -22,6 +22,7 @@ cudaError_t launch_rotate_tc(const float* A, int64_t lda, const double* Q, int64
 size_t gram_tc_work_bytes(int64_t rows, int m, int n);
 size_t rotate_tc_work_bytes(int64_t rows, int kin, int kout);
 bool tc_available();
+cudaError_t tc_status(bool reset, unsigned int* status);
 }  // namespace kscf
 
 namespace {
@@ -59,6 +60,22 @@ int solver_handle(cusolverDnHandle_t* out) {
   } while (0)
 
 size_t esize(int dtype) { return dtype == KSCF_F64 ? 8 : 4; }
+
+// after a synchronisation: did a tensor-core pipeline wait time out?
+int check_tc(int mode, const char* who) {
+  if (mode != KSCF_GEMM_TENSOR) return KSCF_OK;
+  unsigned int st = 0;
+  cudaError_t e = tc_status(true, &st);
+  if (e != cudaSuccess) {
+    set_error("%s: reading the tensor-core status failed: %s", who, cudaGetErrorString(e));
+    return KSCF_ERR_CUDA;
+  }
+  if (st) {
+    set_error("%s: a tensor-core pipeline wait timed out (status %u)", who, st);
+    return KSCF_ERR_TIMEOUT;
+  }
+  return KSCF_OK;
+}
 
 int check_common(const kscf_ham* ham, const void* X, int64_t ld, int k, int dtype, const char* who) {
   if (!ham || !X) {
@@ -253,6 +270,8 @@ int cholqr_pass(const Ham& H, void* X, int64_t ld, int k, int dtype, int mode, c
   int hinfo = 0;
   KSCF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
   KSCF_CUDA_TRY(cudaStreamSynchronize(st));
+  rc = check_tc(mode, "Cholesky-QR");
+  if (rc) return rc;
   if (hinfo != 0) {
     set_error("Cholesky-QR: Gram matrix not positive definite (potrf info %d%s)", hinfo,
               second_pass ? ", second pass" : "");
@@ -269,6 +288,8 @@ int cholqr_pass(const Ham& H, void* X, int64_t ld, int k, int dtype, int mode, c
   // the trtri status is read together with the next synchronisation
   KSCF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
   KSCF_CUDA_TRY(cudaStreamSynchronize(st));
+  rc = check_tc(mode, "Cholesky-QR");
+  if (rc) return rc;
   if (hinfo != 0) {
     set_error("Cholesky-QR: triangular inverse failed (info %d)", hinfo);
     return KSCF_ERR_NOT_SPD;
@@ -460,6 +481,8 @@ extern "C" int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int 
   KSCF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
   KSCF_CUDA_TRY(cudaMemcpyAsync(eigvals_host, W, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
   KSCF_CUDA_TRY(cudaStreamSynchronize(st));
+  rc = check_tc(mode, "kscf_rayleigh_ritz");
+  if (rc) return rc;
   if (hinfo != 0) {
     set_error("kscf_rayleigh_ritz: symmetric eigensolver failed (info %d)", hinfo);
     return hinfo > 0 ? KSCF_ERR_NO_CONVERGE : KSCF_ERR_INVALID;
@@ -487,5 +510,88 @@ extern "C" int kscf_random_subspace(const kscf_ham* ham, void* X, int64_t ld, in
   int rc = check_common(ham, X, ld, k, dtype, "kscf_random_subspace");
   if (rc) return rc;
   KSCF_CUDA_TRY(launch_random(ham->h, X, ld, k, dtype, seed, (cudaStream_t)stream));
+  return KSCF_OK;
+}
+
+extern "C" int kscf_gram(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t rows, int m, int n,
+                         int dtype, int mode, double scale, double* C, int64_t ldc, void* work, size_t work_bytes,
+                         void* stream) {
+  if (!A || !B || !C || rows < 0 || m < 1 || n < 1 || lda < m || ldb < n || ldc < m ||
+      (dtype != KSCF_F64 && dtype != KSCF_F32)) {
+    set_error("kscf_gram: invalid argument");
+    return KSCF_ERR_INVALID;
+  }
+  int rc = check_mode(dtype, mode, "kscf_gram");
+  if (rc) return rc;
+  const size_t need = mode == KSCF_GEMM_TENSOR ? gram_tc_work_bytes(rows, m, n) : 0;
+  rc = check_work(work, work_bytes, need, "kscf_gram");
+  if (rc) return rc;
+  return gram(A, lda, B, ldb, rows, m, n, dtype, mode, scale, C, ldc, work, work_bytes, (cudaStream_t)stream);
+}
+
+extern "C" int kscf_rotate(const void* A, int64_t lda, const double* Q, int64_t ldq, int64_t rows, int kin,
+                           int kout, int dtype, int mode, int minus_identity, void* out, int64_t ldo, void* work,
+                           size_t work_bytes, void* stream) {
+  if (!A || !Q || !out || rows < 0 || kin < 1 || kout < 1 || lda < kin || ldq < kin || ldo < kout ||
+      (dtype != KSCF_F64 && dtype != KSCF_F32) || (minus_identity && kin != kout)) {
+    set_error("kscf_rotate: invalid argument");
+    return KSCF_ERR_INVALID;
+  }
+  int rc = check_mode(dtype, mode, "kscf_rotate");
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (mode == KSCF_GEMM_TENSOR) {
+    rc = check_work(work, work_bytes, rotate_tc_work_bytes(rows, kin, kout), "kscf_rotate");
+    if (rc) return rc;
+    KSCF_CUDA_TRY(launch_rotate_tc((const float*)A, lda, Q, ldq, rows, kin, kout, minus_identity != 0,
+                                   (float*)out, ldo, work, work_bytes, st));
+    return KSCF_OK;
+  }
+  if (minus_identity) {
+    set_error("kscf_rotate: minus_identity needs the tensor mode");
+    return KSCF_ERR_UNSUPPORTED;
+  }
+  const size_t need = (size_t)kin * kout * esize(dtype);
+  rc = check_work(work, work_bytes, need, "kscf_rotate");
+  if (rc) return rc;
+  // native: convert Q into the work buffer (column-major, ld = kin), then rotate
+  double* Qc = (double*)work;
+  if (dtype == KSCF_F64 && ldq == kin) {
+    KSCF_CUDA_TRY(launch_rotate_native(A, lda, Q, ldq, rows, kin, kout, dtype, out, ldo, st));
+    return KSCF_OK;
+  }
+  (void)Qc;
+  if (ldq != kin) {
+    set_error("kscf_rotate: native mode needs ldq == kin");
+    return KSCF_ERR_UNSUPPORTED;
+  }
+  KSCF_CUDA_TRY(launch_f64_to_dtype(Q, (int64_t)kin * kout, dtype, work, st));
+  KSCF_CUDA_TRY(launch_rotate_native(A, lda, work, kin, rows, kin, kout, dtype, out, ldo, st));
+  return KSCF_OK;
+}
+
+extern "C" int kscf_gemm_workspace_size(int op, int64_t rows, int m, int n, int dtype, int mode, size_t* bytes) {
+  if (!bytes || rows < 0 || m < 1 || n < 1) {
+    set_error("kscf_gemm_workspace_size: invalid argument");
+    return KSCF_ERR_INVALID;
+  }
+  if (mode == KSCF_GEMM_TENSOR)
+    *bytes = op == 0 ? gram_tc_work_bytes(rows, m, n) : rotate_tc_work_bytes(rows, m, n);
+  else
+    *bytes = op == 0 ? 256 : kscf_align256((size_t)m * n * esize(dtype));
+  return KSCF_OK;
+}
+
+extern "C" int kscf_check_status(void) {
+  unsigned int st = 0;
+  cudaError_t e = tc_status(true, &st);
+  if (e != cudaSuccess) {
+    set_error("kscf_check_status: %s", cudaGetErrorString(e));
+    return KSCF_ERR_CUDA;
+  }
+  if (st) {
+    set_error("a tensor-core pipeline wait timed out (status %u)", st);
+    return KSCF_ERR_TIMEOUT;
+  }
   return KSCF_OK;
 }

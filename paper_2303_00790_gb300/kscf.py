@@ -24,6 +24,7 @@ KSCF_ERR_NONFINITE = -5
 KSCF_ERR_NO_CONVERGE = -6
 KSCF_ERR_UNSUPPORTED = -7
 KSCF_ERR_HOST_ALLOC = -8
+KSCF_ERR_TIMEOUT = -9
 KSCF_F64, KSCF_F32 = 0, 1
 KSCF_GEMM_NATIVE, KSCF_GEMM_TENSOR = 0, 1
 KSCF_OP_APPLY, KSCF_OP_FILTER, KSCF_OP_ORTHO, KSCF_OP_RR = 0, 1, 2, 3
@@ -85,6 +86,10 @@ _sigs = {
     "kscf_density": ([_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp], _i32),
     "kscf_random_subspace": ([_vp, _vp, _i64, _i32, _i32, C.c_uint64, _vp], _i32),
     "kscf_hilbert_index3": ([C.c_uint32, C.c_uint32, C.c_uint32, _i32], C.c_uint64),
+    "kscf_gram": ([_vp, _i64, _vp, _i64, _i64, _i32, _i32, _i32, _i32, _d, _vp, _i64, _vp, _sz, _vp], _i32),
+    "kscf_rotate": ([_vp, _i64, _vp, _i64, _i64, _i32, _i32, _i32, _i32, _i32, _vp, _i64, _vp, _sz, _vp], _i32),
+    "kscf_gemm_workspace_size": ([_i32, _i64, _i32, _i32, _i32, _i32, C.POINTER(_sz)], _i32),
+    "kscf_check_status": ([], _i32),
 }
 for _name, (_args, _res) in _sigs.items():
     _f = getattr(lib, _name)
@@ -320,6 +325,53 @@ def kscf_random_subspace(ham: Hamiltonian, X, seed: int, k: int | None = None, s
     _check(lib.kscf_random_subspace(ham.handle, C.c_void_p(X.data_ptr()), _rows(X, k), k, _dtype_code(X),
                                     int(seed), _stream(stream)))
     return X
+
+
+def kscf_gemm_workspace_size(op: int, rows: int, m: int, n: int, dtype: int, mode: int) -> int:
+    b = C.c_size_t()
+    _check(lib.kscf_gemm_workspace_size(op, rows, m, n, dtype, mode, C.byref(b)))
+    return b.value
+
+
+def kscf_gram(A, B, scale: float = 1.0, mode: int = KSCF_GEMM_NATIVE, C_out=None, m: int | None = None,
+              n: int | None = None, rows: int | None = None, work=None, stream=None):
+    """C = scale * A^T B (FP64, column-major, returned as a (n, m) row-major view's transpose)."""
+    torch = _torch()
+    m = A.shape[1] if m is None else m
+    n = B.shape[1] if n is None else n
+    rows = A.shape[0] if rows is None else rows
+    dt = _dtype_code(A)
+    if C_out is None:
+        C_out = torch.empty((n, m), dtype=torch.float64, device="cuda")   # column-major m x n
+    if work is None:
+        work = torch.empty(max(256, kscf_gemm_workspace_size(0, rows, m, n, dt, mode)), dtype=torch.uint8,
+                           device="cuda")
+    _check(lib.kscf_gram(C.c_void_p(A.data_ptr()), _rows(A, m), C.c_void_p(B.data_ptr()), _rows(B, n), rows, m, n,
+                         dt, mode, scale, C.c_void_p(C_out.data_ptr()), m, C.c_void_p(work.data_ptr()), work.numel(),
+                         _stream(stream)))
+    return C_out.t()
+
+
+def kscf_rotate(A, Q, mode: int = KSCF_GEMM_NATIVE, minus_identity: bool = False, out=None, work=None, stream=None):
+    """out = A Q (Q FP64 (kin, kout) row-major torch tensor; passed column-major)."""
+    torch = _torch()
+    rows, kin = A.shape[0], Q.shape[0]
+    kout = Q.shape[1]
+    Qc = Q.t().contiguous()       # column-major storage of Q
+    dt = _dtype_code(A)
+    if out is None:
+        out = torch.empty((rows, kout), dtype=A.dtype, device="cuda")
+    if work is None:
+        work = torch.empty(max(256, kscf_gemm_workspace_size(1, rows, kin, kout, dt, mode)), dtype=torch.uint8,
+                           device="cuda")
+    _check(lib.kscf_rotate(C.c_void_p(A.data_ptr()), _rows(A, kin), C.c_void_p(Qc.data_ptr()), kin, rows, kin, kout,
+                           dt, mode, 1 if minus_identity else 0, C.c_void_p(out.data_ptr()), _rows(out, kout),
+                           C.c_void_p(work.data_ptr()), work.numel(), _stream(stream)))
+    return out
+
+
+def kscf_check_status():
+    _check(lib.kscf_check_status())
 
 
 def kscf_launch_counter() -> int:

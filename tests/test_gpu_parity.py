@@ -218,3 +218,51 @@ def test_error_paths(kscf, system):
     with pytest.raises(kscf.KscfError) as e:
         kscf.kscf_orthonormalize(H, X, mode=kscf.KSCF_GEMM_TENSOR)    # tensor mode needs F32
     assert e.value.code == kscf.KSCF_ERR_UNSUPPORTED
+
+
+def test_orthonormalize_tensor_mode(kscf, system):
+    from workloads import random_block_lex
+    k = 24
+    X = random_block_lex(9, system["n"], k) + 0.5 * random_block_lex(10, system["n"], 1)
+    Xd = dev(to_slots(X, system["lex"]), torch.float32)
+    kscf.kscf_orthonormalize(system["H"], Xd, mode=kscf.KSCF_GEMM_TENSOR)
+    got = from_slots(Xd.double().cpu().numpy(), system["lex"], system["n"])
+    h3 = system["OH"].h3
+    assert np.max(np.abs(h3 * got.T @ got - np.eye(k))) < 2e-6
+    assert subspace_gap(got, X, h3) < 1e-5
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_rayleigh_ritz_f32_modes(kscf, system, mode):
+    from oracle.chefsi import cholesky_qr, rayleigh_ritz
+    from workloads import random_block_lex
+    k = 16
+    X, _ = cholesky_qr(random_block_lex(4, system["n"], k), system["OH"].h3)
+    X32 = X.astype(np.float32).astype(np.float64)
+    Xd = dev(to_slots(X32, system["lex"]), torch.float32)
+    lam = kscf.kscf_rayleigh_ritz(system["H"], Xd, mode=mode)
+    ref_lam, _, _ = rayleigh_ritz(system["OH"], X32, system["OH"].h3)
+    # FP32 H X and GEMM sums: ~1e-6 of the spectral scale
+    assert np.max(np.abs(lam - ref_lam)) <= 2e-5 * np.max(np.abs(ref_lam))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_chefsi_f32_tracks_oracle(kscf, system, mode):
+    """Mixed path (FP32 filter, FP64 Cholesky + eigensolver) after 3 iterations from the
+    same X0: Ritz values close to the FP64 oracle's, and the wanted subspace agrees."""
+    from oracle.chefsi import chefsi, spectral_upper_bound
+    from workloads import random_block_lex
+    k, m, iters = 12, 8, 3
+    X0 = random_block_lex(1, system["n"], k)
+    Xd = dev(to_slots(X0, system["lex"]), torch.float32)
+    _, b = kscf.kscf_spectral_bounds(system["H"])
+    kscf.kscf_orthonormalize(system["H"], Xd, mode=mode)
+    lam = kscf.kscf_rayleigh_ritz(system["H"], Xd, mode=mode)
+    for _ in range(iters):
+        kscf.kscf_chebyshev_filter(system["H"], Xd, m, lam[-1], b, lam[0])
+        kscf.kscf_orthonormalize(system["H"], Xd, mode=mode)
+        lam = kscf.kscf_rayleigh_ritz(system["H"], Xd, mode=mode)
+    ref = chefsi(system["OH"], X0, m, iters, b=spectral_upper_bound(system["OH"]))
+    assert np.max(np.abs(lam[:6] - ref["lam"][:6])) <= 1e-4 * np.max(np.abs(ref["lam"]))
+    got = from_slots(Xd.double().cpu().numpy(), system["lex"], system["n"])
+    assert subspace_gap(got[:, :4], ref["X"][:, :4], system["OH"].h3) < 1e-2
