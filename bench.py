@@ -206,7 +206,7 @@ def run_kscf(args):
     world, rank, local = setup_dist(args)
     assert torch.cuda.is_available(), "the kscf arm needs a CUDA device"
     w = workload(args.workload)
-    block = args.block or min(w.block, 128)
+    block = args.block or w.block
     mode = {"auto": kscf.KSCF_GEMM_NATIVE, "native": kscf.KSCF_GEMM_NATIVE, "tensor": kscf.KSCF_GEMM_TENSOR}[args.mode]
     pos, z = w.atoms()
     species = pseudo_params()
@@ -215,7 +215,11 @@ def run_kscf(args):
     k, m = w.k, w.degree
     nocc = n_occupied(z)
     dt = torch.float32
-    X = torch.empty((n_slots, k), dtype=dt, device="cuda")
+    # row stride padded to a multiple of 8 floats: every column block of the filter can
+    # use the staged brick kernel
+    kpad = (k + 7) // 8 * 8
+    Xfull = torch.zeros((n_slots, kpad), dtype=dt, device="cuda")
+    X = Xfull[:, :k]
     kscf.kscf_random_subspace(H, X, seed=1 + rank)
     rho = torch.empty(n_slots, dtype=torch.float64, device="cuda")
     lo, b = kscf.kscf_spectral_bounds(H)
@@ -289,9 +293,9 @@ def run_kscf(args):
     # end-to-end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
-        Xh = torch.empty((n_slots, k), dtype=dt, pin_memory=True)
-        Xh.copy_(X)
-        outh = torch.empty((n_slots, k), dtype=dt, pin_memory=True)
+        Xh = torch.empty((n_slots, kpad), dtype=dt, pin_memory=True)
+        Xh.copy_(Xfull)
+        outh = torch.empty((n_slots, kpad), dtype=dt, pin_memory=True)
         torch.cuda.synchronize()
         barrier(world)
         s0 = torch.cuda.Event(enable_timing=True)
@@ -299,9 +303,9 @@ def run_kscf(args):
         s0.record(stream)
         nE = max(1, min(args.steps, 3))
         for _ in range(nE):
-            X.copy_(Xh, non_blocking=True)
+            Xfull.copy_(Xh, non_blocking=True)
             step(False)
-            outh.copy_(X, non_blocking=True)
+            outh.copy_(Xfull, non_blocking=True)
         s1.record(stream)
         torch.cuda.synchronize()
         e_ms = max_over_ranks(s0.elapsed_time(s1) / nE, world)

@@ -67,13 +67,13 @@ extern "C" int kscf_hamiltonian_apply_noalloc(const kscf_ham* ham, void* Y, int6
     return KSCF_ERR_INVALID;
   }
   const kscf::Ham& H = ham->h;
-  const size_t need = (size_t)H.n_kb * 4 * (size_t)k * (dtype == KSCF_F64 ? 8 : 4);
+  const size_t need = (size_t)H.n_kb * 4 * (size_t)kscf::coef_ld(k) * (dtype == KSCF_F64 ? 8 : 4);
   if (need > (size_t)KSCF_NOALLOC_SCRATCH_BYTES) {
     kscf::set_error(
         "kscf_hamiltonian_apply_noalloc: %d vectors need %zu bytes of projection scratch, above the fixed "
         "%d-byte array; call it on fewer columns at a time (at most %zu here)",
         k, need, KSCF_NOALLOC_SCRATCH_BYTES,
-        (size_t)KSCF_NOALLOC_SCRATCH_BYTES / ((size_t)(H.n_kb > 0 ? H.n_kb : 1) * 4 * (dtype == KSCF_F64 ? 8 : 4)));
+        (size_t)KSCF_NOALLOC_SCRATCH_BYTES / ((size_t)(H.n_kb > 0 ? H.n_kb : 1) * 4 * (dtype == KSCF_F64 ? 8 : 4)) / 8 * 8);
     return KSCF_ERR_INVALID;
   }
   void* coef = nullptr;
@@ -83,7 +83,8 @@ extern "C" int kscf_hamiltonian_apply_noalloc(const kscf_ham* ham, void* Y, int6
   // every coefficient the step kernel reads is written by the gather first, so the
   // array needs no clearing between calls
   KSCF_CUDA_TRY(kscf::launch_zero_rows(H, Y, ld_y, k, dtype, st));
-  KSCF_CUDA_TRY(kscf::launch_kb_gather(H, Y, ld_y, k, dtype, coef, st));
-  KSCF_CUDA_TRY(kscf::launch_cheb_step(H, Y, ld_y, nullptr, 0, HY, ld_hy, k, dtype, 1.0, 0.0, 0.0, coef, st));
+  KSCF_CUDA_TRY(kscf::launch_kb_gather(H, Y, ld_y, k, dtype, coef, kscf::coef_ld(k), st));
+  KSCF_CUDA_TRY(kscf::launch_cheb_step(H, Y, ld_y, nullptr, 0, HY, ld_hy, k, (int)(ld_y < ld_hy ? ld_y : ld_hy), dtype,
+                                       1.0, 0.0, 0.0, coef, kscf::coef_ld(k), st));
   return KSCF_OK;
 }

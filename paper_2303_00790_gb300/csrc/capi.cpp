@@ -162,8 +162,8 @@ int rr_plan(const Ham& H, int k, int dtype, int mode, int block, RRPlan* p) {
   SOLVER_TRY(cusolverDnDsyevd_bufferSize(hs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, k, nullptr, k,
                                          nullptr, &lw));
   p->w = block_width(k, block);
-  p->hxb = (size_t)H.grid.n_slots * p->w * esize(dtype);
-  p->coef = (size_t)std::max(H.n_kb, 1) * 4 * p->w * esize(dtype);
+  p->hxb = (size_t)H.grid.n_slots * coef_ld(p->w) * esize(dtype);
+  p->coef = (size_t)std::max(H.n_kb, 1) * 4 * coef_ld(p->w) * esize(dtype);
   p->Hs = (size_t)k * k * 8;
   p->W = (size_t)k * 8;
   p->Q = (size_t)k * k * esize(dtype);
@@ -185,12 +185,12 @@ size_t rr_bytes(const RRPlan& p) {
 
 size_t filter_bytes(const Ham& H, int k, int dtype, int block) {
   const int w = block_width(k, block);
-  return kscf_align256((size_t)H.grid.n_slots * w * esize(dtype)) +
-         kscf_align256((size_t)std::max(H.n_kb, 1) * 4 * w * esize(dtype));
+  return kscf_align256((size_t)H.grid.n_slots * coef_ld(w) * esize(dtype)) +
+         kscf_align256((size_t)std::max(H.n_kb, 1) * 4 * coef_ld(w) * esize(dtype));
 }
 
 size_t apply_bytes(const Ham& H, int k, int dtype) {
-  return kscf_align256((size_t)std::max(H.n_kb, 1) * 4 * k * esize(dtype));
+  return kscf_align256((size_t)std::max(H.n_kb, 1) * 4 * coef_ld(k) * esize(dtype));
 }
 
 int check_work(void* work, size_t have, size_t need, const char* who) {
@@ -349,8 +349,9 @@ extern "C" int kscf_hamiltonian_apply(const kscf_ham* ham, void* Y, int64_t ld_y
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   KSCF_CUDA_TRY(launch_zero_rows(H, Y, ld_y, k, dtype, st));
-  KSCF_CUDA_TRY(launch_kb_gather(H, Y, ld_y, k, dtype, work, st));
-  KSCF_CUDA_TRY(launch_cheb_step(H, Y, ld_y, nullptr, 0, HY, ld_hy, k, dtype, 1.0, 0.0, 0.0, work, st));
+  KSCF_CUDA_TRY(launch_kb_gather(H, Y, ld_y, k, dtype, work, coef_ld(k), st));
+  KSCF_CUDA_TRY(launch_cheb_step(H, Y, ld_y, nullptr, 0, HY, ld_hy, k, (int)std::min<int64_t>(ld_y, ld_hy), dtype,
+                                 1.0, 0.0, 0.0, work, coef_ld(k), st));
   return KSCF_OK;
 }
 
@@ -370,28 +371,33 @@ extern "C" int kscf_chebyshev_filter(const kscf_ham* ham, void* X, int64_t ld, i
   const int w = block_width(k, block);
   const size_t es = esize(dtype);
   Carver cv(work);
-  void* buf = cv.take((size_t)H.grid.n_slots * w * es);
-  void* coef = cv.take((size_t)std::max(H.n_kb, 1) * 4 * w * es);
+  const int64_t wpad = coef_ld(w);
+  void* buf = cv.take((size_t)H.grid.n_slots * wpad * es);
+  void* coef = cv.take((size_t)std::max(H.n_kb, 1) * 4 * wpad * es);
   const double e = (b - a) / 2.0, c = (b + a) / 2.0;
   const double sigma1 = e / (a0 - c), tau = 2.0 / sigma1;
   KSCF_CUDA_TRY(launch_zero_rows(H, X, ld, k, dtype, st));
   for (int c0 = 0; c0 < k; c0 += w) {
     const int wb = std::min(w, k - c0);
     char* Xb = (char*)X + (size_t)c0 * es;
+    // columns usable from the block start in every row (lets the FP32 brick kernel read
+    // whole 8-vector chunks when the row has room)
+    const int avail_x = (int)std::min<int64_t>(ld - c0, 1 << 30), avail_b = (int)wpad;
     // Y_1 = (sigma_1/e)(H X - c X)   -> buf
-    KSCF_CUDA_TRY(launch_kb_gather(H, Xb, ld, wb, dtype, coef, st));
-    KSCF_CUDA_TRY(launch_cheb_step(H, Xb, ld, nullptr, 0, buf, wb, wb, dtype, sigma1 / e, 0.0, c, coef, st));
+    KSCF_CUDA_TRY(launch_kb_gather(H, Xb, ld, wb, dtype, coef, wpad, st));
+    KSCF_CUDA_TRY(launch_cheb_step(H, Xb, ld, nullptr, 0, buf, wpad, wb, std::min(avail_x, avail_b), dtype,
+                                   sigma1 / e, 0.0, c, coef, wpad, st));
     void* cur = buf;
-    int64_t ld_cur = wb;
+    int64_t ld_cur = wpad;
     void* prv = Xb;
     int64_t ld_prv = ld;
     double sigma = sigma1;
     for (int j = 2; j <= degree; j++) {
       const double sigma_new = 1.0 / (tau - sigma);
-      KSCF_CUDA_TRY(launch_kb_gather(H, cur, ld_cur, wb, dtype, coef, st));
+      KSCF_CUDA_TRY(launch_kb_gather(H, cur, ld_cur, wb, dtype, coef, wpad, st));
       // Y_j overwrites Y_{j-2} in place (each element is read before it is written)
-      KSCF_CUDA_TRY(launch_cheb_step(H, cur, ld_cur, prv, ld_prv, prv, ld_prv, wb, dtype, 2.0 * sigma_new / e,
-                                     -sigma * sigma_new, c, coef, st));
+      KSCF_CUDA_TRY(launch_cheb_step(H, cur, ld_cur, prv, ld_prv, prv, ld_prv, wb, std::min(avail_x, avail_b), dtype,
+                                     2.0 * sigma_new / e, -sigma * sigma_new, c, coef, wpad, st));
       std::swap(cur, prv);
       std::swap(ld_cur, ld_prv);
       sigma = sigma_new;
@@ -467,10 +473,12 @@ extern "C" int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int 
   for (int c0 = 0; c0 < k; c0 += p.w) {
     const int wb = std::min(p.w, k - c0);
     char* Xb = (char*)X + (size_t)c0 * es;
-    KSCF_CUDA_TRY(launch_kb_gather(H, Xb, ld, wb, dtype, coef, st));
-    KSCF_CUDA_TRY(launch_cheb_step(H, Xb, ld, nullptr, 0, hxb, wb, wb, dtype, 1.0, 0.0, 0.0, coef, st));
+    const int64_t wpad = coef_ld(wb);
+    KSCF_CUDA_TRY(launch_kb_gather(H, Xb, ld, wb, dtype, coef, wpad, st));
+    KSCF_CUDA_TRY(launch_cheb_step(H, Xb, ld, nullptr, 0, hxb, wpad, wb,
+                                   (int)std::min<int64_t>(ld - c0, wpad), dtype, 1.0, 0.0, 0.0, coef, wpad, st));
     // Hs[:, c0:c0+wb] = h^3 X^T (H X_b)
-    rc = gram(X, ld, hxb, wb, rows, k, wb, dtype, mode, h3, Hs + (size_t)c0 * k, k, tcw, p.tc, st);
+    rc = gram(X, ld, hxb, wpad, rows, k, wb, dtype, mode, h3, Hs + (size_t)c0 * k, k, tcw, p.tc, st);
     if (rc) return rc;
   }
   KSCF_CUDA_TRY(launch_symmetrize(Hs, k, k, st));

@@ -34,7 +34,7 @@ static void free_ham(Ham& H) {
   void* ptrs[] = {H.d_nbr,           H.d_mask,         H.d_lex,          H.d_pad,
                   H.d_v64,           H.d_v32,          H.d_kb_atom_ptr,  H.d_kb_atom_slot,
                   H.d_kb_atom_chi64, H.d_kb_atom_chi32, H.d_kb_slot_ptr, H.d_kb_slot_atom,
-                  H.d_kb_slot_chi64, H.d_kb_slot_chi32, H.d_kb_energy};
+                  H.d_kb_slot_chi64, H.d_kb_slot_chi32, H.d_kb_energy, H.d_kb_entry_lslot};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -282,6 +282,14 @@ extern "C" int kscf_build_hamiltonian(const kscf_grid* grid, const kscf_atom* at
     if (e == cudaSuccess) e = upload(&H.d_kb_slot_chi64, s_chi.data(), s_chi.size());
     if (e == cudaSuccess) e = upload(&H.d_kb_slot_chi32, s_chi32.data(), s_chi32.size());
     if (e == cudaSuccess) e = upload(&H.d_kb_energy, energy.data(), energy.size());
+    {
+      // entry (slot order) -> slot index inside its brick
+      const int64_t b3 = (int64_t)g.B * g.B * g.B;
+      std::vector<uint16_t> lslot(ne);
+      for (int64_t s2 = 0; s2 < g.n_slots; s2++)
+        for (int64_t q = s_ptr[s2]; q < s_ptr[s2 + 1]; q++) lslot[q] = (uint16_t)(s2 % b3);
+      if (e == cudaSuccess) e = upload(&H.d_kb_entry_lslot, lslot.data(), lslot.size());
+    }
     if (e != cudaSuccess) {
       set_error("kscf_build_hamiltonian: KB upload failed: %s", cudaGetErrorString(e));
       rc = KSCF_ERR_CUDA;

@@ -74,6 +74,7 @@ struct Ham {
   int32_t* d_kb_slot_atom = nullptr;  // entry -> kb atom
   double* d_kb_slot_chi64 = nullptr;  // entry*4
   float* d_kb_slot_chi32 = nullptr;
+  uint16_t* d_kb_entry_lslot = nullptr;  // entry -> slot index inside its brick (slot order)
   double* d_kb_energy = nullptr;      // n_kb*4: E_l * h^3
   double kb_upper = 0.0, kb_lower = 0.0;  // Gershgorin bounds of V_NL
   int max_slot_entries = 0;
@@ -81,11 +82,16 @@ struct Ham {
 
 // ---- launchers (filter.cu) ----
 cudaError_t launch_zero_rows(const Ham& H, void* X, int64_t ld, int k, int dtype, cudaStream_t st);
+// coef rows have stride cld (>= w); round_up8(w) lets the FP32 brick kernel read lane pairs
 cudaError_t launch_kb_gather(const Ham& H, const void* Y, int64_t ld, int w, int dtype, void* coef,
-                             cudaStream_t st);
+                             int64_t cld, cudaStream_t st);
+// wavail: columns readable and writable from in/prev/out in every row (>= w); the FP32
+// brick kernel is used when wavail and cld cover round_up8(w)
 cudaError_t launch_cheb_step(const Ham& H, const void* in, int64_t ld_in, const void* prev,
-                             int64_t ld_prev, void* out, int64_t ld_out, int w, int dtype,
-                             double alpha, double beta, double c, const void* coef, cudaStream_t st);
+                             int64_t ld_prev, void* out, int64_t ld_out, int w, int wavail, int dtype,
+                             double alpha, double beta, double c, const void* coef, int64_t cld,
+                             cudaStream_t st);
+inline int64_t coef_ld(int w) { return (int64_t)(w + 7) / 8 * 8; }
 cudaError_t launch_copy_cols(const void* src, int64_t ld_src, void* dst, int64_t ld_dst, int64_t rows,
                              int w, int dtype, cudaStream_t st);
 

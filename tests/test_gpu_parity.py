@@ -266,3 +266,29 @@ def test_chefsi_f32_tracks_oracle(kscf, system, mode):
     assert np.max(np.abs(lam[:6] - ref["lam"][:6])) <= 1e-4 * np.max(np.abs(ref["lam"]))
     got = from_slots(Xd.double().cpu().numpy(), system["lex"], system["n"])
     assert subspace_gap(got[:, :4], ref["X"][:, :4], system["OH"].h3) < 1e-2
+
+
+@pytest.mark.parametrize("k,ldpad,block", [(13, 16, 0), (19, 24, 0), (19, 24, 8), (32, 32, 16)])
+def test_f32_brick_kernel_paths(kscf, system, k, ldpad, block):
+    """Row strides padded to a multiple of 8 select the staged FP32 brick kernel (brick
+    8); compared with the oracle like the generic path."""
+    if system["brick"] != 8:
+        pytest.skip("the staged kernel is built for 8^3 bricks")
+    from oracle.chefsi import chebyshev_filter, spectral_upper_bound
+    from workloads import random_block_lex
+    X = random_block_lex(31, system["n"], k).astype(np.float32).astype(np.float64)
+    full = torch.zeros((system["g"].info["n_slots"], ldpad), dtype=torch.float32, device="cuda")
+    full[:, :k] = dev(to_slots(X, system["lex"]), torch.float32)
+    Y = full[:, :k]
+    HYf = torch.full_like(full, 7.0)
+    kscf.kscf_hamiltonian_apply(system["H"], Y, HYf[:, :k])
+    got = from_slots(HYf[:, :k].double().cpu().numpy(), system["lex"], system["n"])
+    ref = system["OH"].apply(X)
+    assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
+    assert torch.all(HYf[:, k:] == 7.0)
+    b = spectral_upper_bound(system["OH"])
+    kscf.kscf_chebyshev_filter(system["H"], Y, 10, -0.5, b, -9.0, block=block)
+    got = from_slots(full[:, :k].double().cpu().numpy(), system["lex"], system["n"])
+    ref = chebyshev_filter(system["OH"], X, 10, -0.5, b, -9.0)
+    colmax = np.max(np.abs(ref), axis=0)
+    assert np.all(np.max(np.abs(got - ref), axis=0) <= 1e-4 * colmax)
