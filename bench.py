@@ -215,9 +215,9 @@ def run_kscf(args):
     k, m = w.k, w.degree
     nocc = n_occupied(z)
     dt = torch.float32
-    # row stride padded to a multiple of 8 floats: every column block of the filter can
-    # use the staged brick kernel
-    kpad = (k + 7) // 8 * 8
+    # row stride padded to a multiple of 32 floats: every column block of the filter can
+    # use the 32-vector brick kernel
+    kpad = (k + 31) // 32 * 32
     Xfull = torch.zeros((n_slots, kpad), dtype=dt, device="cuda")
     X = Xfull[:, :k]
     kscf.kscf_random_subspace(H, X, seed=1 + rank)

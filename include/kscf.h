@@ -22,6 +22,9 @@
  *     Rows of slots outside the domain (padding of boundary bricks) are zero on
  *     output; the library zeroes them on input where a stencil reads them.
  *   - dtype: KSCF_F64 (double) or KSCF_F32 (float) for X and the filter arithmetic.
+ *     For F32 X a row stride ld that is a multiple of 32 (16-byte aligned rows) lets
+ *     every column block of the filter run on the fastest (32-vector brick) kernel; any
+ *     ld >= k is accepted.
  *   - Inner products use the grid weight h^3: <u, v> = h^3 sum_s u_s v_s.
  *   - Device work buffers must be at least the size kscf_workspace_size() reports for
  *     the same (op, k, dtype, mode, block); a smaller buffer gives KSCF_ERR_WORKSPACE

@@ -73,7 +73,7 @@ extern "C" int kscf_hamiltonian_apply_noalloc(const kscf_ham* ham, void* Y, int6
         "kscf_hamiltonian_apply_noalloc: %d vectors need %zu bytes of projection scratch, above the fixed "
         "%d-byte array; call it on fewer columns at a time (at most %zu here)",
         k, need, KSCF_NOALLOC_SCRATCH_BYTES,
-        (size_t)KSCF_NOALLOC_SCRATCH_BYTES / ((size_t)(H.n_kb > 0 ? H.n_kb : 1) * 4 * (dtype == KSCF_F64 ? 8 : 4)) / 8 * 8);
+        (size_t)KSCF_NOALLOC_SCRATCH_BYTES / ((size_t)(H.n_kb > 0 ? H.n_kb : 1) * 4 * (dtype == KSCF_F64 ? 8 : 4)) / 32 * 32);
     return KSCF_ERR_INVALID;
   }
   void* coef = nullptr;

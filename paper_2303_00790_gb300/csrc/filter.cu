@@ -142,28 +142,36 @@ __device__ __forceinline__ float2 ld2(const float* base, int64_t slot, int64_t l
 }
 }  // namespace
 
-// VEC: rows are read with vector loads (ld and column offsets even / multiples of 4)
-template <bool VEC>
-__global__ void __launch_bounds__(256, 3) cheb_step_brick8(StepArgs<float> a, int nchunk,
-                                                            const uint16_t* __restrict__ entry_lslot) {
+// NV vectors per CTA (8 or 32): a point slot in shared memory is NV floats; the 64
+// lines of a pass are spread over 64 * NV/2 threads, NV/2 lanes per line, two vectors
+// per lane.  NV = 32 makes every halo load instruction cover two 128-byte row segments.
+// VEC: rows are read with vector loads (ld and column offsets multiples of 4).
+template <int NV, bool VEC>
+__global__ void __launch_bounds__(NV * 32, NV == 8 ? 3 : 1)
+    cheb_step_brick8(StepArgs<float> a, int nchunk, const uint16_t* __restrict__ entry_lslot) {
+  constexpr int VPL = NV / 2;       // lanes per line
+  constexpr int NT = 64 * VPL;      // threads
+  constexpr int Q4 = NV / 4;        // float4 per point slot
   const int64_t cld = a.cld;
   extern __shared__ float4 sb4[];
   float* sm = (float*)sb4;
   const int brick = blockIdx.x / nchunk, chunk = blockIdx.x - (blockIdx.x / nchunk) * nchunk;
-  const int v0 = chunk * 8;
+  const int v0 = chunk * NV;
   const int tid = threadIdx.x;
-  const int vp = tid & 3, line = tid >> 2;
+  const int vp = tid % VPL, line = tid / VPL;
   const int vl = v0 + 2 * vp;  // this lane's first vector
   const int64_t b0 = (int64_t)brick * 512;
   const int nbx0 = __ldg(a.nbr + (int64_t)brick * 6 + 0), nbx1 = __ldg(a.nbr + (int64_t)brick * 6 + 1);
   const int nby0 = __ldg(a.nbr + (int64_t)brick * 6 + 2), nby1 = __ldg(a.nbr + (int64_t)brick * 6 + 3);
   const int nbz0 = __ldg(a.nbr + (int64_t)brick * 6 + 4), nbz1 = __ldg(a.nbr + (int64_t)brick * 6 + 5);
+  // point slot of (x, y, z): XOR swizzle for 32-byte slots, plain for 128-byte slots
+  auto core = [](int x, int y, int z) { return NV == 8 ? sb_core(x, y, z) : (z * 8 + y) * 8 + x; };
 
-  // ---- stage the brick core: 512 rows x 32 B ----
-  for (int t = tid; t < 1024; t += 256) {
-    const int r = t >> 1, half = t & 1;
-    const float* p = a.in + (b0 + r) * a.ld_in + v0 + half * 4;
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(&sb4[(SB_CORE + sb_core(r & 7, (r >> 3) & 7, r >> 6)) * 2 + half]);
+  // ---- stage the brick core: 512 rows x NV floats ----
+  for (int t = tid; t < 512 * Q4; t += NT) {
+    const int r = t / Q4, part = t - (t / Q4) * Q4;
+    const float* p = a.in + (b0 + r) * a.ld_in + v0 + part * 4;
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(&sb4[(SB_CORE + core(r & 7, (r >> 3) & 7, r >> 6)) * Q4 + part]);
     if (VEC) {
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(p) : "memory");
     } else {
@@ -173,7 +181,7 @@ __global__ void __launch_bounds__(256, 3) cheb_step_brick8(StepArgs<float> a, in
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
 
-  const float2* s2 = (const float2*)sm + vp;  // point slot q -> s2[q * 4]
+  const float2* s2 = (const float2*)sm + vp;  // point slot q -> s2[q * VPL]
   float2* a2 = (float2*)sm + vp;
   float st[7];
 #pragma unroll
@@ -192,9 +200,9 @@ __global__ void __launch_bounds__(256, 3) cheb_step_brick8(StepArgs<float> a, in
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
 #pragma unroll
-    for (int x = 0; x < 8; x++) w[6 + x] = s2[(SB_CORE + sb_core(x, y, z)) * 4];
+    for (int x = 0; x < 8; x++) w[6 + x] = s2[(SB_CORE + core(x, y, z)) * VPL];
 #pragma unroll
-    for (int x = 0; x < 8; x++) a2[(SB_ACC + sb_core(x, y, z)) * 4] = line_terms<true>(w, 6 + x, st);
+    for (int x = 0; x < 8; x++) a2[(SB_ACC + core(x, y, z)) * VPL] = line_terms<true>(w, 6 + x, st);
   }
   // ---- y pass: line (x, z) ----
   {
@@ -206,11 +214,11 @@ __global__ void __launch_bounds__(256, 3) cheb_step_brick8(StepArgs<float> a, in
       w[14 + yy] = nby1 >= 0 ? ld2<VEC>(a.in, (int64_t)nby1 * 512 + (z * 8 + yy) * 8 + x, a.ld_in, vl) : zero2;
     }
 #pragma unroll
-    for (int y = 0; y < 8; y++) w[6 + y] = s2[(SB_CORE + sb_core(x, y, z)) * 4];
+    for (int y = 0; y < 8; y++) w[6 + y] = s2[(SB_CORE + core(x, y, z)) * VPL];
     __syncthreads();  // x-pass accumulator writes are visible
 #pragma unroll
     for (int y = 0; y < 8; y++) {
-      const int q = (SB_ACC + sb_core(x, y, z)) * 4;
+      const int q = (SB_ACC + core(x, y, z)) * VPL;
       a2[q] = f2_add(a2[q], line_terms<false>(w, 6 + y, st));
     }
   }
@@ -226,7 +234,7 @@ __global__ void __launch_bounds__(256, 3) cheb_step_brick8(StepArgs<float> a, in
       c = f2_fma(f2(ch.y), make_float2(cf[cld], cf[cld + 1]), c);
       c = f2_fma(f2(ch.z), make_float2(cf[2 * cld], cf[2 * cld + 1]), c);
       c = f2_fma(f2(ch.w), make_float2(cf[3 * cld], cf[3 * cld + 1]), c);
-      float* acc = (float*)&a2[(SB_ACC + sb_core(ls & 7, (ls >> 3) & 7, ls >> 6)) * 4];
+      float* acc = (float*)&a2[(SB_ACC + core(ls & 7, (ls >> 3) & 7, ls >> 6)) * VPL];
       atomicAdd(acc, c.x);
       atomicAdd(acc + 1, c.y);
     }
@@ -235,25 +243,13 @@ __global__ void __launch_bounds__(256, 3) cheb_step_brick8(StepArgs<float> a, in
   {
     const int x = line & 7, y = line >> 3;
     float2 w[20];
-    float2 pv[8];
-    float vv[8];
-    uint8_t mk[8];
 #pragma unroll
     for (int zz = 0; zz < 6; zz++) {
       w[zz] = nbz0 >= 0 ? ld2<VEC>(a.in, (int64_t)nbz0 * 512 + (2 + zz) * 64 + y * 8 + x, a.ld_in, vl) : zero2;
       w[14 + zz] = nbz1 >= 0 ? ld2<VEC>(a.in, (int64_t)nbz1 * 512 + zz * 64 + y * 8 + x, a.ld_in, vl) : zero2;
     }
 #pragma unroll
-    for (int z = 0; z < 8; z++) {
-      const int64_t s = b0 + z * 64 + y * 8 + x;
-      mk[z] = __ldg(a.mask + s);
-      vv[z] = __ldg(a.V + s);
-      pv[z] = a.prev ? (VEC ? *(const float2*)(a.prev + s * a.ld_prev + vl)
-                            : make_float2(a.prev[s * a.ld_prev + vl], a.prev[s * a.ld_prev + vl + 1]))
-                     : zero2;
-    }
-#pragma unroll
-    for (int z = 0; z < 8; z++) w[6 + z] = s2[(SB_CORE + sb_core(x, y, z)) * 4];
+    for (int z = 0; z < 8; z++) w[6 + z] = s2[(SB_CORE + core(x, y, z)) * VPL];
     __syncthreads();  // scatter atomics are complete
     const bool st0 = vl < a.w, st1 = vl + 1 < a.w;
     const float2 alpha = f2(a.alpha), beta = f2(a.beta), negc = f2(-a.c);
@@ -261,11 +257,16 @@ __global__ void __launch_bounds__(256, 3) cheb_step_brick8(StepArgs<float> a, in
     for (int z = 0; z < 8; z++) {
       const int64_t s = b0 + z * 64 + y * 8 + x;
       float2 res = zero2;
-      if (mk[z]) {
+      if (__ldg(a.mask + s)) {
         const float2 yc = w[6 + z];
-        float2 hy = f2_add(a2[(SB_ACC + sb_core(x, y, z)) * 4], line_terms<false>(w, 6 + z, st));
-        hy = f2_fma(f2(vv[z]), yc, hy);
-        res = f2_fma(beta, pv[z], f2_mul(alpha, f2_fma(negc, yc, hy)));
+        float2 hy = f2_add(a2[(SB_ACC + core(x, y, z)) * VPL], line_terms<false>(w, 6 + z, st));
+        hy = f2_fma(f2(__ldg(a.V + s)), yc, hy);
+        res = f2_mul(alpha, f2_fma(negc, yc, hy));
+        if (a.prev) {
+          const float2 pv = VEC ? *(const float2*)(a.prev + s * a.ld_prev + vl)
+                                : make_float2(a.prev[s * a.ld_prev + vl], a.prev[s * a.ld_prev + vl + 1]);
+          res = f2_fma(beta, pv, res);
+        }
       }
       float* o = a.out + s * a.ld_out + vl;
       if (st0 && st1 && VEC) {
@@ -382,28 +383,38 @@ static cudaError_t step_t(const Ham& H, const void* in, int64_t ld_in, const voi
   a.n_slots = H.grid.n_slots;
   const int w8 = (w + 7) / 8 * 8;
   if (sizeof(T) == 4 && H.grid.B == 8 && wavail >= w8 && cld >= w8 && cld % 2 == 0) {
-    // staged brick kernel: every row chunk it touches lies inside the first w8 columns
+    // brick kernel: every row chunk it touches lies inside the first w8 columns
+    const bool wide = w >= 32 && wavail >= (w + 31) / 32 * 32 && cld >= (w + 31) / 32 * 32;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !g_brick_attr[dev]) {
-      cudaError_t e = cudaFuncSetAttribute(cheb_step_brick8<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           SB_SMEM_BYTES);
+      cudaError_t e = cudaFuncSetAttribute(cheb_step_brick8<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           SB_TOTAL * 128);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(cheb_step_brick8<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 SB_SMEM_BYTES);
+        e = cudaFuncSetAttribute(cheb_step_brick8<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SB_TOTAL * 128);
       if (e != cudaSuccess) return e;
       g_brick_attr[dev] = true;
     }
     const bool vec = (ld_in % 4 == 0) && (ld_out % 4 == 0) && (!prev || ld_prev % 4 == 0) && (cld % 2 == 0) &&
                      ((uintptr_t)in % 16 == 0) && ((uintptr_t)out % 16 == 0) &&
                      (!prev || (uintptr_t)prev % 16 == 0);
-    const int nchunk = w8 / 8;
-    const unsigned grid = (unsigned)(H.grid.n_bricks * nchunk);
     StepArgs<float>& af = *reinterpret_cast<StepArgs<float>*>(&a);
-    if (vec)
-      cheb_step_brick8<true><<<grid, 256, SB_SMEM_BYTES, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
-    else
-      cheb_step_brick8<false><<<grid, 256, SB_SMEM_BYTES, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
+    if (wide) {
+      const int nchunk = (w + 31) / 32;
+      const unsigned grid = (unsigned)(H.grid.n_bricks * nchunk);
+      if (vec)
+        cheb_step_brick8<32, true><<<grid, 1024, SB_TOTAL * 128, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
+      else
+        cheb_step_brick8<32, false><<<grid, 1024, SB_TOTAL * 128, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
+    } else {
+      const int nchunk = w8 / 8;
+      const unsigned grid = (unsigned)(H.grid.n_bricks * nchunk);
+      if (vec)
+        cheb_step_brick8<8, true><<<grid, 256, SB_TOTAL * 32, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
+      else
+        cheb_step_brick8<8, false><<<grid, 256, SB_TOTAL * 32, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
+    }
     return cudaGetLastError();
   }
   const int64_t n = a.n_slots * w;

@@ -36,7 +36,8 @@ constexpr int A_STAGE_BYTES = NPIECE * BLK_ELEMS * 2;       // 24 KB
 constexpr int B_STAGE_BYTES = NPIECE * 2 * BLK_ELEMS * 2;   // 48 KB
 constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;  // 72 KB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr int GRAM_CHUNK_ROWS = 16384;                      // rows split per launch
+constexpr int64_t GRAM_CHUNK_MIN = 16384, GRAM_CHUNK_MAX = 262144;  // rows split per launch
+constexpr size_t GRAM_PIECE_BUDGET = (size_t)1 << 30;               // bytes of split pieces per launch
 constexpr uint32_t WAIT_LIMIT = 1u << 20;                   // bounded spin on mbarriers
 
 __device__ unsigned int g_tc_status;  // 0 ok, else a wait timed out
@@ -153,7 +154,8 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(TcArgs p) {
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x;
-  const int mt = tile % p.m_tiles, nt = tile / p.m_tiles;
+  // N tiles fastest: the CTAs that share one A row panel run side by side (L2 reuse)
+  const int nt = tile % p.n_tiles, mt = tile / p.n_tiles;
   if (p.symmetric && nt * TN + TN - 1 < mt * TM) return;  // tile entirely below the diagonal
   const int kb0 = blockIdx.y * p.kb_per_cta;
   const int kb1 = min(p.kb_total, kb0 + p.kb_per_cta);
@@ -250,15 +252,23 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(TcArgs p) {
             }
           }
         } else {
-          if ((int64_t)i < p.rows) {
-            float* o = p.out + (int64_t)i * p.ldo + nt * TN + c0;
-            const float* ad = p.addA ? p.addA + (int64_t)i * p.lda_add + nt * TN + c0 : nullptr;
-#pragma unroll 4
-            for (int c = 0; c < 32; c++) {
-              const int j = nt * TN + c0 + c;
-              if (j < p.n) o[c] = ad ? v[c] + ad[c] : v[c];
+          // transpose the 32 x 32 block through shared memory (the pipeline buffers are
+          // idle once the accumulator is complete) so that each store instruction writes
+          // one contiguous 128-byte row segment
+          float* tr = (float*)smem + q * 32 * 33;
+#pragma unroll
+          for (int c = 0; c < 32; c++) tr[lane * 33 + c] = v[c];
+          __syncwarp();
+          const int j = nt * TN + c0 + lane;
+          for (int r = 0; r < 32; r++) {
+            const int64_t ir = (int64_t)mt * TM + q * 32 + r;
+            if (ir < p.rows && j < p.n) {
+              float val = tr[r * 33 + lane];
+              if (p.addA) val += p.addA[ir * p.lda_add + j];
+              p.out[ir * p.ldo + j] = val;
             }
           }
+          __syncwarp();
         }
       }
     }
@@ -580,9 +590,28 @@ size_t piece_bytes(int64_t mn, int64_t k) { return (size_t)pad_to(mn, TN) * pad_
 
 bool tc_available() { return true; }
 
-size_t gram_tc_work_bytes(int64_t rows, int m, int n) {
-  const int64_t chunk = std::min<int64_t>(rows, GRAM_CHUNK_ROWS);
+int64_t gram_chunk_rows(int64_t rows, int m, int n) {
+  const size_t per_row = (size_t)NPIECE * 2 * (pad_to(m, TN) + pad_to(n, TN));
+  int64_t c = (int64_t)(GRAM_PIECE_BUDGET / per_row) / TK * TK;
+  c = std::max<int64_t>(GRAM_CHUNK_MIN, std::min<int64_t>(GRAM_CHUNK_MAX, c));
+  return std::min<int64_t>(rows, c);
+}
+
+size_t gram_pieces_bytes(int m, int n, int64_t chunk) {
   return NPIECE * (kscf_align256(piece_bytes(m, chunk)) + kscf_align256(piece_bytes(n, chunk))) + 256;
+}
+
+size_t gram_tc_work_bytes(int64_t rows, int m, int n) { return gram_pieces_bytes(m, n, gram_chunk_rows(rows, m, n)); }
+
+// largest row chunk (multiple of TK, at most GRAM_CHUNK_MAX and rows) whose pieces fit
+int64_t gram_chunk_for_work(int64_t rows, int m, int n, size_t work_bytes) {
+  const size_t per_row = (size_t)NPIECE * 2 * (pad_to(m, TN) + pad_to(n, TN));
+  const size_t slack = 256 + 2 * NPIECE * 256;
+  if (work_bytes <= slack) return 0;
+  int64_t c = (int64_t)((work_bytes - slack) / per_row) / TK * TK;
+  c = std::min<int64_t>(c, std::min<int64_t>(pad_to(rows, TK), GRAM_CHUNK_MAX));
+  while (c > 0 && gram_pieces_bytes(m, n, c) > work_bytes) c -= TK;
+  return c;
 }
 
 size_t rotate_tc_work_bytes(int64_t rows, int kin, int kout) {
@@ -592,7 +621,8 @@ size_t rotate_tc_work_bytes(int64_t rows, int kin, int kout) {
 cudaError_t launch_gram_tc(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t rows, int m, int n,
                            double scale, double* C, int64_t ldc, bool accumulate, void* work, size_t work_bytes,
                            cudaStream_t st) {
-  if (work_bytes < gram_tc_work_bytes(rows, m, n)) return cudaErrorInvalidValue;
+  const int64_t chunk = gram_chunk_for_work(rows, m, n, work_bytes);
+  if (chunk < TK && rows > 0) return cudaErrorInvalidValue;
   cudaError_t e = prepare_kernel();
   if (e != cudaSuccess) return e;
   if (!accumulate) {
@@ -600,7 +630,6 @@ cudaError_t launch_gram_tc(const float* A, int64_t lda, const float* B, int64_t 
   }
   if (rows == 0 || m == 0 || n == 0) return cudaGetLastError();
   const bool sym = (A == B && lda == ldb && m == n);
-  const int64_t chunk = std::min<int64_t>(rows, GRAM_CHUNK_ROWS);
   char* w = (char*)work;
   __nv_bfloat16* Ap[NPIECE];
   __nv_bfloat16* Bp[NPIECE];
@@ -637,8 +666,29 @@ cudaError_t launch_gram_tc(const float* A, int64_t lda, const float* B, int64_t 
                                                                            Bp[2]),
           count_launch();
     a.nkb = nkb;
-    // split the K range over CTAs only as far as needed to fill the GPU
-    int ks = std::max(1, std::min(cdiv(2 * 152, tiles), cdiv(nkb, G_SUB_KB)));
+    // split the K range over CTAs: pick the split whose active CTAs fill whole waves
+    // of one CTA per SM best (the lower-triangle tiles of a symmetric Gram exit at once)
+    int active = 0;
+    for (int t = 0; t < tiles; t++) {
+      const int mt = t % a.m_tiles, nt = t / a.m_tiles;
+      if (!(sym && nt * GN + GN - 1 < mt * TM)) active++;
+    }
+    int ks = 1;
+    double best = -1.0;
+    const int max_ks = std::max(1, cdiv(nkb, G_SUB_KB));
+    for (int cand = 1; cand <= max_ks; cand++) {
+      const int kpc = cdiv(cdiv(nkb, cand), G_SUB_KB) * G_SUB_KB;
+      const int real = cdiv(nkb, kpc);
+      const int64_t ctas = (int64_t)active * real;
+      const double waves = (double)((ctas + 151) / 152);
+      const double eff = (double)ctas / (waves * 152.0);
+      // prefer filled waves, then more parallelism up to ~4 waves
+      const double score = eff - 0.02 * std::max(0.0, waves - 4.0) + (ctas >= 152 ? 0.05 : 0.0);
+      if (score > best + 1e-9) {
+        best = score;
+        ks = real;
+      }
+    }
     a.kb_per_cta = cdiv(cdiv(nkb, ks), G_SUB_KB) * G_SUB_KB;
     ks = cdiv(nkb, a.kb_per_cta);
     tc_gram_kernel<<<dim3(tiles, ks), 320, G_SMEM_BYTES, st>>>(a), count_launch();

@@ -82,16 +82,18 @@ struct Ham {
 
 // ---- launchers (filter.cu) ----
 cudaError_t launch_zero_rows(const Ham& H, void* X, int64_t ld, int k, int dtype, cudaStream_t st);
-// coef rows have stride cld (>= w); round_up8(w) lets the FP32 brick kernel read lane pairs
+// coef rows have stride cld (>= w); coef_ld(w) = round_up32(w) lets the FP32 brick kernel
+// read whole 32-vector chunks
 cudaError_t launch_kb_gather(const Ham& H, const void* Y, int64_t ld, int w, int dtype, void* coef,
                              int64_t cld, cudaStream_t st);
 // wavail: columns readable and writable from in/prev/out in every row (>= w); the FP32
-// brick kernel is used when wavail and cld cover round_up8(w)
+// brick kernel is used when wavail and cld cover round_up8(w) (32-vector CTAs when they
+// cover round_up32(w))
 cudaError_t launch_cheb_step(const Ham& H, const void* in, int64_t ld_in, const void* prev,
                              int64_t ld_prev, void* out, int64_t ld_out, int w, int wavail, int dtype,
                              double alpha, double beta, double c, const void* coef, int64_t cld,
                              cudaStream_t st);
-inline int64_t coef_ld(int w) { return (int64_t)(w + 7) / 8 * 8; }
+inline int64_t coef_ld(int w) { return (int64_t)(w + 31) / 32 * 32; }
 cudaError_t launch_copy_cols(const void* src, int64_t ld_src, void* dst, int64_t ld_dst, int64_t rows,
                              int w, int dtype, cudaStream_t st);
 

@@ -268,7 +268,8 @@ def test_chefsi_f32_tracks_oracle(kscf, system, mode):
     assert subspace_gap(got[:, :4], ref["X"][:, :4], system["OH"].h3) < 1e-2
 
 
-@pytest.mark.parametrize("k,ldpad,block", [(13, 16, 0), (19, 24, 0), (19, 24, 8), (32, 32, 16)])
+@pytest.mark.parametrize("k,ldpad,block", [(13, 16, 0), (19, 24, 0), (19, 24, 8), (32, 32, 16), (40, 64, 0),
+                                           (70, 96, 64), (33, 64, 0)])
 def test_f32_brick_kernel_paths(kscf, system, k, ldpad, block):
     """Row strides padded to a multiple of 8 select the staged FP32 brick kernel (brick
     8); compared with the oracle like the generic path."""
