@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU seconds of the oracle sample")
+    p.add_argument("--alu-peaks", action="store_true", help="build and run the FP32/FP64 FMA microbenchmark")
     return p.parse_args()
 
 
@@ -146,7 +147,7 @@ def oracle_step_sample(w, cpu_seconds: float):
     # calibrate the column count on a 4-column filter
     X = random_block_lex(1, OH.n, 4)
     t0 = time.perf_counter()
-    orc.chebyshev_filter(OH, X, w.degree, -1.0, b, -30.0)
+    orc.chebyshev_filter(OH, X, w.degree, b - 10.0, b, b - 20.0)
     per_col = (time.perf_counter() - t0) / 4
     ks = int(max(4, min(w.k, cpu_seconds / max(per_col, 1e-6))))
     X0 = random_block_lex(1, OH.n, ks)
@@ -207,7 +208,7 @@ def run_kscf(args):
     assert torch.cuda.is_available(), "the kscf arm needs a CUDA device"
     w = workload(args.workload)
     block = args.block or w.block
-    mode = {"auto": kscf.KSCF_GEMM_NATIVE, "native": kscf.KSCF_GEMM_NATIVE, "tensor": kscf.KSCF_GEMM_TENSOR}[args.mode]
+    mode = {"auto": kscf.KSCF_GEMM_TENSOR, "native": kscf.KSCF_GEMM_NATIVE, "tensor": kscf.KSCF_GEMM_TENSOR}[args.mode]
     pos, z = w.atoms()
     species = pseudo_params()
     grid, H = kscf.build_cluster(pos, z, species, w.radius, w.h, brick=args.brick)
@@ -341,8 +342,20 @@ def run_kscf(args):
         dist.destroy_process_group()
 
 
+def alu_peaks():
+    """Compile and run csrc/alu_peaks.cu (FP32, FP32x2 and FP64 FMA throughput)."""
+    import tempfile
+    src = os.path.join(ROOT, "paper_2303_00790_gb300", "csrc", "alu_peaks.cu")
+    exe = os.path.join(tempfile.mkdtemp(), "alu_peaks")
+    subprocess.run(["nvcc", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-o", exe, src], check=True)
+    print(subprocess.run([exe], check=True, capture_output=True, text=True).stdout, end="")
+
+
 def main():
     args = parse()
+    if args.alu_peaks:
+        alu_peaks()
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

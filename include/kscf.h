@@ -265,10 +265,11 @@ int kscf_rotate(const void* A, int64_t lda, const double* Q, int64_t ldq, int64_
                 void* stream);
 int kscf_gemm_workspace_size(int op, int64_t rows, int m, int n, int dtype, int mode, size_t* bytes);
 
-/* Reads and clears the device status word of the tensor-core kernels: KSCF_ERR_TIMEOUT
- * if a bounded mbarrier wait gave up since the last check (the kernel then skipped its
- * remaining work and freed its tensor memory), else KSCF_OK.  Synchronising.
- * orthonormalize and rayleigh_ritz check it themselves. */
+/* Reads and clears the device status words of the kernels that wait on mbarriers (the
+ * tensor-core GEMMs and the TMA filter step): KSCF_ERR_TIMEOUT if a bounded wait gave
+ * up since the last check (the kernel then skipped its remaining work and, for the
+ * GEMMs, freed its tensor memory), else KSCF_OK.  Synchronising.  orthonormalize and
+ * rayleigh_ritz check the GEMM word themselves; filter callers check after the filter. */
 int kscf_check_status(void);
 
 /* Hilbert index of brick coordinates (x, y, z) on the 2^bits cube, as used to order the

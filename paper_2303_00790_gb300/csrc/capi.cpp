@@ -23,6 +23,7 @@ size_t gram_tc_work_bytes(int64_t rows, int m, int n);
 size_t rotate_tc_work_bytes(int64_t rows, int kin, int kout);
 bool tc_available();
 cudaError_t tc_status(bool reset, unsigned int* status);
+cudaError_t filter_status(bool reset, unsigned int* status);
 }  // namespace kscf
 
 namespace {
@@ -591,14 +592,16 @@ extern "C" int kscf_gemm_workspace_size(int op, int64_t rows, int m, int n, int 
 }
 
 extern "C" int kscf_check_status(void) {
-  unsigned int st = 0;
+  unsigned int st = 0, fs = 0;
   cudaError_t e = tc_status(true, &st);
+  if (e == cudaSuccess) e = filter_status(true, &fs);
+  st |= fs << 1;
   if (e != cudaSuccess) {
     set_error("kscf_check_status: %s", cudaGetErrorString(e));
     return KSCF_ERR_CUDA;
   }
   if (st) {
-    set_error("a tensor-core pipeline wait timed out (status %u)", st);
+    set_error("a bounded device wait timed out (status %u: bit 0 tensor-core GEMM, bit 1 filter)", st);
     return KSCF_ERR_TIMEOUT;
   }
   return KSCF_OK;

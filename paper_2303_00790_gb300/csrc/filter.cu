@@ -8,7 +8,11 @@
 // Chelikowsky 2006) with the stencil, the local potential, the nonlocal scatter and
 // the recurrence update fused in one pass over the grid.  The projections
 // <chi_i, in> come from kb_gather, launched just before on the same stream.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
 
 #include "kscf_internal.h"
 
@@ -102,7 +106,6 @@ __global__ void __launch_bounds__(256) cheb_step_generic(StepArgs<T> a) {
 // and acc with the same swizzle, conflict-free for all three passes.
 namespace {
 constexpr int SB_CORE = 0, SB_ACC = 512, SB_TOTAL = 1024;
-constexpr int SB_SMEM_BYTES = SB_TOTAL * 32;
 
 __device__ __forceinline__ int sb_core(int x, int y, int z) { return (z * 8 + y) * 8 + (x ^ (y & 3)); }
 
@@ -142,13 +145,13 @@ __device__ __forceinline__ float2 ld2(const float* base, int64_t slot, int64_t l
 }
 }  // namespace
 
-// NV vectors per CTA (8 or 32): a point slot in shared memory is NV floats; the 64
-// lines of a pass are spread over 64 * NV/2 threads, NV/2 lanes per line, two vectors
-// per lane.  NV = 32 makes every halo load instruction cover two 128-byte row segments.
+// NV = 8 vectors per CTA: a point slot in shared memory is 8 floats (32 bytes); the 64
+// lines of a pass are spread over 256 threads, 4 lanes per line, two vectors per lane.
 // VEC: rows are read with vector loads (ld and column offsets multiples of 4).
 template <int NV, bool VEC>
-__global__ void __launch_bounds__(NV * 32, NV == 8 ? 3 : 1)
+__global__ void __launch_bounds__(NV * 32, 3)
     cheb_step_brick8(StepArgs<float> a, int nchunk, const uint16_t* __restrict__ entry_lslot) {
+  static_assert(NV == 8, "the swizzled shared layout assumes 32-byte point slots");
   constexpr int VPL = NV / 2;       // lanes per line
   constexpr int NT = 64 * VPL;      // threads
   constexpr int Q4 = NV / 4;        // float4 per point slot
@@ -164,8 +167,7 @@ __global__ void __launch_bounds__(NV * 32, NV == 8 ? 3 : 1)
   const int nbx0 = __ldg(a.nbr + (int64_t)brick * 6 + 0), nbx1 = __ldg(a.nbr + (int64_t)brick * 6 + 1);
   const int nby0 = __ldg(a.nbr + (int64_t)brick * 6 + 2), nby1 = __ldg(a.nbr + (int64_t)brick * 6 + 3);
   const int nbz0 = __ldg(a.nbr + (int64_t)brick * 6 + 4), nbz1 = __ldg(a.nbr + (int64_t)brick * 6 + 5);
-  // point slot of (x, y, z): XOR swizzle for 32-byte slots, plain for 128-byte slots
-  auto core = [](int x, int y, int z) { return NV == 8 ? sb_core(x, y, z) : (z * 8 + y) * 8 + x; };
+  auto core = [](int x, int y, int z) { return sb_core(x, y, z); };
 
   // ---- stage the brick core: 512 rows x NV floats ----
   for (int t = tid; t < 512 * Q4; t += NT) {
@@ -279,6 +281,249 @@ __global__ void __launch_bounds__(NV * 32, NV == 8 ? 3 : 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// TMA brick kernel (FP32, 8^3 bricks, 8 vectors per CTA): the wavefunction block is
+// viewed as a 5D tensor [brick][z][y][x][column] and the Tensor Memory Accelerator
+// copies the six 6-deep neighbour faces (one box each) into shared memory, densely
+// (no swizzle); the x faces use a view with x and y exchanged so that they land as
+// [z][x][y] and the x pass reads them without bank conflicts.  Boxes of missing
+// neighbours use an out-of-range brick coordinate and arrive zero-filled.  The brick
+// core is copied with cp.async into the XOR-swizzled layout of the kernel above.  All
+// stencil reads then come from shared memory; the line passes, the nonlocal scatter
+// and the fused recurrence are those of the kernel above.
+struct BrickMaps {
+  CUtensorMap fx;  // view [brick][z][x][y][col], box {8, 8 y, 6 x, 8 z, 1}
+  CUtensorMap fy;  // view [brick][z][y][x][col], box {8, 8 x, 6 y, 8 z, 1}
+  CUtensorMap fz;  // view [brick][z][y][x][col], box {8, 8 x, 8 y, 6 z, 1}
+};
+
+__device__ unsigned int g_filter_status;  // set when a bounded wait gave up
+
+namespace {
+constexpr int TB_CORE = 0, TB_FXM = 16384, TB_FXP = TB_FXM + 12288, TB_FYM = TB_FXP + 12288,
+              TB_FYP = TB_FYM + 12288, TB_FZM = TB_FYP + 12288, TB_FZP = TB_FZM + 12288,
+              TB_ACC = TB_FZP + 12288, TB_BAR = TB_ACC + 16384, TB_BYTES = TB_BAR + 64;
+constexpr uint32_t TB_TX = 6 * 12288;        // bytes the TMA delivers per CTA
+constexpr int TB_SMEM = TB_BYTES + 1024;      // + alignment slack
+
+__device__ __forceinline__ void tma_load5(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
+}  // namespace
+
+template <int dummy>
+__global__ void __launch_bounds__(256, 2)
+    cheb_step_tma8(StepArgs<float> a, const __grid_constant__ BrickMaps maps, int nchunk, int n_bricks,
+                   int64_t wavail_prev, int core_cols, const uint16_t* __restrict__ entry_lslot) {
+  extern __shared__ uint8_t tb_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)tb_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm);
+  uint64_t* bar = (uint64_t*)(sm + TB_BAR);
+  const int64_t cld = a.cld;
+  const int brick = blockIdx.x / nchunk, chunk = blockIdx.x - (blockIdx.x / nchunk) * nchunk;
+  const int v0 = chunk * 8;
+  const int tid = threadIdx.x;
+  const int vp = tid & 3, line = tid >> 2;
+  const int vl = v0 + 2 * vp;
+  const int64_t b0 = (int64_t)brick * 512;
+
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(TB_TX) : "memory");
+    const int32_t* nb = a.nbr + (int64_t)brick * 6;
+    auto nbc = [&](int f) { const int q = __ldg(nb + f); return q >= 0 ? q : n_bricks; };  // OOB -> zeros
+    tma_load5(sbase + TB_FXM, &maps.fx, v0, 0, 2, 0, nbc(0), b);
+    tma_load5(sbase + TB_FXP, &maps.fx, v0, 0, 0, 0, nbc(1), b);
+    tma_load5(sbase + TB_FYM, &maps.fy, v0, 0, 2, 0, nbc(2), b);
+    tma_load5(sbase + TB_FYP, &maps.fy, v0, 0, 0, 0, nbc(3), b);
+    tma_load5(sbase + TB_FZM, &maps.fz, v0, 0, 0, 2, nbc(4), b);
+    tma_load5(sbase + TB_FZP, &maps.fz, v0, 0, 0, 0, nbc(5), b);
+  }
+  // brick core: 512 rows x 32 B into the XOR-swizzled layout (asynchronous copies)
+  for (int t = tid; t < 1024; t += 256) {
+    const int r = t >> 1, half = t & 1;
+    const bool live = v0 + half * 4 < core_cols;  // columns past the block arrive as zeros
+    const float* p = live ? a.in + (b0 + r) * a.ld_in + v0 + half * 4 : a.in;
+    const uint32_t d = sbase + TB_CORE + (uint32_t)(sb_core(r & 7, (r >> 3) & 7, r >> 6) * 32 + half * 16);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(p), "r"(live ? 16 : 0) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  // z-pass operands are fetched while the copies are in flight
+  const int zx = line & 7, zy = line >> 3;
+  float2 pv[8];
+  float vv[8];
+  uint32_t mk = 0;
+  const bool pv_ok = vl + 1 < wavail_prev;
+#pragma unroll
+  for (int z = 0; z < 8; z++) {
+    const int64_t s = b0 + z * 64 + zy * 8 + zx;
+    mk |= (uint32_t)__ldg(a.mask + s) << z;
+    vv[z] = __ldg(a.V + s);
+    pv[z] = (a.prev && pv_ok) ? *(const float2*)(a.prev + s * a.ld_prev + vl) : make_float2(0.f, 0.f);
+  }
+  {
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < (1u << 22) && !done; it++) {
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n}"
+          : "=r"(done)
+          : "r"(b)
+          : "memory");
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!done) {
+      atomicOr(&g_filter_status, 1u);
+      return;
+    }
+  }
+  __syncthreads();  // core copies of all threads have landed
+  auto rd = [&](int region, int point) -> float2 { return *(const float2*)(sm + region + point * 32 + 8 * vp); };
+  auto rc = [&](int x, int y, int z) -> float2 { return *(const float2*)(sm + TB_CORE + sb_core(x, y, z) * 32 + 8 * vp); };
+  float2* a2 = (float2*)(sm + TB_ACC) + vp;
+  float st[7];
+#pragma unroll
+  for (int k = 0; k < 7; k++) st[k] = a.st[k];
+
+  // ---- x pass: line (y, z) ----
+  {
+    const int y = line & 7, z = line >> 3;
+    float2 w[20];
+#pragma unroll
+    for (int xx = 0; xx < 6; xx++) {
+      w[xx] = rd(TB_FXM, (z * 6 + xx) * 8 + y);
+      w[14 + xx] = rd(TB_FXP, (z * 6 + xx) * 8 + y);
+    }
+#pragma unroll
+    for (int x = 0; x < 8; x++) w[6 + x] = rc(x, y, z);
+#pragma unroll
+    for (int x = 0; x < 8; x++) a2[sb_core(x, y, z) * 4] = line_terms<true>(w, 6 + x, st);
+  }
+  __syncthreads();
+  // ---- y pass: line (x, z) ----
+  {
+    const int x = line & 7, z = line >> 3;
+    float2 w[20];
+#pragma unroll
+    for (int yy = 0; yy < 6; yy++) {
+      w[yy] = rd(TB_FYM, (z * 6 + yy) * 8 + x);
+      w[14 + yy] = rd(TB_FYP, (z * 6 + yy) * 8 + x);
+    }
+#pragma unroll
+    for (int y = 0; y < 8; y++) w[6 + y] = rc(x, y, z);
+#pragma unroll
+    for (int y = 0; y < 8; y++) {
+      const int q = sb_core(x, y, z) * 4;
+      a2[q] = f2_add(a2[q], line_terms<false>(w, 6 + y, st));
+    }
+  }
+  __syncthreads();
+  // ---- nonlocal scatter over the brick's contiguous entry range ----
+  {
+    const int64_t e0 = __ldg(a.kb_ptr + b0), e1 = __ldg(a.kb_ptr + b0 + 512);
+    for (int64_t e = e0 + line; e < e1; e += 64) {
+      const int ls = __ldg(entry_lslot + e);
+      const float4 ch = __ldg((const float4*)(a.kb_chi + 4 * e));
+      const float* cf = a.coef + (int64_t)__ldg(a.kb_atom + e) * 4 * cld + vl;
+      float2 c = f2_mul(f2(ch.x), make_float2(cf[0], cf[1]));
+      c = f2_fma(f2(ch.y), make_float2(cf[cld], cf[cld + 1]), c);
+      c = f2_fma(f2(ch.z), make_float2(cf[2 * cld], cf[2 * cld + 1]), c);
+      c = f2_fma(f2(ch.w), make_float2(cf[3 * cld], cf[3 * cld + 1]), c);
+      float* acc = (float*)&a2[sb_core(ls & 7, (ls >> 3) & 7, ls >> 6) * 4];
+      atomicAdd(acc, c.x);
+      atomicAdd(acc + 1, c.y);
+    }
+  }
+  __syncthreads();
+  // ---- z pass: line (x, y) ----
+  {
+    const int x = zx, y = zy;
+    float2 w[20];
+#pragma unroll
+    for (int zz = 0; zz < 6; zz++) {
+      w[zz] = rd(TB_FZM, (zz * 8 + y) * 8 + x);
+      w[14 + zz] = rd(TB_FZP, (zz * 8 + y) * 8 + x);
+    }
+#pragma unroll
+    for (int z = 0; z < 8; z++) w[6 + z] = rc(x, y, z);
+    const bool st0 = vl < a.w, st1 = vl + 1 < a.w;
+    const float2 alpha = f2(a.alpha), beta = f2(a.beta), negc = f2(-a.c);
+#pragma unroll
+    for (int z = 0; z < 8; z++) {
+      const int64_t s = b0 + z * 64 + y * 8 + x;
+      float2 res = make_float2(0.f, 0.f);
+      if ((mk >> z) & 1u) {
+        const float2 yc = w[6 + z];
+        float2 hy = f2_add(a2[sb_core(x, y, z) * 4], line_terms<false>(w, 6 + z, st));
+        hy = f2_fma(f2(vv[z]), yc, hy);
+        res = f2_fma(beta, pv[z], f2_mul(alpha, f2_fma(negc, yc, hy)));
+      }
+      float* o = a.out + s * a.ld_out + vl;
+      if (st0 && st1) {
+        *(float2*)o = res;
+      } else if (st0) {
+        o[0] = res.x;
+      }
+    }
+  }
+}
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+cudaError_t encode_brick_maps(BrickMaps* m, const float* base, int64_t ld, int64_t cols, int64_t n_bricks) {
+  std::call_once(g_encode_once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  });
+  if (!g_encode) return cudaErrorNotSupported;
+  const cuuint64_t dims[5] = {(cuuint64_t)cols, 8, 8, 8, (cuuint64_t)n_bricks};
+  const cuuint64_t row = (cuuint64_t)ld * 4;
+  // x faces: dims (col, y, x, z, brick); y and z faces: dims (col, x, y, z, brick)
+  const cuuint64_t str_xy[4] = {row * 8, row, row * 64, row * 512};
+  const cuuint64_t str_n[4] = {row, row * 8, row * 64, row * 512};
+  const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  const cuuint32_t box_x[5] = {8, 8, 6, 8, 1}, box_y[5] = {8, 8, 6, 8, 1}, box_z[5] = {8, 8, 8, 6, 1};
+  struct Spec {
+    CUtensorMap* map;
+    const cuuint64_t* str;
+    const cuuint32_t* box;
+  } spec[3] = {{&m->fx, str_xy, box_x}, {&m->fy, str_n, box_y}, {&m->fz, str_n, box_z}};
+  for (int i = 0; i < 3; i++) {
+    CUresult r = g_encode(spec[i].map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 5, (void*)base, dims, spec[i].str,
+                          spec[i].box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+bool g_tma_attr[64] = {false};
+}  // namespace
+
+cudaError_t filter_status(bool reset, unsigned int* status) {
+  cudaError_t e = cudaMemcpyFromSymbol(status, g_filter_status, sizeof(unsigned int));
+  if (e == cudaSuccess && reset && *status) {
+    unsigned int z = 0;
+    e = cudaMemcpyToSymbol(g_filter_status, &z, sizeof(unsigned int));
+  }
+  return e;
+}
+
 // coef[(a*4+l)*w + v] = E_l h^3 sum_{entries e of atom a} chi_l(e) Y[slot_e][v]
 template <typename T>
 __global__ void __launch_bounds__(256) kb_gather_kernel(const T* __restrict__ Y, int64_t ld, int w, int64_t cld,
@@ -354,7 +599,6 @@ cudaError_t launch_kb_gather(const Ham& H, const void* Y, int64_t ld, int w, int
   return cudaGetLastError();
 }
 
-static bool g_brick_attr[64] = {false};
 
 template <typename T>
 static cudaError_t step_t(const Ham& H, const void* in, int64_t ld_in, const void* prev, int64_t ld_prev,
@@ -382,40 +626,41 @@ static cudaError_t step_t(const Ham& H, const void* in, int64_t ld_in, const voi
   for (int k = 0; k < 7; k++) a.st[k] = (T)H.stencil[k];
   a.n_slots = H.grid.n_slots;
   const int w8 = (w + 7) / 8 * 8;
+  StepArgs<float>& af = *reinterpret_cast<StepArgs<float>*>(&a);
+  // 1) brick kernel with register halos: rows must have room for whole 8-vector chunks
   if (sizeof(T) == 4 && H.grid.B == 8 && wavail >= w8 && cld >= w8 && cld % 2 == 0) {
-    // brick kernel: every row chunk it touches lies inside the first w8 columns
-    const bool wide = w >= 32 && wavail >= (w + 31) / 32 * 32 && cld >= (w + 31) / 32 * 32;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !g_brick_attr[dev]) {
-      cudaError_t e = cudaFuncSetAttribute(cheb_step_brick8<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           SB_TOTAL * 128);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(cheb_step_brick8<32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 SB_TOTAL * 128);
-      if (e != cudaSuccess) return e;
-      g_brick_attr[dev] = true;
-    }
     const bool vec = (ld_in % 4 == 0) && (ld_out % 4 == 0) && (!prev || ld_prev % 4 == 0) && (cld % 2 == 0) &&
                      ((uintptr_t)in % 16 == 0) && ((uintptr_t)out % 16 == 0) &&
                      (!prev || (uintptr_t)prev % 16 == 0);
-    StepArgs<float>& af = *reinterpret_cast<StepArgs<float>*>(&a);
-    if (wide) {
-      const int nchunk = (w + 31) / 32;
-      const unsigned grid = (unsigned)(H.grid.n_bricks * nchunk);
-      if (vec)
-        cheb_step_brick8<32, true><<<grid, 1024, SB_TOTAL * 128, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
-      else
-        cheb_step_brick8<32, false><<<grid, 1024, SB_TOTAL * 128, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
-    } else {
-      const int nchunk = w8 / 8;
-      const unsigned grid = (unsigned)(H.grid.n_bricks * nchunk);
-      if (vec)
-        cheb_step_brick8<8, true><<<grid, 256, SB_TOTAL * 32, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
-      else
-        cheb_step_brick8<8, false><<<grid, 256, SB_TOTAL * 32, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
-    }
+    const int nchunk = w8 / 8;
+    const unsigned grid = (unsigned)(H.grid.n_bricks * nchunk);
+    if (vec)
+      cheb_step_brick8<8, true><<<grid, 256, SB_TOTAL * 32, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
+    else
+      cheb_step_brick8<8, false><<<grid, 256, SB_TOTAL * 32, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
     return cudaGetLastError();
+  }
+  // 2) TMA brick kernel: rows without spare width (columns past wavail arrive as zeros);
+  //    needs 16-byte row strides and a 16-byte aligned base
+  if (sizeof(T) == 4 && H.grid.B == 8 && ld_in % 4 == 0 && ((uintptr_t)in % 16) == 0 && cld >= w8 && cld % 2 == 0 &&
+      ld_out % 2 == 0 && (!prev || ld_prev % 2 == 0) && ((uintptr_t)out % 8) == 0 &&
+      (!prev || ((uintptr_t)prev % 8) == 0)) {
+    BrickMaps maps;
+    cudaError_t e = encode_brick_maps(&maps, (const float*)in, ld_in, wavail, H.grid.n_bricks);
+    if (e == cudaSuccess) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (dev >= 0 && dev < 64 && !g_tma_attr[dev]) {
+        e = cudaFuncSetAttribute(cheb_step_tma8<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TB_SMEM);
+        if (e != cudaSuccess) return e;
+        g_tma_attr[dev] = true;
+      }
+      const int nchunk = w8 / 8;
+      cheb_step_tma8<0><<<(unsigned)(H.grid.n_bricks * nchunk), 256, TB_SMEM, st>>>(
+          af, maps, nchunk, (int)H.grid.n_bricks, (int64_t)wavail, wavail, H.d_kb_entry_lslot),
+          count_launch();
+      return cudaGetLastError();
+    }
   }
   const int64_t n = a.n_slots * w;
   if (H.grid.B == 8)

@@ -7,7 +7,7 @@
 // x = x1 + x2 + x3 (x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2)), and
 // the six products x1y1, x1y2, x2y1, x1y3, x2y2, x3y1 are accumulated in FP32 in
 // tensor memory; the dropped terms are O(2^-24).  Gram partial sums cover at most
-// 2048 rows before they are added in FP64.
+// 256 rows before they are added into compensated FP32 pairs and, per CTA, into FP64.
 //
 // Data path: a split kernel writes the pieces in the tensor core's K-major
 // "no swizzle" canonical layout, pre-tiled so that every (128 rows x 32 K) operand
@@ -35,7 +35,7 @@ constexpr int NPIECE = 3;
 constexpr int A_STAGE_BYTES = NPIECE * BLK_ELEMS * 2;       // 24 KB
 constexpr int B_STAGE_BYTES = NPIECE * 2 * BLK_ELEMS * 2;   // 48 KB
 constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;  // 72 KB
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256 + 4 * 32 * 17 * 4;
 constexpr int64_t GRAM_CHUNK_MIN = 16384, GRAM_CHUNK_MAX = 262144;  // rows split per launch
 constexpr size_t GRAM_PIECE_BUDGET = (size_t)1 << 30;               // bytes of split pieces per launch
 constexpr uint32_t WAIT_LIMIT = 1u << 20;                   // bounded spin on mbarriers
@@ -118,61 +118,69 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
 struct TcArgs {
   const __nv_bfloat16* A[NPIECE];  // pre-tiled, MN blocks of 128 x K blocks of 32
   const __nv_bfloat16* B[NPIECE];
   int a_nkb, b_nkb;                // K blocks per MN block row in A and B storage
   int m_tiles, n_tiles;            // tiles of 128 (M) and 256 (N)
   int kb_total;                    // K blocks to reduce over
-  int kb_per_cta;
-  int m, n;                        // valid output extent
-  int symmetric;                   // gram of A with itself: only tiles touching j >= i
-  // gram epilogue
-  double* C;
-  int64_t ldc;
-  double scale;
-  // rotate epilogue
+  int n;                           // valid output columns
   float* out;
   int64_t ldo;
-  const float* addA;  // if non-null, out += addA (same indexing, lda_add)
-  int64_t lda_add;
-  int64_t rows;       // valid rows of out
-  int mode;           // 0 gram, 1 rotate
+  int64_t rows;                    // valid rows of out
 };
 
 // products (A piece, B piece) kept: orders 2^0, 2^-8 (two), 2^-16 (three)
 __constant__ int kProdA[6] = {0, 0, 1, 0, 1, 2};
 __constant__ int kProdB[6] = {0, 1, 0, 2, 1, 0};
 
+// Rotation GEMM out = A Q, persistent: CTA c handles tiles c, c + grid, ... (N tiles
+// fastest, so CTAs sharing an A row panel run side by side).  The producer streams the
+// K blocks of consecutive tiles through one STAGES-deep ring; the MMA thread alternates
+// between two 256-column TMEM accumulators, so the four epilogue warps drain tile i
+// (TMEM -> registers -> shared-memory transpose -> coalesced row stores) while tile i+1
+// is being multiplied.
 __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(TcArgs p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* accum = empty + STAGES;
-  uint32_t* tmem_slot = (uint32_t*)(accum + 1);
+  uint64_t* tfull = empty + STAGES;   // 2
+  uint64_t* tempty = tfull + 2;       // 2
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+  float* trbuf = (float*)(tmem_slot + 4);  // 4 x 32 x 17 floats for the epilogue transpose
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x;
-  // N tiles fastest: the CTAs that share one A row panel run side by side (L2 reuse)
-  const int nt = tile % p.n_tiles, mt = tile / p.n_tiles;
-  if (p.symmetric && nt * TN + TN - 1 < mt * TM) return;  // tile entirely below the diagonal
-  const int kb0 = blockIdx.y * p.kb_per_cta;
-  const int kb1 = min(p.kb_total, kb0 + p.kb_per_cta);
-  const int nk = kb1 - kb0;
-  if (nk <= 0) return;
+  const int ntiles = p.m_tiles * p.n_tiles;
+  const int nk = p.kb_total;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; s++) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accum, 1);
+    for (int b = 0; b < 2; b++) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TN));
+                 "r"(2 * TN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
@@ -182,102 +190,107 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(TcArgs p) {
 
   if (warp == 0) {
     if (lane == 0) {
-      // producer: bulk copies of the 3 A pieces (8 KB) and 3 x 2 B blocks (8 KB) per stage
-      int issued = 0;
-      for (int it = 0; it < nk; it++) {
-        const int s = it % STAGES;
-        if (it >= STAGES && !mbar_wait(&empty[s], ((it / STAGES) - 1) & 1)) break;
-        uint8_t* sa = smem + s * STAGE_BYTES;
-        uint8_t* sb = sa + A_STAGE_BYTES;
-        mbar_expect_tx(&full[s], STAGE_BYTES);
-        const int kb = kb0 + it;
-        for (int q = 0; q < NPIECE; q++) {
-          bulk_g2s(sa + q * BLK_ELEMS * 2, p.A[q] + ((int64_t)mt * p.a_nkb + kb) * BLK_ELEMS, BLK_ELEMS * 2, &full[s]);
-          for (int h = 0; h < 2; h++)
-            bulk_g2s(sb + (q * 2 + h) * BLK_ELEMS * 2, p.B[q] + ((int64_t)(2 * nt + h) * p.b_nkb + kb) * BLK_ELEMS,
-                     BLK_ELEMS * 2, &full[s]);
+      // producer: one continuous stream of K blocks over this CTA's tiles
+      int g = 0;  // global stage counter
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int nt = t % p.n_tiles, mt = t / p.n_tiles;
+        for (int kb = 0; kb < nk; kb++, g++) {
+          const int s = g % STAGES;
+          if (g >= STAGES && !mbar_wait(&empty[s], ((g / STAGES) - 1) & 1)) {
+            ok = false;
+            break;
+          }
+          uint8_t* sa = smem + s * STAGE_BYTES;
+          uint8_t* sb = sa + A_STAGE_BYTES;
+          mbar_expect_tx(&full[s], STAGE_BYTES);
+          for (int q = 0; q < NPIECE; q++) {
+            bulk_g2s(sa + q * BLK_ELEMS * 2, p.A[q] + ((int64_t)mt * p.a_nkb + kb) * BLK_ELEMS, BLK_ELEMS * 2,
+                     &full[s]);
+            for (int h = 0; h < 2; h++)
+              bulk_g2s(sb + (q * 2 + h) * BLK_ELEMS * 2, p.B[q] + ((int64_t)(2 * nt + h) * p.b_nkb + kb) * BLK_ELEMS,
+                       BLK_ELEMS * 2, &full[s]);
+          }
         }
-        issued = it + 1;
       }
-      // wait (bounded) until the copies of the last stages issued have landed, so that
-      // none is in flight when the CTA exits, also on a timeout path
-      for (int it = max(0, issued - STAGES); it < issued; it++) mbar_wait(&full[it % STAGES], (it / STAGES) & 1);
+      // the copies of the last stages issued have landed before the CTA can exit
+      for (int q = max(0, g - STAGES); q < g; q++) mbar_wait(&full[q % STAGES], (q / STAGES) & 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // MMA issuer
+      int g = 0, it = 0;
       bool ok = true;
-      for (int it = 0; it < nk && ok; it++) {
-        const int s = it % STAGES;
-        ok = mbar_wait(&full[s], (it / STAGES) & 1);
-        if (!ok) break;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, it++) {
+        const int b = it & 1;
+        if (it >= 2 && !mbar_wait(&tempty[b], ((it >> 1) - 1) & 1)) break;
         tc_fence_after();
-        const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
-        const uint32_t sb = sa + A_STAGE_BYTES;
+        const uint32_t acc = tmem + b * TN;
+        for (int kb = 0; kb < nk; kb++, g++) {
+          const int s = g % STAGES;
+          ok = mbar_wait(&full[s], (g / STAGES) & 1);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+          const uint32_t sb = sa + A_STAGE_BYTES;
 #pragma unroll
-        for (int pr = 0; pr < 6; pr++) {
-          const uint32_t a_base = sa + kProdA[pr] * BLK_ELEMS * 2;
-          const uint32_t b_base = sb + kProdB[pr] * 2 * BLK_ELEMS * 2;
+          for (int pr = 0; pr < 6; pr++) {
+            const uint32_t a_base = sa + kProdA[pr] * BLK_ELEMS * 2;
+            const uint32_t b_base = sb + kProdB[pr] * 2 * BLK_ELEMS * 2;
 #pragma unroll
-          for (int kk = 0; kk < TK / 16; kk++) {
-            // K = 16 covers two core matrices along K (128 B apart); 8-row groups are
-            // 4 core matrices (512 B) apart
-            const uint64_t ad = smem_desc(a_base + kk * 256, 128, 512);
-            const uint64_t bd = smem_desc(b_base + kk * 256, 128, 512);
-            mma_bf16(tmem, ad, bd, (it > 0 || pr > 0 || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < TK / 16; kk++) {
+              // K = 16 covers two core matrices along K (128 B apart); 8-row groups
+              // are 4 core matrices (512 B) apart
+              const uint64_t ad = smem_desc(a_base + kk * 256, 128, 512);
+              const uint64_t bd = smem_desc(b_base + kk * 256, 128, 512);
+              mma_bf16(acc, ad, bd, (kb > 0 || pr > 0 || kk > 0) ? 1u : 0u);
+            }
           }
+          mma_commit(&empty[s]);
         }
-        mma_commit(&empty[s]);
+        mma_commit(&tfull[b]);
       }
-      mma_commit(accum);
     }
   } else {
     // epilogue warps 2..5 -> TMEM lane quadrants 2, 3, 0, 1
     const int q = warp & 3;
-    const int row = q * 32 + lane;
-    // warp-uniform decision: tcgen05.ld below is executed by all lanes or none
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(accum, 0));
-    tc_fence_after();
-    if (ok) {
-      const int i = mt * TM + row;
-      for (int c0 = 0; c0 < TN; c0 += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + c0, v);
-        if (p.mode == 0) {
-          if (i < p.m) {
-#pragma unroll 4
-            for (int c = 0; c < 32; c++) {
-              const int j = nt * TN + c0 + c;
-              if (j < p.n && (!p.symmetric || j >= i)) atomicAdd(p.C + i + (int64_t)j * p.ldc, p.scale * (double)v[c]);
-            }
-          }
-        } else {
-          // transpose the 32 x 32 block through shared memory (the pipeline buffers are
-          // idle once the accumulator is complete) so that each store instruction writes
-          // one contiguous 128-byte row segment
-          float* tr = (float*)smem + q * 32 * 33;
+    float* tr = trbuf + q * 32 * 17;
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
+      const int nt = t % p.n_tiles, mt = t / p.n_tiles;
+      const int b = it & 1;
+      // warp-uniform decision: tcgen05.ld below is executed by all lanes or none
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&tfull[b], (it >> 1) & 1));
+      if (!ok) break;
+      tc_fence_after();
+      for (int c0 = 0; c0 < TN; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + b * TN + c0, v);
+        // transpose the 32 x 16 block through shared memory: each store instruction then
+        // writes two contiguous 64-byte row segments
 #pragma unroll
-          for (int c = 0; c < 32; c++) tr[lane * 33 + c] = v[c];
-          __syncwarp();
-          const int j = nt * TN + c0 + lane;
-          for (int r = 0; r < 32; r++) {
-            const int64_t ir = (int64_t)mt * TM + q * 32 + r;
-            if (ir < p.rows && j < p.n) {
-              float val = tr[r * 33 + lane];
-              if (p.addA) val += p.addA[ir * p.lda_add + j];
-              p.out[ir * p.ldo + j] = val;
-            }
+        for (int c = 0; c < 16; c++) tr[lane * 17 + c] = v[c];
+        __syncwarp();
+        const int jj = lane & 15, rh = lane >> 4;
+        const int j = nt * TN + c0 + jj;
+        if (j < p.n) {
+#pragma unroll 8
+          for (int r = 0; r < 32; r += 2) {
+            const int64_t ir = (int64_t)mt * TM + q * 32 + r + rh;
+            if (ir < p.rows) p.out[ir * p.ldo + j] = tr[(r + rh) * 17 + jj];
           }
-          __syncwarp();
         }
+        __syncwarp();
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[b])) : "memory");
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TN));
   }
 }
 
@@ -287,10 +300,10 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(TcArgs p) {
 // sums of squares.  Here the leading product x1*y1 goes to a "main" accumulator and the
 // five cross products to a "side" accumulator, each chain covers one 512-row
 // sub-chunk, and two TMEM buffer pairs alternate: while the MMA thread fills one pair,
-// eight epilogue warps drain the other into FP64 registers (one row and 64 columns per
-// thread).  FP64 sums are added to C once per CTA.
+// eight epilogue warps drain the other into compensated FP32 (hi, lo) register pairs
+// (one row and 64 columns per thread).  The pairs are added to C in FP64 once per CTA.
 constexpr int GN = 128;                                  // N tile of the Gram kernel
-constexpr int G_SUB_KB = 16;                             // K blocks per FP32 chain (512 rows)
+constexpr int G_SUB_KB = 8;                              // K blocks per FP32 chain (256 rows)
 constexpr int G_STAGES = 4;
 constexpr int G_A_BYTES = NPIECE * BLK_ELEMS * 2;        // 24 KB
 constexpr int G_STAGE_BYTES = 2 * G_A_BYTES;             // 48 KB
@@ -413,9 +426,14 @@ __global__ void __launch_bounds__(320, 1) tc_gram_kernel(GramArgs p) {
     // epilogue warps 2..9: TMEM lane quadrant warp % 4, column half (warp - 2) / 4
     const int q = warp & 3, h = (warp - 2) >> 2;
     const int row = q * 32 + lane;
-    double acc[64];
+    // compensated FP32 sum (hi, lo) per element: ~48 significant bits at FP32 speed
+    // (GB300 runs FP64 at 1/70 of FP32, too slow for a drain every 256 rows)
+    float hi[64], lo[64];
 #pragma unroll
-    for (int c = 0; c < 64; c++) acc[c] = 0.0;
+    for (int c = 0; c < 64; c++) {
+      hi[c] = 0.f;
+      lo[c] = 0.f;
+    }
     bool ok = true;
     for (int c = 0; c < nsub; c++) {
       const int b = c & 1;
@@ -424,11 +442,21 @@ __global__ void __launch_bounds__(320, 1) tc_gram_kernel(GramArgs p) {
       tc_fence_after();
       const uint32_t lane_off = (uint32_t)(q * 32) << 16;
 #pragma unroll
-      for (int part = 0; part < 4; part++) {
-        float v[32];
-        tmem_ld32(tmem + lane_off + b * 256 + (part & 1) * 128 + h * 64 + (part >> 1) * 32, v);
+      for (int qt = 0; qt < 4; qt++) {
+        float vm[16], vs[16];
+        tmem_ld16(tmem + lane_off + b * 256 + h * 64 + qt * 16, vm);        // main accumulator
+        tmem_ld16(tmem + lane_off + b * 256 + 128 + h * 64 + qt * 16, vs);  // side accumulator
 #pragma unroll
-        for (int e = 0; e < 32; e++) acc[(part >> 1) * 32 + e] += (double)v[e];
+        for (int e = 0; e < 16; e++) {
+          // TwoSum (Knuth): hi + v = s + err exactly
+          const int c = qt * 16 + e;
+          const float v = vm[e] + vs[e];
+          const float s2 = hi[c] + v;
+          const float bp = s2 - hi[c];
+          const float err = (hi[c] - (s2 - bp)) + (v - bp);
+          hi[c] = s2;
+          lo[c] += err;
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -439,7 +467,8 @@ __global__ void __launch_bounds__(320, 1) tc_gram_kernel(GramArgs p) {
 #pragma unroll
       for (int e = 0; e < 64; e++) {
         const int j = nt * GN + h * 64 + e;
-        if (j < p.n && (!p.symmetric || j >= i)) atomicAdd(p.C + i + (int64_t)j * p.ldc, p.scale * acc[e]);
+        if (j < p.n && (!p.symmetric || j >= i))
+          atomicAdd(p.C + i + (int64_t)j * p.ldc, p.scale * ((double)hi[e] + (double)lo[e]));
       }
     }
   }
@@ -549,6 +578,16 @@ __global__ void __launch_bounds__(256) split_Q_kernel(const double* __restrict__
     ((uint4*)(P1 + base))[e] = ((const uint4*)sp[1])[e];
     ((uint4*)(P2 + base))[e] = ((const uint4*)sp[2])[e];
   }
+}
+
+// out[r][j] += A[r][j]
+__global__ void add_rows_kernel(const float* __restrict__ A, int64_t lda, float* __restrict__ out, int64_t ldo,
+                                int64_t rows, int n) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * n) return;
+  const int64_t r = idx / n;
+  const int j = (int)(idx - r * n);
+  out[r * ldo + j] += A[r * lda + j];
 }
 
 __global__ void mirror_upper_kernel(double* C, int k, int64_t ldc) {
@@ -734,17 +773,21 @@ cudaError_t launch_rotate_tc(const float* A, int64_t lda, const double* Q, int64
   a.m_tiles = cdiv(rows, TM);
   a.n_tiles = cdiv(kout, TN);
   a.kb_total = nkb;
-  a.kb_per_cta = nkb;
-  a.m = (int)std::min<int64_t>(rows, 1 << 30);
   a.n = kout;
-  a.mode = 1;
   a.out = out;
   a.ldo = ldo;
-  a.addA = add_identity_input ? A : nullptr;
-  a.lda_add = lda;
   a.rows = rows;
-  dim3 grid(a.m_tiles * a.n_tiles, 1);
-  tc_gemm_kernel<<<grid, 192, SMEM_BYTES, st>>>(a), count_launch();
+  int sms = 152;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int ntiles = a.m_tiles * a.n_tiles;
+  tc_gemm_kernel<<<std::min(ntiles, sms), 192, SMEM_BYTES, st>>>(a), count_launch();
+  if (add_identity_input) {
+    // out = A (Q - I) + A
+    add_rows_kernel<<<cdiv(rows * (int64_t)kout, 256), 256, 0, st>>>(A, lda, out, ldo, rows, kout), count_launch();
+  }
   return cudaGetLastError();
 }
 

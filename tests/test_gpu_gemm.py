@@ -50,6 +50,8 @@ def test_gram_symmetric(kscf, mode):
     ref = A64.T @ A64
     assert np.array_equal(C, C.T)
     assert np.all(np.abs(C - ref) <= 2e-6 * (np.abs(A64).T @ np.abs(A64)))
+    # sums of squares expose any systematic truncation of long FP32 accumulation chains
+    assert np.max(np.abs(np.diag(C) - np.diag(ref)) / np.diag(ref)) < 5e-7
 
 
 @pytest.mark.parametrize("mode", MODES)

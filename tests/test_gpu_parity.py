@@ -269,10 +269,11 @@ def test_chefsi_f32_tracks_oracle(kscf, system, mode):
 
 
 @pytest.mark.parametrize("k,ldpad,block", [(13, 16, 0), (19, 24, 0), (19, 24, 8), (32, 32, 16), (40, 64, 0),
-                                           (70, 96, 64), (33, 64, 0)])
+                                           (70, 96, 64), (33, 64, 0), (13, 18, 0), (30, 34, 0)])
 def test_f32_brick_kernel_paths(kscf, system, k, ldpad, block):
-    """Row strides padded to a multiple of 8 select the staged FP32 brick kernel (brick
-    8); compared with the oracle like the generic path."""
+    """Padded row strides select the FP32 brick kernels (brick 8): the TMA kernel for
+    strides that are multiples of 4, the cp.async kernel otherwise; compared with the
+    oracle like the generic path."""
     if system["brick"] != 8:
         pytest.skip("the staged kernel is built for 8^3 bricks")
     from oracle.chefsi import chebyshev_filter, spectral_upper_bound
