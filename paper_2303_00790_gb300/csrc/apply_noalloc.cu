@@ -83,6 +83,7 @@ extern "C" int kscf_hamiltonian_apply_noalloc(const kscf_ham* ham, void* Y, int6
   // every coefficient the step kernel reads is written by the gather first, so the
   // array needs no clearing between calls
   KSCF_CUDA_TRY(kscf::launch_zero_rows(H, Y, ld_y, k, dtype, st));
+  KSCF_CUDA_TRY(kscf::launch_zero_rows(H, HY, ld_hy, k, dtype, st));
   KSCF_CUDA_TRY(kscf::launch_kb_gather(H, Y, ld_y, k, dtype, coef, kscf::coef_ld(k), st));
   KSCF_CUDA_TRY(kscf::launch_cheb_step(H, Y, ld_y, nullptr, 0, HY, ld_hy, k, (int)(ld_y < ld_hy ? ld_y : ld_hy), dtype,
                                        1.0, 0.0, 0.0, coef, kscf::coef_ld(k), st));

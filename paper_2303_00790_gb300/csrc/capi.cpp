@@ -350,6 +350,7 @@ extern "C" int kscf_hamiltonian_apply(const kscf_ham* ham, void* Y, int64_t ld_y
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   KSCF_CUDA_TRY(launch_zero_rows(H, Y, ld_y, k, dtype, st));
+  KSCF_CUDA_TRY(launch_zero_rows(H, HY, ld_hy, k, dtype, st));
   KSCF_CUDA_TRY(launch_kb_gather(H, Y, ld_y, k, dtype, work, coef_ld(k), st));
   KSCF_CUDA_TRY(launch_cheb_step(H, Y, ld_y, nullptr, 0, HY, ld_hy, k, (int)std::min<int64_t>(ld_y, ld_hy), dtype,
                                  1.0, 0.0, 0.0, work, coef_ld(k), st));
@@ -384,6 +385,7 @@ extern "C" int kscf_chebyshev_filter(const kscf_ham* ham, void* X, int64_t ld, i
     // columns usable from the block start in every row (lets the FP32 brick kernel read
     // whole 8-vector chunks when the row has room)
     const int avail_x = (int)std::min<int64_t>(ld - c0, 1 << 30), avail_b = (int)wpad;
+    KSCF_CUDA_TRY(launch_zero_rows(H, buf, wpad, wb, dtype, st));
     // Y_1 = (sigma_1/e)(H X - c X)   -> buf
     KSCF_CUDA_TRY(launch_kb_gather(H, Xb, ld, wb, dtype, coef, wpad, st));
     KSCF_CUDA_TRY(launch_cheb_step(H, Xb, ld, nullptr, 0, buf, wpad, wb, std::min(avail_x, avail_b), dtype,
@@ -475,6 +477,7 @@ extern "C" int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int 
     const int wb = std::min(p.w, k - c0);
     char* Xb = (char*)X + (size_t)c0 * es;
     const int64_t wpad = coef_ld(wb);
+    KSCF_CUDA_TRY(launch_zero_rows(H, hxb, wpad, wb, dtype, st));
     KSCF_CUDA_TRY(launch_kb_gather(H, Xb, ld, wb, dtype, coef, wpad, st));
     KSCF_CUDA_TRY(launch_cheb_step(H, Xb, ld, nullptr, 0, hxb, wpad, wb,
                                    (int)std::min<int64_t>(ld - c0, wpad), dtype, 1.0, 0.0, 0.0, coef, wpad, st));

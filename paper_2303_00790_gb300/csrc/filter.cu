@@ -145,19 +145,23 @@ __device__ __forceinline__ float2 ld2(const float* base, int64_t slot, int64_t l
 }
 }  // namespace
 
-// NV = 8 vectors per CTA: a point slot in shared memory is 8 floats (32 bytes); the 64
-// lines of a pass are spread over 256 threads, 4 lanes per line, two vectors per lane.
+// NV vectors per CTA (8 or 16): a point slot in shared memory is NV floats; the 64 lines
+// of a pass are spread over 64 * NV/2 threads, NV/2 lanes per line, two vectors per lane.
+// The point slots are XOR-swizzled so that the lines of one warp read distinct banks in
+// every pass (x ^ (y & 3) for 32-byte slots, x ^ (y & 1) for 64-byte slots).
 // VEC: rows are read with vector loads (ld and column offsets multiples of 4).
 template <int NV, bool VEC>
-__global__ void __launch_bounds__(NV * 32, 3)
+__global__ void __launch_bounds__(NV * 32, NV == 8 ? 3 : 2)
     cheb_step_brick8(StepArgs<float> a, int nchunk, const uint16_t* __restrict__ entry_lslot) {
-  static_assert(NV == 8, "the swizzled shared layout assumes 32-byte point slots");
+  static_assert(NV == 8 || NV == 16, "point slots of 32 or 64 bytes");
   constexpr int VPL = NV / 2;       // lanes per line
   constexpr int NT = 64 * VPL;      // threads
   constexpr int Q4 = NV / 4;        // float4 per point slot
   const int64_t cld = a.cld;
   extern __shared__ float4 sb4[];
   float* sm = (float*)sb4;
+  // brick-major order: CTAs follow the Hilbert order of the bricks, the column chunks of
+  // one brick side by side (neighbouring bricks, and so the halo rows, stay close in L2)
   const int brick = blockIdx.x / nchunk, chunk = blockIdx.x - (blockIdx.x / nchunk) * nchunk;
   const int v0 = chunk * NV;
   const int tid = threadIdx.x;
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(NV * 32, 3)
   const int nbx0 = __ldg(a.nbr + (int64_t)brick * 6 + 0), nbx1 = __ldg(a.nbr + (int64_t)brick * 6 + 1);
   const int nby0 = __ldg(a.nbr + (int64_t)brick * 6 + 2), nby1 = __ldg(a.nbr + (int64_t)brick * 6 + 3);
   const int nbz0 = __ldg(a.nbr + (int64_t)brick * 6 + 4), nbz1 = __ldg(a.nbr + (int64_t)brick * 6 + 5);
-  auto core = [](int x, int y, int z) { return sb_core(x, y, z); };
+  auto core = [](int x, int y, int z) { return NV == 8 ? sb_core(x, y, z) : (z * 8 + y) * 8 + (x ^ (y & 1)); };
 
   // ---- stage the brick core: 512 rows x NV floats ----
   for (int t = tid; t < 512 * Q4; t += NT) {
@@ -225,20 +229,38 @@ __global__ void __launch_bounds__(NV * 32, 3)
     }
   }
   __syncthreads();
-  // ---- nonlocal scatter: the brick's entries are one contiguous range ----
+  // ---- nonlocal scatter: the brick's entries are one contiguous range; four entries
+  //      per thread and iteration, their loads issued before any is used ----
   {
     const int64_t e0 = __ldg(a.kb_ptr + b0), e1 = __ldg(a.kb_ptr + b0 + 512);
-    for (int64_t e = e0 + line; e < e1; e += 64) {
-      const int ls = __ldg(entry_lslot + e);
-      const float4 ch = __ldg((const float4*)(a.kb_chi + 4 * e));
-      const float* cf = a.coef + (int64_t)__ldg(a.kb_atom + e) * 4 * cld + vl;
-      float2 c = f2_mul(f2(ch.x), make_float2(cf[0], cf[1]));
-      c = f2_fma(f2(ch.y), make_float2(cf[cld], cf[cld + 1]), c);
-      c = f2_fma(f2(ch.z), make_float2(cf[2 * cld], cf[2 * cld + 1]), c);
-      c = f2_fma(f2(ch.w), make_float2(cf[3 * cld], cf[3 * cld + 1]), c);
-      float* acc = (float*)&a2[(SB_ACC + core(ls & 7, (ls >> 3) & 7, ls >> 6)) * VPL];
-      atomicAdd(acc, c.x);
-      atomicAdd(acc + 1, c.y);
+    for (int64_t eb = e0 + line; eb < e1; eb += 4 * 64) {
+      int ls[4];
+      float4 ch[4];
+      const float* cf[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const int64_t e = eb + u * 64;
+        const bool ok = e < e1;
+        ls[u] = ok ? __ldg(entry_lslot + e) : -1;
+        ch[u] = ok ? __ldg((const float4*)(a.kb_chi + 4 * e)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        cf[u] = a.coef + (ok ? (int64_t)__ldg(a.kb_atom + e) * 4 * cld : 0) + vl;
+      }
+      float2 cv[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; u++)
+#pragma unroll
+        for (int l = 0; l < 4; l++) cv[u][l] = make_float2(cf[u][l * cld], cf[u][l * cld + 1]);
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        if (ls[u] < 0) continue;
+        float2 c = f2_mul(f2(ch[u].x), cv[u][0]);
+        c = f2_fma(f2(ch[u].y), cv[u][1], c);
+        c = f2_fma(f2(ch[u].z), cv[u][2], c);
+        c = f2_fma(f2(ch[u].w), cv[u][3], c);
+        float* acc = (float*)&a2[(SB_ACC + core(ls[u] & 7, (ls[u] >> 3) & 7, ls[u] >> 6)) * VPL];
+        atomicAdd(acc, c.x);
+        atomicAdd(acc + 1, c.y);
+      }
     }
   }
   // ---- z pass: line (x, y); potential, recurrence, store ----
@@ -258,17 +280,16 @@ __global__ void __launch_bounds__(NV * 32, 3)
 #pragma unroll
     for (int z = 0; z < 8; z++) {
       const int64_t s = b0 + z * 64 + y * 8 + x;
-      float2 res = zero2;
-      if (__ldg(a.mask + s)) {
-        const float2 yc = w[6 + z];
-        float2 hy = f2_add(a2[(SB_ACC + core(x, y, z)) * VPL], line_terms<false>(w, 6 + z, st));
-        hy = f2_fma(f2(__ldg(a.V + s)), yc, hy);
-        res = f2_mul(alpha, f2_fma(negc, yc, hy));
-        if (a.prev) {
-          const float2 pv = VEC ? *(const float2*)(a.prev + s * a.ld_prev + vl)
-                                : make_float2(a.prev[s * a.ld_prev + vl], a.prev[s * a.ld_prev + vl + 1]);
-          res = f2_fma(beta, pv, res);
-        }
+      // padding rows are left untouched: they are zero in every buffer of the recurrence
+      if (!__ldg(a.mask + s)) continue;
+      const float2 yc = w[6 + z];
+      float2 hy = f2_add(a2[(SB_ACC + core(x, y, z)) * VPL], line_terms<false>(w, 6 + z, st));
+      hy = f2_fma(f2(__ldg(a.V + s)), yc, hy);
+      float2 res = f2_mul(alpha, f2_fma(negc, yc, hy));
+      if (a.prev) {
+        const float2 pv = VEC ? *(const float2*)(a.prev + s * a.ld_prev + vl)
+                              : make_float2(a.prev[s * a.ld_prev + vl], a.prev[s * a.ld_prev + vl + 1]);
+        res = f2_fma(beta, pv, res);
       }
       float* o = a.out + s * a.ld_out + vl;
       if (st0 && st1 && VEC) {
@@ -369,7 +390,8 @@ __global__ void __launch_bounds__(256, 2)
     const int64_t s = b0 + z * 64 + zy * 8 + zx;
     mk |= (uint32_t)__ldg(a.mask + s) << z;
     vv[z] = __ldg(a.V + s);
-    pv[z] = (a.prev && pv_ok) ? *(const float2*)(a.prev + s * a.ld_prev + vl) : make_float2(0.f, 0.f);
+    pv[z] = (a.prev && pv_ok && ((mk >> z) & 1u)) ? *(const float2*)(a.prev + s * a.ld_prev + vl)
+                                                  : make_float2(0.f, 0.f);
   }
   {
     const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
@@ -461,13 +483,12 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
     for (int z = 0; z < 8; z++) {
       const int64_t s = b0 + z * 64 + y * 8 + x;
-      float2 res = make_float2(0.f, 0.f);
-      if ((mk >> z) & 1u) {
-        const float2 yc = w[6 + z];
-        float2 hy = f2_add(a2[sb_core(x, y, z) * 4], line_terms<false>(w, 6 + z, st));
-        hy = f2_fma(f2(vv[z]), yc, hy);
-        res = f2_fma(beta, pv[z], f2_mul(alpha, f2_fma(negc, yc, hy)));
-      }
+      // padding rows are left untouched: they are zero in every buffer of the recurrence
+      if (!((mk >> z) & 1u)) continue;
+      const float2 yc = w[6 + z];
+      float2 hy = f2_add(a2[sb_core(x, y, z) * 4], line_terms<false>(w, 6 + z, st));
+      hy = f2_fma(f2(vv[z]), yc, hy);
+      const float2 res = f2_fma(beta, pv[z], f2_mul(alpha, f2_fma(negc, yc, hy)));
       float* o = a.out + s * a.ld_out + vl;
       if (st0 && st1) {
         *(float2*)o = res;
@@ -600,6 +621,8 @@ cudaError_t launch_kb_gather(const Ham& H, const void* Y, int64_t ld, int w, int
 }
 
 
+static bool g_brick16_attr[64] = {false};
+
 template <typename T>
 static cudaError_t step_t(const Ham& H, const void* in, int64_t ld_in, const void* prev, int64_t ld_prev,
                           void* out, int64_t ld_out, int w, int wavail, double alpha, double beta, double c,
@@ -632,12 +655,34 @@ static cudaError_t step_t(const Ham& H, const void* in, int64_t ld_in, const voi
     const bool vec = (ld_in % 4 == 0) && (ld_out % 4 == 0) && (!prev || ld_prev % 4 == 0) && (cld % 2 == 0) &&
                      ((uintptr_t)in % 16 == 0) && ((uintptr_t)out % 16 == 0) &&
                      (!prev || (uintptr_t)prev % 16 == 0);
-    const int nchunk = w8 / 8;
-    const unsigned grid = (unsigned)(H.grid.n_bricks * nchunk);
-    if (vec)
-      cheb_step_brick8<8, true><<<grid, 256, SB_TOTAL * 32, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
-    else
-      cheb_step_brick8<8, false><<<grid, 256, SB_TOTAL * 32, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
+    const int w16 = (w + 15) / 16 * 16;
+    if (w >= 16 && wavail >= w16 && cld >= w16) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (dev >= 0 && dev < 64 && !g_brick16_attr[dev]) {
+        // 64 KB of dynamic shared memory needs the opt-in attribute
+        cudaError_t e = cudaFuncSetAttribute(cheb_step_brick8<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SB_TOTAL * 64);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(cheb_step_brick8<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   SB_TOTAL * 64);
+        if (e != cudaSuccess) return e;
+        g_brick16_attr[dev] = true;
+      }
+      const int nchunk = w16 / 16;
+      const unsigned grid = (unsigned)(H.grid.n_bricks * nchunk);
+      if (vec)
+        cheb_step_brick8<16, true><<<grid, 512, SB_TOTAL * 64, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
+      else
+        cheb_step_brick8<16, false><<<grid, 512, SB_TOTAL * 64, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
+    } else {
+      const int nchunk = w8 / 8;
+      const unsigned grid = (unsigned)(H.grid.n_bricks * nchunk);
+      if (vec)
+        cheb_step_brick8<8, true><<<grid, 256, SB_TOTAL * 32, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
+      else
+        cheb_step_brick8<8, false><<<grid, 256, SB_TOTAL * 32, st>>>(af, nchunk, H.d_kb_entry_lslot), count_launch();
+    }
     return cudaGetLastError();
   }
   // 2) TMA brick kernel: rows without spare width (columns past wavail arrive as zeros);

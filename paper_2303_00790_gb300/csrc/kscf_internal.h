@@ -86,6 +86,8 @@ cudaError_t launch_zero_rows(const Ham& H, void* X, int64_t ld, int k, int dtype
 // read whole 32-vector chunks
 cudaError_t launch_kb_gather(const Ham& H, const void* Y, int64_t ld, int w, int dtype, void* coef,
                              int64_t cld, cudaStream_t st);
+// The FP32 brick kernels do not write padding rows of `out`: callers keep padding rows
+// zero in every buffer they pass (launch_zero_rows once per buffer).
 // wavail: columns readable and writable from in/prev/out in every row (>= w); the FP32
 // brick kernel is used when wavail and cld cover round_up8(w) (32-vector CTAs when they
 // cover round_up32(w))
