@@ -66,3 +66,28 @@ class Hamiltonian:
     def dense(self) -> np.ndarray:
         """Dense matrix (tiny grids only)."""
         return self.apply(np.eye(self.n))
+
+
+def apply_at_rows(grid, rows, V_rows, P, E, Y, M: int = 6):
+    """(H Y)[rows] by the definition, for sampled rows of a large grid: the stencil from
+    the row's axis neighbours (zero outside the domain), V at the rows, and the nonlocal
+    term P[rows] (E h^3 (P^T Y)).  Y holds all grid points (lexicographic) x columns."""
+    w = weights_float(M)
+    h2 = grid.h * grid.h
+    rows = np.asarray(rows, dtype=np.int64)
+    Y = np.asarray(Y, dtype=np.float64)
+    out = (-0.5 * 3.0 * w[0] / h2) * Y[rows]
+    for axis in range(3):
+        for k in range(1, M + 1):
+            for sgn in (-1, 1):
+                off = np.zeros(3, dtype=np.int64)
+                off[axis] = sgn * k
+                nb = grid.index_of(grid.ijk[rows] + off[None, :])
+                ok = nb >= 0
+                out[ok] += (-0.5 * w[k] / h2) * Y[nb[ok]]
+    out += np.asarray(V_rows, dtype=np.float64)[:, None] * Y[rows]
+    if P is not None and P.shape[1] > 0:
+        Pc = P.tocsc()
+        coef = (np.asarray(E) * grid.h ** 3)[:, None] * (Pc.T @ Y)
+        out += P.tocsr()[rows] @ coef
+    return out

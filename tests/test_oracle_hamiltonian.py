@@ -143,3 +143,12 @@ def test_upper_bound_is_above_spectrum(species):
     b = spectral_upper_bound(H)
     assert b >= lam_max
     assert b - lam_max < 0.3 * (b - V.min())      # and not absurdly loose
+
+
+def test_apply_at_rows_equals_full_apply(species):
+    from oracle.hamiltonian import apply_at_rows
+    g, pos, z, V, P, E, _ = _small_system(species)
+    H = Hamiltonian(g, V, P, E)
+    Y = np.random.default_rng(1).standard_normal((g.n, 3))
+    rows = np.array([0, 5, 100, g.n - 1, 1234])
+    assert np.max(np.abs(apply_at_rows(g, rows, V[rows], P, E, Y) - H.apply(Y)[rows])) < 1e-12
