@@ -1,0 +1,215 @@
+"""Self-consistent field loop (oracle, float64) -- test infrastructure only.
+
+Kohn-Sham DFT with the LDA (Computational details: Ceperley-Alder correlation as
+parametrised by Perdew & Zunger 1981) at fixed ions:
+
+  V_eff = V_ion + V_H[rho] + V_xc[rho]
+  V_H    solves  -Lap_h V_H = 4 pi rho  on the domain (order-12 FD Laplacian); the
+         values the stencil needs outside the sphere come from the multipole expansion
+         (monopole, dipole, quadrupole) of rho about the grid centre; conjugate
+         gradients in float64
+  V_xc   Slater exchange + PZ81 correlation (unpolarised, Hartree units)
+  mixing Anderson mixing of the input potential (the Broyden-type quasi-Newton scheme;
+         history m, linear step alpha)
+  SRE    sqrt(h^3 sum_p rho_p (V_out - V_in)_p^2), reported in Ry (x 2); stop below 1e-4 Ry
+  CheFSI four filter/Cholesky-QR/Rayleigh-Ritz iterations in the first SCF step, one in
+         every later step (the schedule the paper states)
+
+The starting potential is the superposition of neutral atoms: Gaussian valence densities
+Z/(pi^{3/2} r_a^3) exp(-r^2/r_a^2) per atom, V_in = V_ion + V_H[rho_at] + V_xc[rho_at].
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.sparse.linalg as spla
+
+from . import chefsi as cf
+from .fd import weights_float
+from .hamiltonian import Hamiltonian, kinetic_matrix
+
+# Perdew-Zunger 1981 correlation of the Ceperley-Alder gas, unpolarised (Hartree)
+PZ_GAMMA, PZ_BETA1, PZ_BETA2 = -0.1423, 1.0529, 0.3334
+PZ_A, PZ_B, PZ_C, PZ_D = 0.0311, -0.048, 0.0020, -0.0116
+RHO_FLOOR = 1e-14
+
+ATOM_DENSITY_RADIUS = {14: 1.2, 1: 0.7}   # Gaussian widths of the starting densities (bohr)
+
+
+def lda_xc(rho: np.ndarray):
+    """(eps_xc, V_xc) per point for density rho (LDA: Slater + PZ81)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    eps = np.zeros_like(rho)
+    v = np.zeros_like(rho)
+    m = rho > RHO_FLOOR
+    r = rho[m]
+    rs = (3.0 / (4.0 * math.pi * r)) ** (1.0 / 3.0)
+    ex = -0.75 * (3.0 * r / math.pi) ** (1.0 / 3.0)
+    vx = (4.0 / 3.0) * ex
+    ec = np.empty_like(r)
+    vc = np.empty_like(r)
+    hi = rs >= 1.0
+    s = np.sqrt(rs[hi])
+    den = 1.0 + PZ_BETA1 * s + PZ_BETA2 * rs[hi]
+    ec[hi] = PZ_GAMMA / den
+    vc[hi] = ec[hi] * (1.0 + 7.0 / 6.0 * PZ_BETA1 * s + 4.0 / 3.0 * PZ_BETA2 * rs[hi]) / den
+    lo = ~hi
+    x = rs[lo]
+    lnx = np.log(x)
+    ec[lo] = PZ_A * lnx + PZ_B + PZ_C * x * lnx + PZ_D * x
+    vc[lo] = PZ_A * lnx + (PZ_B - PZ_A / 3.0) + 2.0 / 3.0 * PZ_C * x * lnx + (2.0 * PZ_D - PZ_C) / 3.0 * x
+    eps[m] = ex + ec
+    v[m] = vx + vc
+    return eps, v
+
+
+def atomic_density(points, atom_pos, atom_z, species):
+    """Superposition of Gaussian valence densities (start of the SCF)."""
+    table = {int(s["z_number"]): s for s in species}
+    rho = np.zeros(len(points))
+    for pos, z in zip(atom_pos, atom_z):
+        ra = ATOM_DENSITY_RADIUS[int(z)]
+        zv = table[int(z)]["z_valence"]
+        d = points - pos
+        r2 = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]
+        rho += zv / (math.pi ** 1.5 * ra ** 3) * np.exp(-r2 / (ra * ra))
+    return rho
+
+
+def multipole_potential(rho: np.ndarray, grid, targets: np.ndarray) -> np.ndarray:
+    """Potential of rho at target points from its multipoles about the grid centre:
+    Q/r + p.r/r^3 + (1/2) sum_ij Q_ij r_i r_j / r^5,  Q_ij = int rho (3 x_i x_j - r^2 d_ij)."""
+    h3 = grid.h ** 3
+    x = grid.h * grid.ijk.astype(np.float64)
+    q = h3 * rho.sum()
+    p = h3 * (rho[:, None] * x).sum(0)
+    r2s = (x * x).sum(1)
+    Qm = h3 * (3.0 * np.einsum("n,ni,nj->ij", rho, x, x) - np.eye(3) * (rho * r2s).sum())
+    t = targets - grid.center
+    r2 = (t * t).sum(1)
+    r = np.sqrt(r2)
+    return q / r + (t @ p) / (r2 * r) + 0.5 * np.einsum("ni,ij,nj->n", t, Qm, t) / (r2 * r2 * r)
+
+
+def ghost_rhs(grid, M: int = 6):
+    """Ghost points (outside the domain, within M steps of a domain point along an axis)
+    and the coupling matrix G with (Lap_h V)_p = (Lap_h restricted V)_p + (G V_ghost)_p."""
+    import scipy.sparse as sp
+    w = weights_float(M)
+    h2 = grid.h * grid.h
+    rows, keys = [], []
+    vals = []
+    for axis in range(3):
+        for k in range(1, M + 1):
+            for sgn in (-1, 1):
+                off = np.zeros(3, dtype=np.int64)
+                off[axis] = sgn * k
+                q = grid.ijk + off[None, :]
+                outside = grid.index_of(q) < 0
+                idx = np.nonzero(outside)[0]
+                rows.append(idx)
+                keys.append(q[idx])
+                vals.append(np.full(len(idx), w[k] / h2))
+    allq = np.concatenate(keys)
+    uq, inv = np.unique(allq, axis=0, return_inverse=True)
+    G = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), inv.ravel())), shape=(grid.n, len(uq)))
+    return uq, G
+
+
+class Poisson:
+    """-Lap_h V = 4 pi rho with multipole values outside the sphere (conjugate gradients)."""
+
+    def __init__(self, grid, M: int = 6):
+        self.grid = grid
+        self.A = 2.0 * kinetic_matrix(grid, M)       # -Lap_h restricted to the domain (SPD)
+        self.ghost_ijk, self.G = ghost_rhs(grid, M)
+        self.ghost_xyz = grid.center[None, :] + grid.h * self.ghost_ijk.astype(np.float64)
+
+    def solve(self, rho: np.ndarray, x0=None, tol: float = 1e-12):
+        vg = multipole_potential(rho, self.grid, self.ghost_xyz)
+        b = 4.0 * math.pi * rho + self.G @ vg
+        x, info = spla.cg(self.A, b, x0=x0, rtol=tol, atol=0.0, maxiter=20000)
+        if info != 0:
+            raise RuntimeError("Poisson CG did not converge")
+        return x
+
+
+class Anderson:
+    """Anderson mixing of the input potential: V_next = V_in + a F - sum_j g_j (dV_j + a dF_j),
+    g = argmin |F - sum_j g_j dF_j|, F = V_out - V_in, history of the last m differences."""
+
+    def __init__(self, alpha: float = 0.3, history: int = 8):
+        self.alpha = alpha
+        self.m = history
+        self.prev = None          # (V_in, F) of the previous step
+        self.dV, self.dF = [], []
+
+    def step(self, v_in: np.ndarray, f: np.ndarray) -> np.ndarray:
+        if self.prev is not None:
+            self.dV.append(v_in - self.prev[0])
+            self.dF.append(f - self.prev[1])
+            if len(self.dV) > self.m:
+                self.dV.pop(0)
+                self.dF.pop(0)
+        self.prev = (v_in.copy(), f.copy())
+        nxt = v_in + self.alpha * f
+        if self.dF:
+            DF = np.stack(self.dF, 1)
+            DV = np.stack(self.dV, 1)
+            g = np.linalg.solve(DF.T @ DF, DF.T @ f)
+            nxt = nxt - (DV + self.alpha * DF) @ g
+        return nxt
+
+
+def scf(atom_pos, atom_z, species, radius, h, k, degree, X0, max_steps=40, sre_tol_ry=1e-4,
+        first_iters=4, alpha=0.3, history=8, center=None):
+    """Run the SCF; returns a dict with per-step reports and the final state."""
+    from .grid import sphere_grid
+    from .potential import kb_projectors, local_potential
+    from workloads.cluster import n_electrons
+
+    atom_pos = np.asarray(atom_pos, dtype=np.float64)
+    c = atom_pos[0] if center is None else np.asarray(center)
+    g = sphere_grid(c, radius, h)
+    pts = g.points()
+    v_ion = local_potential(pts, atom_pos, atom_z, species)
+    P, E, _ = kb_projectors(g, atom_pos, atom_z, species)
+    pois = Poisson(g)
+    ne = n_electrons(atom_z)
+    nocc = ne // 2
+    occ = np.full(nocc, 2.0)
+    rho0 = atomic_density(pts, atom_pos, atom_z, species)
+    vh = pois.solve(rho0)
+    _, vxc = lda_xc(rho0)
+    v_in = v_ion + vh + vxc
+    H = Hamiltonian(g, v_in, P, E)
+    X, _ = cf.cholesky_qr(np.array(X0, dtype=np.float64), H.h3)
+    lam, X, _ = cf.rayleigh_ritz(H, X, H.h3)
+    mixer = Anderson(alpha, history)
+    reports = []
+    vh_prev = vh
+    for step in range(1, max_steps + 1):
+        H = Hamiltonian(g, v_in, P, E)
+        b = cf.spectral_upper_bound(H)
+        for _ in range(first_iters if step == 1 else 1):
+            Y = cf.chebyshev_filter(H, X, degree, lam[-1], b, lam[0])
+            X, _ = cf.cholesky_qr(Y, H.h3)
+            lam, X, _ = cf.rayleigh_ritz(H, X, H.h3)
+        rho = cf.density(X, occ)
+        vh = pois.solve(rho, x0=vh_prev)
+        vh_prev = vh
+        eps, vxc = lda_xc(rho)
+        v_out = v_ion + vh + vxc
+        f = v_out - v_in
+        sre = 2.0 * math.sqrt(H.h3 * float(np.sum(rho * f * f)))
+        e_band = float(np.dot(occ, lam[:nocc]))
+        e_tot = (e_band - H.h3 * float(np.dot(rho, v_in - v_ion)) + 0.5 * H.h3 * float(np.dot(rho, vh))
+                 + H.h3 * float(np.dot(rho, eps)))
+        reports.append({"step": step, "sre_ry": sre, "e_band": e_band, "e_total": e_tot,
+                        "homo": float(lam[nocc - 1]), "lumo": float(lam[nocc]) if k > nocc else float("nan"),
+                        "electrons": H.h3 * float(rho.sum()), "lam": lam.copy()})
+        if sre < sre_tol_ry:
+            break
+        v_in = mixer.step(v_in, f)
+    return {"reports": reports, "X": X, "lam": lam, "rho": rho, "v_in": v_in, "grid": g, "n_occ": nocc}
