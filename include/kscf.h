@@ -272,6 +272,120 @@ int kscf_gemm_workspace_size(int op, int64_t rows, int m, int n, int dtype, int 
  * rayleigh_ritz check the GEMM word themselves; filter callers check after the filter. */
 int kscf_check_status(void);
 
+/* ---------------------------------------------------------------------------------
+ * Self-consistent field (Computational details: Kohn-Sham DFT with the LDA,
+ * Ceperley-Alder correlation as parametrised by Perdew & Zunger; SCF stopped when the
+ * self-consistent residual error falls below 1e-4 Ry; four CheFSI iterations in the
+ * first SCF step, one in each later step).  Everything below runs on the device in
+ * FP64 except the CheFSI filter/Gram arithmetic, which follows params.dtype/gemm_mode.
+ *
+ *   V_eff = V_ion + V_H[rho] + V_xc[rho]
+ *   V_ion  the Hamiltonian's V_loc as built by kscf_build_hamiltonian
+ *   V_H    -Lap_h V_H = 4 pi rho on the domain (the same order-12 Laplacian as H); the
+ *          values the stencil needs outside the sphere come from the monopole, dipole
+ *          and quadrupole of rho about the grid centre; conjugate gradients in FP64 until
+ *          |r| < poisson_rtol |b|, warm-started from the previous V_H
+ *   V_xc   Slater exchange + PZ81 correlation, unpolarised (kscf_lda_xc)
+ *   rho    sum over the n_e/2 lowest Ritz vectors of 2 |x|^2 (n_e = sum of z_valence)
+ *   SRE    2 sqrt(h^3 sum_s rho_s (V_out - V_in)_s^2) in Ry, V_out = V_eff[rho_out]
+ *   E_tot  sum_i f_i lambda_i - h^3 sum rho (V_in - V_ion) + 1/2 h^3 sum rho V_H
+ *          + h^3 sum rho eps_xc       (band energy minus double counting)
+ *   mixing Anderson mixing of V_in: F = V_out - V_in, history of the last `history`
+ *          differences (dV_j, dF_j), g = argmin |F - sum_j g_j dF_j| by the normal
+ *          equations, V_in <- V_in + alpha F - sum_j g_j (dV_j + alpha dF_j).
+ *          (The paper names no mixing scheme; Anderson's is the Broyden-type method
+ *          used here.)
+ *   start  rho_0 = sum_a Z_a / (pi^{3/2} r_a^3) exp(-|r - R_a|^2 / r_a^2) (neutral-atom
+ *          Gaussian valence densities, r_a per species), V_in = V_ion + V_H[rho_0] +
+ *          V_xc[rho_0] (+ an optional caller correction dV, e.g. a learned one); X is
+ *          orthonormalised and one Rayleigh-Ritz step gives the first filter bounds.
+ *   step   kscf_set_potential(V_in); b = spectral upper bound; (4 or 1) x [filter with
+ *          a = lambda_max, a0 = lambda_min of the previous Ritz values; Cholesky-QR;
+ *          Rayleigh-Ritz]; rho; V_H; V_xc; SRE and energies; mixing unless converged.
+ * The kscf_scf handle borrows the Hamiltonian (it rewrites its potential) and the
+ * caller's X; both must outlive it.  It owns every other buffer (device memory about
+ * (14 + 2 history) * n_slots doubles plus the CheFSI work buffers).  All calls are
+ * synchronous (they read Ritz values and reductions on the host). */
+typedef struct kscf_scf kscf_scf;
+
+typedef struct kscf_scf_params {
+  int32_t k;               /* subspace size (n_e/2 occupied + buffer), > n_e/2 */
+  int32_t degree;          /* Chebyshev degree m */
+  int32_t dtype;           /* KSCF_F64, or KSCF_F32 for the mixed-precision path */
+  int32_t gemm_mode;       /* KSCF_GEMM_NATIVE or KSCF_GEMM_TENSOR (F32 only) */
+  int32_t block;           /* filter column block, 0 = all k */
+  int32_t first_iters;     /* CheFSI iterations in the first SCF step (paper: 4) */
+  int32_t history;         /* Anderson history, 1..8 */
+  int32_t poisson_maxiter; /* CG iteration cap per Hartree solve */
+  double mix_alpha;        /* Anderson linear step (0 < alpha <= 1) */
+  double sre_tol_ry;       /* converged when SRE < sre_tol_ry (paper: 1e-4 Ry) */
+  double poisson_rtol;     /* CG stop |r| < rtol |b| */
+} kscf_scf_params;
+
+typedef struct kscf_scf_report {
+  int32_t step;            /* SCF step number, 1-based (0 after kscf_scf_start) */
+  int32_t converged;       /* 1 when sre_ry < sre_tol_ry (V_in then kept, no mixing) */
+  int32_t poisson_iters;   /* CG iterations of this step's Hartree solve */
+  int32_t chefsi_iters;    /* filter/QR/RR iterations in this step */
+  double sre_ry;           /* SRE of this step (Ry) */
+  double e_band;           /* sum_i f_i lambda_i (Ha) */
+  double e_total;          /* Kohn-Sham total energy without ion-ion term (Ha) */
+  double homo, lumo;       /* lambda_{n_occ-1}, lambda_{n_occ} (Ha) */
+  double electrons;        /* h^3 sum rho */
+} kscf_scf_report;
+
+/* Creates the SCF state for the atoms the Hamiltonian was built from.  atoms/species
+ * as for kscf_build_hamiltonian (read during the call); start_radius[n_species]: the
+ * Gaussian width r_a (bohr) of each species' starting density.  X: caller device
+ * array n_slots x ld of params->dtype (ld >= k), used as the subspace from
+ * kscf_scf_start on.  Builds the ghost-point table of the Poisson problem on the host.
+ * stream: where every later call of this handle runs. */
+int kscf_scf_create(kscf_ham* ham, const kscf_atom* atoms, int n_atoms, const kscf_species* species,
+                    int n_species, const double* start_radius, const kscf_scf_params* params, void* X,
+                    int64_t ld, void* stream, kscf_scf** out);
+
+/* Starting point.  dv_start: device, n_slots doubles added to the superposition
+ * potential (NULL for none).  init_x != 0 fills X with kscf_random_subspace(seed) first;
+ * 0 keeps the caller's X.  Then Cholesky-QR and Rayleigh-Ritz; eigvals_host (k doubles
+ * or NULL) receives the Ritz values.  Clears the mixing history and the step count. */
+int kscf_scf_start(kscf_scf* scf, const double* dv_start, int init_x, uint64_t seed, double* eigvals_host);
+
+/* One SCF step (see above).  report receives its figures; eigvals_host (k doubles or
+ * NULL) the Ritz values.  After a converged step V_in is left as it was, so a further
+ * call repeats the step at the same potential. */
+int kscf_scf_step(kscf_scf* scf, kscf_scf_report* report, double* eigvals_host);
+
+/* Fields for kscf_scf_get (device, n_slots doubles each, slot order, 0 in padding). */
+#define KSCF_FIELD_RHO     0   /* density of the last step (start: rho_0) */
+#define KSCF_FIELD_V_IN    1   /* current input potential (after mixing) */
+#define KSCF_FIELD_V_H     2   /* Hartree potential of the last density */
+#define KSCF_FIELD_V_XC    3   /* exchange-correlation potential of the last density */
+#define KSCF_FIELD_V_ION   4   /* ionic (local pseudopotential) part */
+#define KSCF_FIELD_V_START 5   /* superposition starting potential, without dv_start */
+#define KSCF_FIELD_EPS_XC  6   /* exchange-correlation energy per electron */
+
+/* Copies one field into dst (device, n_slots doubles) on the handle's stream. */
+int kscf_scf_get(const kscf_scf* scf, int field, double* dst);
+
+/* Hartree potential of an arbitrary density with the handle's Poisson solver:
+ * rho (device, n_slots), vh (device, n_slots: starting guess on input, solution on
+ * output), *iters (may be NULL) the CG iterations.  KSCF_ERR_NO_CONVERGE if the
+ * iteration cap is reached first (vh then holds the last iterate). */
+int kscf_scf_hartree(kscf_scf* scf, const double* rho, double* vh, int* iters);
+
+int kscf_scf_free(kscf_scf* scf);
+
+/* LDA exchange-correlation of a density (Slater exchange; Perdew-Zunger 1981 fit of the
+ * Ceperley-Alder correlation, unpolarised; Hartree units):
+ *   eps_x = -3/4 (3 rho/pi)^{1/3}, v_x = 4/3 eps_x, rs = (3/(4 pi rho))^{1/3},
+ *   rs >= 1: eps_c = g/(1 + b1 sqrt(rs) + b2 rs),
+ *            v_c = eps_c (1 + 7/6 b1 sqrt(rs) + 4/3 b2 rs)/(1 + b1 sqrt(rs) + b2 rs)
+ *   rs < 1:  eps_c = A ln rs + B + C rs ln rs + D rs,
+ *            v_c = A ln rs + B - A/3 + 2/3 C rs ln rs + (2D - C)/3 rs
+ *   g = -0.1423, b1 = 1.0529, b2 = 0.3334, A = 0.0311, B = -0.048, C = 0.0020, D = -0.0116;
+ * rho <= 1e-14 gives 0.  rho, eps (may be NULL), vxc: device, n_slots doubles. */
+int kscf_lda_xc(const kscf_ham* ham, const double* rho, double* eps, double* vxc, void* stream);
+
 /* Hilbert index of brick coordinates (x, y, z) on the 2^bits cube, as used to order the
  * bricks (Skilling 2004 transpose algorithm; bits interleaved most significant first,
  * x first).  Pure host function, exported for tests of the ordering. */

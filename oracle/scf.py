@@ -16,7 +16,7 @@ parametrised by Perdew & Zunger 1981) at fixed ions:
          every later step (the schedule the paper states)
 
 The starting potential is the superposition of neutral atoms: Gaussian valence densities
-Z/(pi^{3/2} r_a^3) exp(-r^2/r_a^2) per atom, V_in = V_ion + V_H[rho_at] + V_xc[rho_at].
+Z/(pi^{3/2} r_a^3) exp(-r^2/r_a^2) per atom (r_a = the species' r_start), V_in = V_ion + V_H[rho_at] + V_xc[rho_at].
 """
 from __future__ import annotations
 
@@ -33,8 +33,6 @@ from .hamiltonian import Hamiltonian, kinetic_matrix
 PZ_GAMMA, PZ_BETA1, PZ_BETA2 = -0.1423, 1.0529, 0.3334
 PZ_A, PZ_B, PZ_C, PZ_D = 0.0311, -0.048, 0.0020, -0.0116
 RHO_FLOOR = 1e-14
-
-ATOM_DENSITY_RADIUS = {14: 1.2, 1: 0.7}   # Gaussian widths of the starting densities (bohr)
 
 
 def lda_xc(rho: np.ndarray):
@@ -69,7 +67,7 @@ def atomic_density(points, atom_pos, atom_z, species):
     table = {int(s["z_number"]): s for s in species}
     rho = np.zeros(len(points))
     for pos, z in zip(atom_pos, atom_z):
-        ra = ATOM_DENSITY_RADIUS[int(z)]
+        ra = table[int(z)]["r_start"]
         zv = table[int(z)]["z_valence"]
         d = points - pos
         r2 = d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2]

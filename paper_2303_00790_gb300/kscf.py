@@ -54,6 +54,23 @@ class kscf_grid_info(C.Structure):
                 ("reserved", C.c_int32), ("h", C.c_double), ("center", C.c_double * 3)]
 
 
+class kscf_scf_params(C.Structure):
+    _fields_ = [("k", C.c_int32), ("degree", C.c_int32), ("dtype", C.c_int32), ("gemm_mode", C.c_int32),
+                ("block", C.c_int32), ("first_iters", C.c_int32), ("history", C.c_int32),
+                ("poisson_maxiter", C.c_int32), ("mix_alpha", C.c_double), ("sre_tol_ry", C.c_double),
+                ("poisson_rtol", C.c_double)]
+
+
+class kscf_scf_report(C.Structure):
+    _fields_ = [("step", C.c_int32), ("converged", C.c_int32), ("poisson_iters", C.c_int32),
+                ("chefsi_iters", C.c_int32), ("sre_ry", C.c_double), ("e_band", C.c_double),
+                ("e_total", C.c_double), ("homo", C.c_double), ("lumo", C.c_double), ("electrons", C.c_double)]
+
+
+KSCF_FIELD_RHO, KSCF_FIELD_V_IN, KSCF_FIELD_V_H, KSCF_FIELD_V_XC = 0, 1, 2, 3
+KSCF_FIELD_V_ION, KSCF_FIELD_V_START, KSCF_FIELD_EPS_XC = 4, 5, 6
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libkscf.so not built ({LIB_PATH}); run __graft_entry__.build()")
@@ -90,6 +107,14 @@ _sigs = {
     "kscf_rotate": ([_vp, _i64, _vp, _i64, _i64, _i32, _i32, _i32, _i32, _i32, _vp, _i64, _vp, _sz, _vp], _i32),
     "kscf_gemm_workspace_size": ([_i32, _i64, _i32, _i32, _i32, _i32, C.POINTER(_sz)], _i32),
     "kscf_check_status": ([], _i32),
+    "kscf_scf_create": ([_vp, C.POINTER(kscf_atom), _i32, C.POINTER(kscf_species), _i32, C.POINTER(_d),
+                         C.POINTER(kscf_scf_params), _vp, _i64, _vp, C.POINTER(_vp)], _i32),
+    "kscf_scf_start": ([_vp, _vp, _i32, C.c_uint64, C.POINTER(_d)], _i32),
+    "kscf_scf_step": ([_vp, C.POINTER(kscf_scf_report), C.POINTER(_d)], _i32),
+    "kscf_scf_get": ([_vp, _i32, _vp], _i32),
+    "kscf_scf_hartree": ([_vp, _vp, _vp, C.POINTER(_i32)], _i32),
+    "kscf_scf_free": ([_vp], _i32),
+    "kscf_lda_xc": ([_vp, _vp, _vp, _vp, _vp], _i32),
 }
 for _name, (_args, _res) in _sigs.items():
     _f = getattr(lib, _name)
@@ -380,6 +405,101 @@ def kscf_launch_counter() -> int:
 
 def kscf_hilbert_index3(x: int, y: int, z: int, bits: int) -> int:
     return int(lib.kscf_hilbert_index3(x, y, z, bits))
+
+
+# ------------------------------------------------------------------ SCF
+def kscf_lda_xc(ham: Hamiltonian, rho, eps=None, vxc=None, stream=None):
+    """(eps_xc, V_xc) of a slot-ordered FP64 density (device)."""
+    torch = _torch()
+    if eps is None:
+        eps = torch.empty(ham.n_slots, dtype=torch.float64, device="cuda")
+    if vxc is None:
+        vxc = torch.empty(ham.n_slots, dtype=torch.float64, device="cuda")
+    _check(lib.kscf_lda_xc(ham.handle, C.c_void_p(rho.data_ptr()), C.c_void_p(eps.data_ptr()),
+                           C.c_void_p(vxc.data_ptr()), _stream(stream)))
+    return eps, vxc
+
+
+def scf_params(k: int, degree: int, dtype: int = KSCF_F64, gemm_mode: int = KSCF_GEMM_NATIVE, block: int = 0,
+               first_iters: int = 4, history: int = 8, mix_alpha: float = 0.3, sre_tol_ry: float = 1e-4,
+               poisson_rtol: float = 1e-12, poisson_maxiter: int = 20000) -> kscf_scf_params:
+    return kscf_scf_params(k, degree, dtype, gemm_mode, block, first_iters, history, poisson_maxiter, mix_alpha,
+                           sre_tol_ry, poisson_rtol)
+
+
+class Scf:
+    """SCF state (kscf_scf handle) over a Hamiltonian and a caller-owned subspace X."""
+
+    def __init__(self, ham: Hamiltonian, atom_pos, atom_z, species, params: kscf_scf_params, X=None, stream=None):
+        torch = _torch()
+        self.ham = ham
+        self.params = params
+        self.k = params.k
+        if X is None:
+            ld = (params.k + 31) // 32 * 32
+            X = torch.zeros((ham.n_slots, ld), dtype=torch.float64 if params.dtype == KSCF_F64 else torch.float32,
+                            device="cuda")
+        if _dtype_code(X) != params.dtype:
+            raise TypeError("X dtype does not match params.dtype")
+        self.X = X
+        self.stream = stream
+        atoms, n = atom_array(atom_pos, atom_z)
+        sp = species_array(species)
+        radius = (C.c_double * len(species))(*[float(s["r_start"]) for s in species])
+        out = C.c_void_p()
+        _check(lib.kscf_scf_create(ham.handle, atoms, n, sp, len(species), radius, C.byref(params),
+                                   C.c_void_p(X.data_ptr()), _rows(X, params.k), _stream(stream), C.byref(out)))
+        self.handle = out
+
+    def start(self, seed: int = 1, init_x: bool = True, dv_start=None):
+        lam = np.empty(self.k, dtype=np.float64)
+        dv = C.c_void_p(dv_start.data_ptr()) if dv_start is not None else C.c_void_p(0)
+        _check(lib.kscf_scf_start(self.handle, dv, 1 if init_x else 0, int(seed),
+                                  lam.ctypes.data_as(C.POINTER(C.c_double))))
+        return lam
+
+    def step(self):
+        rep = kscf_scf_report()
+        lam = np.empty(self.k, dtype=np.float64)
+        _check(lib.kscf_scf_step(self.handle, C.byref(rep), lam.ctypes.data_as(C.POINTER(C.c_double))))
+        d = {f: getattr(rep, f) for f, _ in kscf_scf_report._fields_}
+        d["lam"] = lam
+        return d
+
+    def run(self, max_steps: int = 40):
+        reports = []
+        for _ in range(max_steps):
+            r = self.step()
+            reports.append(r)
+            if r["converged"]:
+                break
+        return reports
+
+    def get(self, field: int, out=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.ham.n_slots, dtype=torch.float64, device="cuda")
+        _check(lib.kscf_scf_get(self.handle, field, C.c_void_p(out.data_ptr())))
+        return out
+
+    def hartree(self, rho, vh=None):
+        torch = _torch()
+        if vh is None:
+            vh = torch.zeros(self.ham.n_slots, dtype=torch.float64, device="cuda")
+        it = C.c_int()
+        _check(lib.kscf_scf_hartree(self.handle, C.c_void_p(rho.data_ptr()), C.c_void_p(vh.data_ptr()), C.byref(it)))
+        return vh, it.value
+
+    def free(self):
+        if getattr(self, "handle", None):
+            lib.kscf_scf_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ convenience

@@ -1,0 +1,147 @@
+"""GPU parity of the self-consistent field loop against the FP64 oracle (oracle/scf.py).
+
+Tolerances (derived from the arithmetic):
+  LDA: closed-form expressions evaluated in FP64 on both sides; cbrt/log/sqrt differ by
+    at most a few ulp, so eps_xc and V_xc agree to 1e-13 relative.
+  Hartree: both sides run CG to |r| < 1e-12 |b| on the same matrix and right-hand side;
+    the error of each iterate is at most cond(A) |r|/|b| with cond(-Lap_h) ~ (2R/h)^2 ~ 1e3
+    here, so the two solutions agree to ~1e-9 of max|V_H|.
+  FP64 SCF: the only differences are rounding order and the CG stopping point (~1e-12);
+    the SCF map is a contraction near the fixed point, so per-step energies and Ritz
+    values agree to 1e-8 and the number of steps is the same.
+  Mixed SCF (FP32 filter, split-bf16 tensor-core Gram, FP64 Cholesky/eigensolve): the
+    accuracy targets of the method are 1e-5 Ha for eigenvalues and 1e-6 Ha per atom for
+    the total energy against the FP64 result.
+"""
+import numpy as np
+import pytest
+
+from helpers import from_slots, to_slots
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def kscf():
+    from paper_2303_00790_gb300.build import build
+    build()
+    from paper_2303_00790_gb300 import kscf as mod
+    return mod
+
+
+def sih4():
+    dd = 1.48 / 0.529177210903 / np.sqrt(3.0)
+    pos = np.array([[0.0, 0.0, 0.0], [dd, dd, dd], [dd, -dd, -dd], [-dd, dd, -dd], [-dd, -dd, dd]]) + 0.05
+    z = np.array([14, 1, 1, 1, 1], dtype=np.int32)
+    return pos, z
+
+
+R_SIH4, H_SIH4, K_SIH4, M_SIH4 = 8.0, 0.5, 8, 10
+
+
+@pytest.fixture(scope="module")
+def oracle_scf(species):
+    from oracle.grid import sphere_grid
+    from oracle.scf import scf
+    from workloads import random_block_lex
+    pos, z = sih4()
+    g = sphere_grid(pos[0], R_SIH4, H_SIH4)
+    X0 = random_block_lex(1, g.n, K_SIH4)
+    return scf(pos, z, species, R_SIH4, H_SIH4, K_SIH4, M_SIH4, X0, max_steps=40)
+
+
+def test_lda_matches_oracle(kscf, species):
+    from oracle.scf import lda_xc
+    pos, z = sih4()
+    g, H = kscf.build_cluster(pos, z, species, 6.0, 0.7)
+    lex, _ = g.slots()
+    n = g.info["n_points"]
+    rng = np.random.default_rng(5)
+    rho = 10.0 ** rng.uniform(-16, 1.5, n)       # both PZ81 branches and the cut-off
+    rho[:7] = [0.0, 1e-14, 2e-14, 0.2387324146, 0.2387324147, 1.0, 30.0]   # rs = 1 at rho = 3/(4 pi)
+    rs = to_slots(rho, lex)
+    eps, vxc = kscf.kscf_lda_xc(H, torch.tensor(rs, device="cuda"))
+    e_ref, v_ref = lda_xc(rho)
+    e = from_slots(eps.cpu().numpy(), lex, n)
+    v = from_slots(vxc.cpu().numpy(), lex, n)
+    assert np.all(np.abs(e - e_ref) <= 1e-13 * np.maximum(np.abs(e_ref), 1e-300))
+    assert np.all(np.abs(v - v_ref) <= 1e-13 * np.maximum(np.abs(v_ref), 1e-300))
+    pad = lex < 0
+    assert np.all(eps.cpu().numpy()[pad] == 0) and np.all(vxc.cpu().numpy()[pad] == 0)
+
+
+@pytest.mark.parametrize("brick", [8, 16])
+def test_hartree_matches_oracle(kscf, species, brick):
+    from oracle.grid import sphere_grid
+    from oracle.scf import Poisson
+    pos, z = sih4()
+    R, h = 8.0, 0.5
+    g, H = kscf.build_cluster(pos, z, species, R, h, brick=brick)
+    lex, _ = g.slots()
+    og = sphere_grid(pos[0], R, h)
+    pts = og.points()
+    # off-centre Gaussian charge plus a random positive perturbation
+    rng = np.random.default_rng(3)
+    d = pts - np.array([0.9, -0.6, 0.4]) - pos[0]
+    rho = 2.0 / (np.pi ** 1.5 * 1.3 ** 3) * np.exp(-(d * d).sum(1) / 1.3 ** 2) + 1e-3 * rng.random(og.n)
+    ref = Poisson(og).solve(rho)
+    params = kscf.scf_params(K_SIH4, M_SIH4)
+    S = kscf.Scf(H, pos, z, species, params)
+    vh, iters = S.hartree(torch.tensor(to_slots(rho, lex), device="cuda"))
+    got = from_slots(vh.cpu().numpy(), lex, og.n)
+    assert iters > 10
+    assert np.max(np.abs(got - ref)) < 1e-9 * np.max(np.abs(ref))
+    assert np.all(vh.cpu().numpy()[lex < 0] == 0)
+    # warm start from the solution: converges at once to the same values
+    vh2, it2 = S.hartree(torch.tensor(to_slots(rho, lex), device="cuda"), vh.clone())
+    assert it2 <= 2
+    assert torch.max(torch.abs(vh2 - vh)).item() < 1e-10 * np.max(np.abs(ref))
+    S.free()
+
+
+def run_gpu_scf(kscf, species, dtype, mode):
+    pos, z = sih4()
+    g, H = kscf.build_cluster(pos, z, species, R_SIH4, H_SIH4)
+    params = kscf.scf_params(K_SIH4, M_SIH4, dtype=dtype, gemm_mode=mode)
+    S = kscf.Scf(H, pos, z, species, params)
+    S.start(seed=1)
+    reps = S.run(40)
+    lex, _ = g.slots()
+    rho = from_slots(S.get(kscf.KSCF_FIELD_RHO).cpu().numpy(), lex, g.info["n_points"])
+    S.free()
+    return reps, rho
+
+
+def test_scf_fp64_matches_oracle(kscf, species, oracle_scf):
+    reps, rho = run_gpu_scf(kscf, species, kscf.KSCF_F64, kscf.KSCF_GEMM_NATIVE)
+    ref = oracle_scf["reports"]
+    assert len(reps) == len(ref), (len(reps), len(ref))
+    for a, b in zip(reps, ref):
+        assert a["step"] == b["step"]
+        assert a["chefsi_iters"] == (4 if a["step"] == 1 else 1)
+        assert abs(a["e_total"] - b["e_total"]) < 1e-8, (a["step"], a["e_total"], b["e_total"])
+        assert abs(a["e_band"] - b["e_band"]) < 1e-8
+        assert np.max(np.abs(a["lam"] - b["lam"])) < 1e-8
+        assert abs(a["sre_ry"] - b["sre_ry"]) < 1e-6 * b["sre_ry"] + 1e-10
+        assert abs(a["electrons"] - 8.0) < 1e-9
+    assert reps[-1]["converged"] == 1 and reps[-1]["sre_ry"] < 1e-4
+    assert np.max(np.abs(rho - oracle_scf["rho"])) < 1e-8 * np.max(oracle_scf["rho"])
+
+
+def test_scf_mixed_precision_accuracy(kscf, species, oracle_scf):
+    reps, rho = run_gpu_scf(kscf, species, kscf.KSCF_F32, kscf.KSCF_GEMM_TENSOR)
+    ref = oracle_scf["reports"][-1]
+    last = reps[-1]
+    assert last["converged"] == 1 and last["sre_ry"] < 1e-4
+    assert len(reps) <= len(oracle_scf["reports"]) + 3
+    n_atoms = 5
+    assert abs(last["e_total"] - ref["e_total"]) < 1e-6 * n_atoms
+    assert np.max(np.abs(last["lam"][:4] - ref["lam"][:4])) < 1e-5
+    gap, gap_ref = last["lumo"] - last["homo"], ref["lumo"] - ref["homo"]
+    assert abs(gap - gap_ref) < 1e-5
+    h3 = H_SIH4 ** 3
+    assert h3 * np.sum(np.abs(rho - oracle_scf["rho"])) < 1e-4 * 8.0
