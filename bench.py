@@ -6,6 +6,12 @@ and the density of the occupied states, on a synthetic H-passivated Si nanoclust
 The metric is Gpoint*vec/s = n_points * k * m / step time / 1e9 (one unit is one grid
 point x one vector x one degree step).
 
+With N = 1 the line also carries "scf": the self-consistent field run to SRE < 1e-4 Ry
+on the SCF workload (Si353H196, k = 850, m = 12) twice on the same GPU -- mixed
+precision (FP32 filter, split-bf16 tensor-core Gram, FP64 Cholesky/eigensolve, FP64 final
+evaluation) and plain FP64 -- with both wall times and the mixed run's errors against
+the FP64 run (eigenvalues, gap, total energy per atom, density).
+
 Output: one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead
 (the only other place that runs oracle/ besides the cpu_baseline leg).
 """
@@ -44,6 +50,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU seconds of the oracle sample")
     p.add_argument("--alu-peaks", action="store_true", help="build and run the FP32/FP64 FMA microbenchmark")
+    p.add_argument("--no-scf", action="store_true", help="skip the SCF wall-time comparison (mixed vs FP64)")
+    p.add_argument("--scf-workload", default="si353h196")
+    p.add_argument("--scf-max-steps", type=int, default=80)
     return p.parse_args()
 
 
@@ -197,6 +206,56 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ SCF wall time
+def run_scf_pair(args):
+    """SCF to convergence, mixed precision then plain FP64, on one GPU (wall clock)."""
+    import torch
+
+    from paper_2303_00790_gb300 import kscf
+    from workloads import pseudo_params, workload
+
+    w = workload(args.scf_workload)
+    pos, z = w.atoms()
+    species = pseudo_params()
+    grid, H = kscf.build_cluster(pos, z, species, w.radius, w.h, brick=args.brick)
+    h3 = grid.info["h"] ** 3
+    runs = {}
+    rhos = {}
+    variants = (("mixed", kscf.KSCF_F32, kscf.KSCF_GEMM_TENSOR, w.block),
+                ("fp64", kscf.KSCF_F64, kscf.KSCF_GEMM_NATIVE, 0))
+    for name, dt, mode, block in variants:
+        params = kscf.scf_params(w.k, w.degree, dtype=dt, gemm_mode=mode, block=block)
+        S = kscf.Scf(H, pos, z, species, params)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.start(seed=1)
+        reps = S.run(args.scf_max_steps)
+        ev = S.evaluate()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        rhos[name] = S.get(kscf.KSCF_FIELD_RHO).clone()
+        lam = np.sort(ev["lam"])
+        runs[name] = {"wall_s": wall, "steps": len(reps), "converged": bool(reps[-1]["converged"]),
+                      "sre_ry": reps[-1]["sre_ry"], "e_total": ev["e_total"], "homo": ev["homo"], "lumo": ev["lumo"],
+                      "gap": ev["lumo"] - ev["homo"], "max_resid_occ": float(np.max(ev["resid"][:len(lam)])),
+                      "poisson_iters": int(sum(r["poisson_iters"] for r in reps)), "_lam": lam}
+        S.free()
+        del S
+        torch.cuda.empty_cache()
+    n_occ = (int(np.sum(z == 14)) * 4 + int(np.sum(z == 1))) // 2
+    a, b = runs["mixed"], runs["fp64"]
+    err = {"eig_occ_max_ha": float(np.max(np.abs(a["_lam"][:n_occ] - b["_lam"][:n_occ]))),
+           "gap_ha": abs(a["gap"] - b["gap"]),
+           "e_total_per_atom_ha": abs(a["e_total"] - b["e_total"]) / len(z),
+           "rho_l1_electrons": float(h3 * torch.sum(torch.abs(rhos["mixed"] - rhos["fp64"])).item())}
+    for r in runs.values():
+        r.pop("_lam")
+    return {"workload": w.name, "n_points": grid.info["n_points"], "n_atoms": len(z), "k": w.k, "degree": w.degree,
+            "sre_tol_ry": 1e-4, "mixing": "Anderson alpha 0.3 history 8", "chefsi_schedule": "4 then 1",
+            "wall": "host clock around start + steps + final FP64 evaluation, synchronised",
+            "mixed": a, "fp64": b, "speedup_fp64_over_mixed": b["wall_s"] / a["wall_s"], "mixed_vs_fp64": err}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_kscf(args):
     import torch
@@ -321,6 +380,13 @@ def run_kscf(args):
                "sample": (f"one CheFSI step of the FP64 CPU oracle on the first {info['k_sample']} of {k} columns "
                           f"({info['n_points']} points, degree {m}), {info['seconds']:.1f} s")}
 
+    scf = None
+    x_mib = X.numel() * 4 / 2**20
+    if rank == 0 and world == 1 and not args.no_scf:
+        del Xfull, X, wf, wo, wr
+        torch.cuda.empty_cache()
+        scf = run_scf_pair(args)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -329,13 +395,13 @@ def run_kscf(args):
                            "block": block, "brick": args.brick,
                            "gemm": "tensor" if mode == kscf.KSCF_GEMM_TENSOR else "native",
                            "parallelism": f"replicas{world}" if world > 1 else "single",
-                           "l2": f"inputs larger than L2 (X = {X.numel() * 4 / 2**20:.0f} MiB)"},
+                           "l2": f"inputs larger than L2 (X = {x_mib:.0f} MiB)"},
                 "filter": {"ms": filt_ms, "gpvs": units / (filt_ms * 1e-3) / 1e9},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
                              "kernel": "cheb_step (fused stencil+V+KB+recurrence), per degree-step launch",
                              "alg_bytes_per_launch": alg_bytes, "launch_ms": step_ms},
-                "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks}
+                "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks, "scf": scf}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

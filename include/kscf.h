@@ -286,10 +286,12 @@ int kscf_check_status(void);
  *          and quadrupole of rho about the grid centre; conjugate gradients in FP64 until
  *          |r| < poisson_rtol |b|, warm-started from the previous V_H
  *   V_xc   Slater exchange + PZ81 correlation, unpolarised (kscf_lda_xc)
- *   rho    sum over the n_e/2 lowest Ritz vectors of 2 |x|^2 (n_e = sum of z_valence)
+ *   rho    sum_i occ_i |x_i|^2 / (h^3 |x_i|^2_2) over the Ritz vectors (the norm is 1 up to
+ *          rounding; dividing by it keeps h^3 sum rho = n_e when X is FP32), occ_i = 2 for
+ *          the n_e/2 lowest states (kT = 0) or Fermi-Dirac (kT > 0; n_e = sum of z_valence)
  *   SRE    2 sqrt(h^3 sum_s rho_s (V_out - V_in)_s^2) in Ry, V_out = V_eff[rho_out]
- *   E_tot  sum_i f_i lambda_i - h^3 sum rho (V_in - V_ion) + 1/2 h^3 sum rho V_H
- *          + h^3 sum rho eps_xc       (band energy minus double counting)
+ *   E_tot  sum_i occ_i lambda_i - h^3 sum rho (V_in - V_ion) + 1/2 h^3 sum rho V_H
+ *          + h^3 sum rho eps_xc (- T S when kT > 0)   (band energy minus double counting)
  *   mixing Anderson mixing of V_in: F = V_out - V_in, history of the last `history`
  *          differences (dV_j, dF_j), g = argmin |F - sum_j g_j dF_j| by the normal
  *          equations, V_in <- V_in + alpha F - sum_j g_j (dV_j + alpha dF_j).
@@ -320,6 +322,9 @@ typedef struct kscf_scf_params {
   double mix_alpha;        /* Anderson linear step (0 < alpha <= 1) */
   double sre_tol_ry;       /* converged when SRE < sre_tol_ry (paper: 1e-4 Ry) */
   double poisson_rtol;     /* CG stop |r| < rtol |b| */
+  double kT;               /* electronic temperature (Ha): 0 = the n_e/2 lowest states doubly
+                              occupied; > 0 = Fermi-Dirac occupations 2 f((lambda - mu)/kT),
+                              mu from sum = n_e, and e_total is the free energy E - T S */
 } kscf_scf_params;
 
 typedef struct kscf_scf_report {
@@ -332,6 +337,9 @@ typedef struct kscf_scf_report {
   double e_total;          /* Kohn-Sham total energy without ion-ion term (Ha) */
   double homo, lumo;       /* lambda_{n_occ-1}, lambda_{n_occ} (Ha) */
   double electrons;        /* h^3 sum rho */
+  double mu;               /* Fermi level (kT > 0), else lambda_{n_occ-1} */
+  double minus_ts;         /* -T S = 2 kT sum_i [f_i ln f_i + (1 - f_i) ln(1 - f_i)], f = occ/2 */
+  double occ_last;         /* occupation of the highest Ritz state (k too small if not ~0) */
 } kscf_scf_report;
 
 /* Creates the SCF state for the atoms the Hamiltonian was built from.  atoms/species
@@ -354,6 +362,17 @@ int kscf_scf_start(kscf_scf* scf, const double* dv_start, int init_x, uint64_t s
  * NULL) the Ritz values.  After a converged step V_in is left as it was, so a further
  * call repeats the step at the same potential. */
 int kscf_scf_step(kscf_scf* scf, kscf_scf_report* report, double* eigvals_host);
+
+/* Final evaluation in FP64 (the mixed-precision path keeps FP64 for the last residual
+ * and energy evaluation): the Ritz vectors of the last step (widened to FP64 when X is
+ * FP32) are applied with H at that step's V_in in FP64, giving the Rayleigh quotients
+ * lambda_i = <x_i, H x_i> / <x_i, x_i> and residual norms |H x_i - lambda_i x_i| / |x_i|
+ * (h^3-weighted).  report: the last step's report with e_band, e_total, homo, lumo, mu,
+ * minus_ts and occ_last recomputed from the sorted Rayleigh quotients (the density terms
+ * are those of the last step).  eigvals_host / resid_host: k doubles each (vector
+ * order), or NULL.  Allocates about 2 n_slots k doubles of device memory for the call
+ * and leaves the Hamiltonian at that V_in.  Synchronous. */
+int kscf_scf_evaluate(kscf_scf* scf, kscf_scf_report* report, double* eigvals_host, double* resid_host);
 
 /* Fields for kscf_scf_get (device, n_slots doubles each, slot order, 0 in padding). */
 #define KSCF_FIELD_RHO     0   /* density of the last step (start: rho_0) */

@@ -14,6 +14,10 @@ parametrised by Perdew & Zunger 1981) at fixed ions:
   SRE    sqrt(h^3 sum_p rho_p (V_out - V_in)_p^2), reported in Ry (x 2); stop below 1e-4 Ry
   CheFSI four filter/Cholesky-QR/Rayleigh-Ritz iterations in the first SCF step, one in
          every later step (the schedule the paper states)
+  occupations  kT = 0: the n_e/2 lowest Ritz states doubly occupied.  kT > 0: Fermi-Dirac
+         occupations 2 f((lambda - mu)/kT) with mu fixed by sum = n_e (bisection), and the
+         energy reported is the Mermin free energy E - T S,
+         S = -2 sum_i [f_i ln f_i + (1 - f_i) ln(1 - f_i)]
 
 The starting potential is the superposition of neutral atoms: Gaussian valence densities
 Z/(pi^{3/2} r_a^3) exp(-r^2/r_a^2) per atom (r_a = the species' r_start), V_in = V_ion + V_H[rho_at] + V_xc[rho_at].
@@ -60,6 +64,42 @@ def lda_xc(rho: np.ndarray):
     eps[m] = ex + ec
     v[m] = vx + vc
     return eps, v
+
+
+def fermi_dirac(x):
+    """1/(1 + e^x) written as (1 - tanh(x/2))/2 (no overflow for large |x|)."""
+    return 0.5 * (1.0 - np.tanh(0.5 * np.asarray(x, dtype=np.float64)))
+
+
+def occupations(lam, n_electrons: int, kT: float):
+    """(occ, mu, -T S) for the Ritz values lam (ascending).
+
+    kT = 0: occ = 2 for the n_electrons/2 lowest states, mu = the highest occupied value.
+    kT > 0: occ_i = 2 f((lam_i - mu)/kT); mu by 200 bisection halvings of
+    [min lam - 1 - 50 kT, max lam + 1 + 50 kT] on the electron count (monotone in mu).
+    """
+    lam = np.asarray(lam, dtype=np.float64)
+    if kT == 0.0:
+        nocc = n_electrons // 2
+        occ = np.zeros(len(lam))
+        occ[:nocc] = 2.0
+        return occ, float(lam[nocc - 1]), 0.0
+    lo = float(lam.min()) - 1.0 - 50.0 * kT
+    hi = float(lam.max()) + 1.0 + 50.0 * kT
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if float(np.sum(2.0 * fermi_dirac((lam - mid) / kT))) < n_electrons:
+            lo = mid
+        else:
+            hi = mid
+    mu = 0.5 * (lo + hi)
+    f = fermi_dirac((lam - mu) / kT)
+    s = np.zeros(len(lam))
+    inner = (f > 0.0) & (f < 1.0)
+    fi = f[inner]
+    s[inner] = fi * np.log(fi) + (1.0 - fi) * np.log(1.0 - fi)
+    minus_ts = kT * 2.0 * float(np.sum(s))
+    return 2.0 * f, mu, minus_ts
 
 
 def atomic_density(points, atom_pos, atom_z, species):
@@ -161,7 +201,7 @@ class Anderson:
 
 
 def scf(atom_pos, atom_z, species, radius, h, k, degree, X0, max_steps=40, sre_tol_ry=1e-4,
-        first_iters=4, alpha=0.3, history=8, center=None):
+        first_iters=4, alpha=0.3, history=8, center=None, kT=0.0):
     """Run the SCF; returns a dict with per-step reports and the final state."""
     from .grid import sphere_grid
     from .potential import kb_projectors, local_potential
@@ -176,7 +216,6 @@ def scf(atom_pos, atom_z, species, radius, h, k, degree, X0, max_steps=40, sre_t
     pois = Poisson(g)
     ne = n_electrons(atom_z)
     nocc = ne // 2
-    occ = np.full(nocc, 2.0)
     rho0 = atomic_density(pts, atom_pos, atom_z, species)
     vh = pois.solve(rho0)
     _, vxc = lda_xc(rho0)
@@ -194,6 +233,7 @@ def scf(atom_pos, atom_z, species, radius, h, k, degree, X0, max_steps=40, sre_t
             Y = cf.chebyshev_filter(H, X, degree, lam[-1], b, lam[0])
             X, _ = cf.cholesky_qr(Y, H.h3)
             lam, X, _ = cf.rayleigh_ritz(H, X, H.h3)
+        occ, mu, minus_ts = occupations(lam, ne, kT)
         rho = cf.density(X, occ)
         vh = pois.solve(rho, x0=vh_prev)
         vh_prev = vh
@@ -201,10 +241,11 @@ def scf(atom_pos, atom_z, species, radius, h, k, degree, X0, max_steps=40, sre_t
         v_out = v_ion + vh + vxc
         f = v_out - v_in
         sre = 2.0 * math.sqrt(H.h3 * float(np.sum(rho * f * f)))
-        e_band = float(np.dot(occ, lam[:nocc]))
+        e_band = float(np.dot(occ, lam))
         e_tot = (e_band - H.h3 * float(np.dot(rho, v_in - v_ion)) + 0.5 * H.h3 * float(np.dot(rho, vh))
-                 + H.h3 * float(np.dot(rho, eps)))
-        reports.append({"step": step, "sre_ry": sre, "e_band": e_band, "e_total": e_tot,
+                 + H.h3 * float(np.dot(rho, eps)) + minus_ts)
+        reports.append({"step": step, "sre_ry": sre, "e_band": e_band, "e_total": e_tot, "mu": mu,
+                        "minus_ts": minus_ts,
                         "homo": float(lam[nocc - 1]), "lumo": float(lam[nocc]) if k > nocc else float("nan"),
                         "electrons": H.h3 * float(rho.sum()), "lam": lam.copy()})
         if sre < sre_tol_ry:

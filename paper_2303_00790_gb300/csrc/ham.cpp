@@ -32,7 +32,7 @@ static cudaError_t upload(T** dst, const T* src, size_t n) {
 
 static void free_ham(Ham& H) {
   void* ptrs[] = {H.d_nbr,           H.d_mask,         H.d_lex,          H.d_pad,
-                  H.d_v64,           H.d_v32,          H.d_kb_atom_ptr,  H.d_kb_atom_slot,
+                  H.d_vion,          H.d_v64,           H.d_v32,          H.d_kb_atom_ptr,  H.d_kb_atom_slot,
                   H.d_kb_atom_chi64, H.d_kb_atom_chi32, H.d_kb_slot_ptr, H.d_kb_slot_atom,
                   H.d_kb_slot_chi64, H.d_kb_slot_chi32, H.d_kb_energy, H.d_kb_entry_lslot};
   for (void* p : ptrs)
@@ -131,6 +131,8 @@ extern "C" int kscf_build_hamiltonian(const kscf_grid* grid, const kscf_atom* at
     if (e == cudaSuccess) e = upload(&d_xyz, xyz.data(), xyz.size());
     if (e == cudaSuccess) e = launch_vloc(H, d_xyz, d_at, n_atoms, 0);
     if (e == cudaSuccess) e = launch_v_to_f32(H, 0);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&H.d_vion, sizeof(double) * g.n_slots);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(H.d_vion, H.d_v64, sizeof(double) * g.n_slots, cudaMemcpyDeviceToDevice, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (d_at) cudaFree(d_at);
     if (d_xyz) cudaFree(d_xyz);

@@ -62,6 +62,7 @@ struct Ham {
   int64_t* d_pad = nullptr;        // padding slots
   int64_t n_pad = 0;
   double* d_v64 = nullptr;         // n_slots
+  double* d_vion = nullptr;        // n_slots: V_loc as built (kept when the potential is replaced)
   float* d_v32 = nullptr;          // n_slots
   // KB tables
   int n_kb = 0;                    // atoms with projectors

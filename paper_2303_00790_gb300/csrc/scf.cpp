@@ -24,6 +24,7 @@ struct kscf_scf {
   int64_t ld = 0;
   cudaStream_t st = nullptr;
   int n_occ = 0;
+  int n_e = 0;
   int64_t n = 0;
   int n_atoms = 0;
   // device buffers (FP64, n slots each unless noted)
@@ -39,6 +40,10 @@ struct kscf_scf {
   double* part_pq = nullptr;
   double* small = nullptr;    // 128 doubles of reduction results
   int* d_iters = nullptr;
+  double* part_col = nullptr; // kScfRedBlocks x k partial column sums
+  double* colsq = nullptr;    // k column sums of squares
+  double* d_occ = nullptr;    // k occupations divided by the vector norms
+  double* host_k = nullptr;   // pinned, 2k doubles
   PoissonPlan P;
   void* work = nullptr;
   size_t work_bytes = 0;
@@ -50,6 +55,9 @@ struct kscf_scf {
   bool have_prev = false;
   int ring_next = 0;
   std::vector<int> order;     // history columns in use, oldest first
+  double sums[5] = {0, 0, 0, 0, 0};  // last step: rho f^2, rho (V_in - V_ion), rho V_H, rho eps_xc, rho
+  kscf_scf_report last{};
+  bool stepped = false;
 };
 
 namespace {
@@ -65,10 +73,11 @@ void free_scf(kscf_scf* S) {
                  S->vxc,    S->eps,    S->f,      S->cg_b,    S->cg_r,       S->cg_p,       S->cg_q,
                  S->v_prev, S->f_prev, S->dv,     S->df,      S->part,       S->part_bb,    S->part_rr[0],
                  S->part_rr[1], S->part_pq, S->small, S->d_iters, S->P.d_grel, S->P.d_vghost, S->P.d_gptr,
-                 S->P.d_gidx, S->P.d_gw, S->work};
+                 S->P.d_gidx, S->P.d_gw, S->work, S->part_col, S->colsq, S->d_occ};
   for (void* q : dev)
     if (q) cudaFree(q);
   if (S->host) cudaFreeHost(S->host);
+  if (S->host_k) cudaFreeHost(S->host_k);
 }
 
 template <typename T>
@@ -239,6 +248,47 @@ bool solve_small(int m, std::vector<double> G, std::vector<double> r, double* g)
   return true;
 }
 
+// Occupations of the Ritz values lam (ascending) for n_e electrons (spin-degenerate).
+// kT = 0: 2 for the n_e/2 lowest.  kT > 0: 2 f((lam - mu)/kT), f(x) = (1 - tanh(x/2))/2,
+// mu by 200 bisection halvings of [min lam - 1 - 50 kT, max lam + 1 + 50 kT] on the
+// electron count; minus_ts = 2 kT sum [f ln f + (1 - f) ln(1 - f)].
+void occupations(const std::vector<double>& lam, int n_e, double kT, std::vector<double>& occ, double* mu,
+                 double* minus_ts) {
+  const int k = (int)lam.size();
+  occ.assign(k, 0.0);
+  *minus_ts = 0.0;
+  if (kT == 0.0) {
+    for (int i = 0; i < n_e / 2; i++) occ[i] = 2.0;
+    *mu = lam[n_e / 2 - 1];
+    return;
+  }
+  double lo = lam[0], hi = lam[0];
+  for (double l : lam) {
+    lo = std::min(lo, l);
+    hi = std::max(hi, l);
+  }
+  lo -= 1.0 + 50.0 * kT;
+  hi += 1.0 + 50.0 * kT;
+  auto fd = [](double x) { return 0.5 * (1.0 - std::tanh(0.5 * x)); };
+  for (int it = 0; it < 200; it++) {
+    const double mid = 0.5 * (lo + hi);
+    double cnt = 0.0;
+    for (double l : lam) cnt += 2.0 * fd((l - mid) / kT);
+    if (cnt < (double)n_e)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  *mu = 0.5 * (lo + hi);
+  double s = 0.0;
+  for (int i = 0; i < k; i++) {
+    const double f = fd((lam[i] - *mu) / kT);
+    occ[i] = 2.0 * f;
+    if (f > 0.0 && f < 1.0) s += f * std::log(f) + (1.0 - f) * std::log(1.0 - f);
+  }
+  *minus_ts = kT * 2.0 * s;
+}
+
 int eig_step(kscf_scf* S, bool filter, double b_upper) {
   const kscf_scf_params& p = S->p;
   kscf_ham* ham = S->ham;
@@ -283,7 +333,8 @@ extern "C" int kscf_scf_create(kscf_ham* ham, const kscf_atom* atoms, int n_atom
   if ((p.dtype != KSCF_F64 && p.dtype != KSCF_F32) || (p.gemm_mode != KSCF_GEMM_NATIVE && p.gemm_mode != KSCF_GEMM_TENSOR) ||
       (p.gemm_mode == KSCF_GEMM_TENSOR && p.dtype != KSCF_F32) || p.degree < 1 || p.first_iters < 1 ||
       p.history < 1 || p.history > kAndersonMax || !(p.mix_alpha > 0.0 && p.mix_alpha <= 1.0) ||
-      !(p.sre_tol_ry > 0.0) || !(p.poisson_rtol > 0.0) || p.poisson_maxiter < 1 || p.block < 0 || ld < p.k) {
+      !(p.sre_tol_ry > 0.0) || !(p.poisson_rtol > 0.0) || p.poisson_maxiter < 1 || p.block < 0 || ld < p.k ||
+      !(p.kT >= 0.0) || !std::isfinite(p.kT)) {
     set_error("kscf_scf_create: invalid parameters");
     return KSCF_ERR_INVALID;
   }
@@ -321,6 +372,7 @@ extern "C" int kscf_scf_create(kscf_ham* ham, const kscf_atom* atoms, int n_atom
   S->ld = ld;
   S->st = (cudaStream_t)stream;
   S->n_occ = n_e_int / 2;
+  S->n_e = n_e_int;
   S->n_atoms = n_atoms;
   const Ham& H = ham->h;
   const Grid& g = H.grid;
@@ -345,6 +397,10 @@ extern "C" int kscf_scf_create(kscf_ham* ham, const kscf_atom* atoms, int n_atom
     if (e == cudaSuccess) e = dalloc(&S->part_pq, (size_t)kScfRedBlocks);
     if (e == cudaSuccess) e = dalloc(&S->small, 128);
     if (e == cudaSuccess) e = dalloc(&S->d_iters, 1);
+    if (e == cudaSuccess) e = dalloc(&S->part_col, (size_t)kScfRedBlocks * p.k);
+    if (e == cudaSuccess) e = dalloc(&S->colsq, (size_t)p.k);
+    if (e == cudaSuccess) e = dalloc(&S->d_occ, (size_t)p.k);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&S->host_k, 2 * (size_t)p.k * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&S->host, 128 * sizeof(double));
     if (e != cudaSuccess) {
       set_error("kscf_scf_create: device allocation failed: %s", cudaGetErrorString(e));
@@ -361,7 +417,7 @@ extern "C" int kscf_scf_create(kscf_ham* ham, const kscf_atom* atoms, int n_atom
     e = cudaMemcpyAsync(S->rel, rel.data(), rel.size() * 8, cudaMemcpyHostToDevice, S->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(S->atoms, at.data(), at.size() * 8, cudaMemcpyHostToDevice, S->st);
     // V_ion: the Hamiltonian's local potential as built
-    if (e == cudaSuccess) e = cudaMemcpyAsync(S->v_ion, H.d_v64, sizeof(double) * n, cudaMemcpyDeviceToDevice, S->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S->v_ion, H.d_vion, sizeof(double) * n, cudaMemcpyDeviceToDevice, S->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(S->st);
     if (e != cudaSuccess) {
       set_error("kscf_scf_create: upload failed: %s", cudaGetErrorString(e));
@@ -417,6 +473,7 @@ extern "C" int kscf_scf_start(kscf_scf* scf, const double* dv_start, int init_x,
   S->ring_next = 0;
   S->order.clear();
   S->started = false;
+  S->stepped = false;
   if (init_x) {
     int rc = kscf_random_subspace(S->ham, S->X, S->ld, S->p.k, S->p.dtype, seed, st);
     if (rc) return rc;
@@ -474,22 +531,41 @@ extern "C" int kscf_scf_step(kscf_scf* scf, kscf_scf_report* report, double* eig
   if (rc) return rc;
   report->chefsi_iters = iters;
 
-  // output density and potentials
-  rc = kscf_density(S->ham, S->X, S->ld, S->n_occ, p.dtype, nullptr, S->rho, st);
+  // occupations and the output density of the normalised Ritz vectors
+  std::vector<double> occ;
+  double mu = 0.0, minus_ts = 0.0;
+  occupations(S->lam, S->n_e, p.kT, occ, &mu, &minus_ts);
+  const int n_used = p.kT == 0.0 ? S->n_occ : p.k;
+  KSCF_CUDA_TRY(launch_col_sumsq(S->X, S->ld, S->n, n_used, p.dtype, S->part_col, S->colsq, st));
+  KSCF_CUDA_TRY(cudaMemcpyAsync(S->host_k, S->colsq, sizeof(double) * n_used, cudaMemcpyDeviceToHost, st));
+  KSCF_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < n_used; i++) {
+    const double nrm = h3 * S->host_k[i];
+    if (!(nrm > 0.0) || !std::isfinite(nrm)) {
+      set_error("kscf_scf_step: Ritz vector %d has norm %g", i, nrm);
+      return KSCF_ERR_NONFINITE;
+    }
+    S->host_k[p.k + i] = occ[i] / nrm;
+  }
+  KSCF_CUDA_TRY(cudaMemcpyAsync(S->d_occ, S->host_k + p.k, sizeof(double) * n_used, cudaMemcpyHostToDevice, st));
+  rc = kscf_density(S->ham, S->X, S->ld, n_used, p.dtype, S->d_occ, S->rho, st);
   if (rc) return rc;
   rc = hartree(S, S->rho, S->vh, &report->poisson_iters);
   if (rc) return rc;
   KSCF_CUDA_TRY(launch_lda(H, S->rho, S->eps, S->vxc, st));
   KSCF_CUDA_TRY(launch_residual(H, S->rho, S->v_in, S->v_ion, S->vh, S->vxc, S->eps, S->f, S->part,
                                 S->small + kRes, st));
-  double sums[5];
+  double* sums = S->sums;
   rc = sync_read(S, S->small + kRes, 5, sums);
   if (rc) return rc;
   double e_band = 0.0;
-  for (int i = 0; i < S->n_occ; i++) e_band += 2.0 * S->lam[i];
+  for (int i = 0; i < p.k; i++) e_band += occ[i] * S->lam[i];
   report->sre_ry = 2.0 * std::sqrt(h3 * sums[0]);
   report->e_band = e_band;
-  report->e_total = e_band - h3 * sums[1] + 0.5 * h3 * sums[2] + h3 * sums[3];
+  report->e_total = e_band - h3 * sums[1] + 0.5 * h3 * sums[2] + h3 * sums[3] + minus_ts;
+  report->mu = mu;
+  report->minus_ts = minus_ts;
+  report->occ_last = occ[p.k - 1];
   report->electrons = h3 * sums[4];
   report->homo = S->lam[S->n_occ - 1];
   report->lumo = S->lam[S->n_occ];
@@ -499,6 +575,8 @@ extern "C" int kscf_scf_step(kscf_scf* scf, kscf_scf_report* report, double* eig
     return KSCF_ERR_NONFINITE;
   }
   report->converged = report->sre_ry < p.sre_tol_ry ? 1 : 0;
+  S->last = *report;
+  S->stepped = true;
   if (report->converged) return KSCF_OK;
 
   // Anderson mixing of V_in
@@ -534,6 +612,113 @@ extern "C" int kscf_scf_step(kscf_scf* scf, kscf_scf_report* report, double* eig
     }
   }
   KSCF_CUDA_TRY(launch_anderson_update(H, cols, p.mix_alpha, S->dv, S->df, S->f, S->v_in, st));
+  return KSCF_OK;
+}
+
+extern "C" int kscf_scf_evaluate(kscf_scf* scf, kscf_scf_report* report, double* eigvals_host, double* resid_host) {
+  if (!scf || !report) {
+    set_error("kscf_scf_evaluate: null argument");
+    return KSCF_ERR_INVALID;
+  }
+  kscf_scf* S = scf;
+  if (!S->stepped) {
+    set_error("kscf_scf_evaluate: call kscf_scf_step first");
+    return KSCF_ERR_INVALID;
+  }
+  const Ham& H = S->ham->h;
+  const kscf_scf_params& p = S->p;
+  const int k = p.k;
+  const int64_t n = S->n;
+  const double h3 = H.grid.h * H.grid.h * H.grid.h;
+  cudaStream_t st = S->st;
+  const int64_t ld64 = (k + 31) / 32 * 32;
+  size_t wb = 0;
+  int rc = kscf_workspace_size(S->ham, KSCF_OP_APPLY, k, KSCF_F64, 0, 0, &wb);
+  if (rc) return rc;
+  double *X64 = nullptr, *HX64 = nullptr, *lam_d = nullptr;
+  void* work = nullptr;
+  auto release = [&]() {
+    if (p.dtype != KSCF_F64 && X64) cudaFree(X64);
+    if (HX64) cudaFree(HX64);
+    if (lam_d) cudaFree(lam_d);
+    if (work) cudaFree(work);
+  };
+  int64_t ldx = ld64;
+  cudaError_t e = cudaSuccess;
+  if (p.dtype == KSCF_F64) {
+    X64 = (double*)S->X;
+    ldx = S->ld;
+  } else {
+    e = cudaMalloc((void**)&X64, sizeof(double) * n * ld64);
+  }
+  if (e == cudaSuccess) e = cudaMalloc((void**)&HX64, sizeof(double) * n * ldx);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&lam_d, sizeof(double) * k);
+  if (e == cudaSuccess) e = cudaMalloc(&work, std::max<size_t>(wb, 256));
+  if (e != cudaSuccess) {
+    release();
+    set_error("kscf_scf_evaluate: device allocation failed: %s", cudaGetErrorString(e));
+    return KSCF_ERR_CUDA;
+  }
+  // the Hamiltonian of the last step (its V_in), applied in FP64 to the Ritz vectors
+  rc = kscf_set_potential(S->ham, S->v_in, st);
+  if (!rc && p.dtype != KSCF_F64) {
+    e = launch_widen((const float*)S->X, S->ld, X64, ld64, n, k, st);
+    if (e != cudaSuccess) {
+      set_error("kscf_scf_evaluate: %s", cudaGetErrorString(e));
+      rc = KSCF_ERR_CUDA;
+    }
+  }
+  if (!rc) rc = kscf_hamiltonian_apply(S->ham, X64, ldx, HX64, ldx, k, KSCF_F64, work, std::max<size_t>(wb, 256), st);
+  std::vector<double> num(k), den(k), res(k), lam(k);
+  if (!rc) {
+    e = launch_col_dot(X64, ldx, HX64, ldx, n, k, KSCF_F64, S->part_col, S->colsq, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S->host_k, S->colsq, sizeof(double) * k, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) std::memcpy(num.data(), S->host_k, sizeof(double) * k);
+    if (e == cudaSuccess) e = launch_col_dot(X64, ldx, X64, ldx, n, k, KSCF_F64, S->part_col, S->colsq, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S->host_k, S->colsq, sizeof(double) * k, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) {
+      std::memcpy(den.data(), S->host_k, sizeof(double) * k);
+      for (int i = 0; i < k; i++) lam[i] = num[i] / den[i];
+      std::memcpy(S->host_k, lam.data(), sizeof(double) * k);
+      e = cudaMemcpyAsync(lam_d, S->host_k, sizeof(double) * k, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = launch_col_resid(X64, HX64, ldx, n, k, lam_d, S->part_col, S->colsq, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S->host_k, S->colsq, sizeof(double) * k, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) {
+      for (int i = 0; i < k; i++) res[i] = std::sqrt(S->host_k[i] / den[i]);
+    } else {
+      set_error("kscf_scf_evaluate: %s", cudaGetErrorString(e));
+      rc = KSCF_ERR_CUDA;
+    }
+  }
+  release();
+  if (rc) return rc;
+  for (int i = 0; i < k; i++)
+    if (!std::isfinite(lam[i]) || !std::isfinite(res[i])) {
+      set_error("kscf_scf_evaluate: non-finite Rayleigh quotient or residual (vector %d)", i);
+      return KSCF_ERR_NONFINITE;
+    }
+  // energies of the last step's density with the FP64 Rayleigh quotients
+  std::vector<double> occ;
+  double mu = 0.0, minus_ts = 0.0;
+  std::vector<double> sorted = lam;
+  std::sort(sorted.begin(), sorted.end());
+  occupations(sorted, S->n_e, p.kT, occ, &mu, &minus_ts);
+  double e_band = 0.0;
+  for (int i = 0; i < k; i++) e_band += occ[i] * sorted[i];
+  *report = S->last;
+  report->e_band = e_band;
+  report->e_total = e_band - h3 * S->sums[1] + 0.5 * h3 * S->sums[2] + h3 * S->sums[3] + minus_ts;
+  report->homo = sorted[S->n_occ - 1];
+  report->lumo = sorted[S->n_occ];
+  report->mu = mu;
+  report->minus_ts = minus_ts;
+  report->occ_last = occ[k - 1];
+  if (eigvals_host) std::memcpy(eigvals_host, lam.data(), sizeof(double) * k);
+  if (resid_host) std::memcpy(resid_host, res.data(), sizeof(double) * k);
   return KSCF_OK;
 }
 

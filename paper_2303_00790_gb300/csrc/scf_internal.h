@@ -50,6 +50,17 @@ cudaError_t launch_residual(const Ham& H, const double* rho, const double* v_in,
                             cudaStream_t st);
 cudaError_t launch_sum3(const Ham& H, const double* a, const double* b, const double* c, double* out,
                         cudaStream_t st);
+// out[j] = sum_r X[r][j]^2 (FP64), part: kScfRedBlocks * k doubles
+cudaError_t launch_col_sumsq(const void* X, int64_t ld, int64_t rows, int k, int dtype, double* part, double* out,
+                             cudaStream_t st);
+// out[j] = sum_r A[r][j] B[r][j] (FP64 sums)
+cudaError_t launch_col_dot(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t rows, int k, int dtype,
+                           double* part, double* out, cudaStream_t st);
+// out[j] = sum_r (HX[r][j] - lam[j] X[r][j])^2, lam on the device
+cudaError_t launch_col_resid(const double* X, const double* HX, int64_t ld, int64_t rows, int k, const double* lam,
+                             double* part, double* out, cudaStream_t st);
+cudaError_t launch_widen(const float* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int k,
+                         cudaStream_t st);
 cudaError_t launch_add2(const Ham& H, const double* a, const double* b, double* out, cudaStream_t st);
 cudaError_t launch_anderson_push(int64_t n, const double* v_in, const double* f, double* v_prev, double* f_prev,
                                  double* dv, double* df, bool have_prev, cudaStream_t st);

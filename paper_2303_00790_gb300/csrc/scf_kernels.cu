@@ -466,6 +466,88 @@ cudaError_t launch_add2(const Ham& H, const double* a, const double* b, double* 
   return cudaGetLastError();
 }
 
+// Column inner products in FP64: part[j * gridDim.x + b] = this block's share of
+// sum_r A[r][j] B[r][j] (B = A: column sums of squares).
+template <typename T>
+__global__ void __launch_bounds__(kScfThreads) col_dot_kernel(const T* __restrict__ A, int64_t lda,
+                                                              const T* __restrict__ B, int64_t ldb, int64_t rows,
+                                                              int k, double* __restrict__ part) {
+  const int64_t per = (rows + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * per;
+  const int64_t r1 = r0 + per < rows ? r0 + per : rows;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    double a0 = 0.0, a1 = 0.0;
+    int64_t r = r0;
+    for (; r + 1 < r1; r += 2) {
+      a0 += (double)A[r * lda + j] * (double)B[r * ldb + j];
+      a1 += (double)A[(r + 1) * lda + j] * (double)B[(r + 1) * ldb + j];
+    }
+    if (r < r1) a0 += (double)A[r * lda + j] * (double)B[r * ldb + j];
+    part[(int64_t)j * gridDim.x + blockIdx.x] = a0 + a1;
+  }
+}
+
+// part[j * gridDim.x + b] = this block's share of sum_r (HX[r][j] - lam[j] X[r][j])^2  (FP64)
+__global__ void __launch_bounds__(kScfThreads) col_resid_kernel(const double* __restrict__ X, const double* __restrict__ HX,
+                                                                int64_t ld, int64_t rows, int k,
+                                                                const double* __restrict__ lam,
+                                                                double* __restrict__ part) {
+  const int64_t per = (rows + gridDim.x - 1) / gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * per;
+  const int64_t r1 = r0 + per < rows ? r0 + per : rows;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    const double l = lam[j];
+    double a = 0.0;
+    for (int64_t r = r0; r < r1; r++) {
+      const double d = HX[r * ld + j] - l * X[r * ld + j];
+      a += d * d;
+    }
+    part[(int64_t)j * gridDim.x + blockIdx.x] = a;
+  }
+}
+
+cudaError_t launch_col_dot(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t rows, int k, int dtype,
+                           double* part, double* out, cudaStream_t st) {
+  if (dtype == KSCF_F64)
+    col_dot_kernel<double><<<kScfRedBlocks, kScfThreads, 0, st>>>((const double*)A, lda, (const double*)B, ldb, rows,
+                                                                  k, part), count_launch();
+  else
+    col_dot_kernel<float><<<kScfRedBlocks, kScfThreads, 0, st>>>((const float*)A, lda, (const float*)B, ldb, rows, k,
+                                                                 part), count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_finalize_partials(part, kScfRedBlocks, k, out, st);
+}
+
+cudaError_t launch_col_sumsq(const void* X, int64_t ld, int64_t rows, int k, int dtype, double* part, double* out,
+                             cudaStream_t st) {
+  return launch_col_dot(X, ld, X, ld, rows, k, dtype, part, out, st);
+}
+
+cudaError_t launch_col_resid(const double* X, const double* HX, int64_t ld, int64_t rows, int k, const double* lam,
+                             double* part, double* out, cudaStream_t st) {
+  col_resid_kernel<<<kScfRedBlocks, kScfThreads, 0, st>>>(X, HX, ld, rows, k, lam, part), count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_finalize_partials(part, kScfRedBlocks, k, out, st);
+}
+
+// dst[r][j] = (double) src[r][j]  (FP32 -> FP64), r < rows, j < k
+__global__ void widen_kernel(const float* __restrict__ src, int64_t lds, double* __restrict__ dst, int64_t ldd,
+                             int64_t rows, int k) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * k) return;
+  const int64_t r = idx / k;
+  const int j = (int)(idx - r * k);
+  dst[r * ldd + j] = (double)src[r * lds + j];
+}
+
+cudaError_t launch_widen(const float* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int k,
+                         cudaStream_t st) {
+  widen_kernel<<<nblk(rows * k, 256), 256, 0, st>>>(src, lds, dst, ldd, rows, k), count_launch();
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Anderson mixing.
 // New history column: dV = V_in - V_prev, dF = F - F_prev; then V_prev = V_in, F_prev = F.

@@ -58,13 +58,14 @@ class kscf_scf_params(C.Structure):
     _fields_ = [("k", C.c_int32), ("degree", C.c_int32), ("dtype", C.c_int32), ("gemm_mode", C.c_int32),
                 ("block", C.c_int32), ("first_iters", C.c_int32), ("history", C.c_int32),
                 ("poisson_maxiter", C.c_int32), ("mix_alpha", C.c_double), ("sre_tol_ry", C.c_double),
-                ("poisson_rtol", C.c_double)]
+                ("poisson_rtol", C.c_double), ("kT", C.c_double)]
 
 
 class kscf_scf_report(C.Structure):
     _fields_ = [("step", C.c_int32), ("converged", C.c_int32), ("poisson_iters", C.c_int32),
                 ("chefsi_iters", C.c_int32), ("sre_ry", C.c_double), ("e_band", C.c_double),
-                ("e_total", C.c_double), ("homo", C.c_double), ("lumo", C.c_double), ("electrons", C.c_double)]
+                ("e_total", C.c_double), ("homo", C.c_double), ("lumo", C.c_double), ("electrons", C.c_double),
+                ("mu", C.c_double), ("minus_ts", C.c_double), ("occ_last", C.c_double)]
 
 
 KSCF_FIELD_RHO, KSCF_FIELD_V_IN, KSCF_FIELD_V_H, KSCF_FIELD_V_XC = 0, 1, 2, 3
@@ -112,6 +113,7 @@ _sigs = {
     "kscf_scf_start": ([_vp, _vp, _i32, C.c_uint64, C.POINTER(_d)], _i32),
     "kscf_scf_step": ([_vp, C.POINTER(kscf_scf_report), C.POINTER(_d)], _i32),
     "kscf_scf_get": ([_vp, _i32, _vp], _i32),
+    "kscf_scf_evaluate": ([_vp, C.POINTER(kscf_scf_report), C.POINTER(_d), C.POINTER(_d)], _i32),
     "kscf_scf_hartree": ([_vp, _vp, _vp, C.POINTER(_i32)], _i32),
     "kscf_scf_free": ([_vp], _i32),
     "kscf_lda_xc": ([_vp, _vp, _vp, _vp, _vp], _i32),
@@ -422,9 +424,9 @@ def kscf_lda_xc(ham: Hamiltonian, rho, eps=None, vxc=None, stream=None):
 
 def scf_params(k: int, degree: int, dtype: int = KSCF_F64, gemm_mode: int = KSCF_GEMM_NATIVE, block: int = 0,
                first_iters: int = 4, history: int = 8, mix_alpha: float = 0.3, sre_tol_ry: float = 1e-4,
-               poisson_rtol: float = 1e-12, poisson_maxiter: int = 20000) -> kscf_scf_params:
+               poisson_rtol: float = 1e-12, poisson_maxiter: int = 20000, kT: float = 0.0) -> kscf_scf_params:
     return kscf_scf_params(k, degree, dtype, gemm_mode, block, first_iters, history, poisson_maxiter, mix_alpha,
-                           sre_tol_ry, poisson_rtol)
+                           sre_tol_ry, poisson_rtol, kT)
 
 
 class Scf:
@@ -464,6 +466,18 @@ class Scf:
         _check(lib.kscf_scf_step(self.handle, C.byref(rep), lam.ctypes.data_as(C.POINTER(C.c_double))))
         d = {f: getattr(rep, f) for f, _ in kscf_scf_report._fields_}
         d["lam"] = lam
+        return d
+
+    def evaluate(self):
+        """FP64 Rayleigh quotients, residual norms and energies of the last step's vectors."""
+        rep = kscf_scf_report()
+        lam = np.empty(self.k, dtype=np.float64)
+        res = np.empty(self.k, dtype=np.float64)
+        _check(lib.kscf_scf_evaluate(self.handle, C.byref(rep), lam.ctypes.data_as(C.POINTER(C.c_double)),
+                                     res.ctypes.data_as(C.POINTER(C.c_double))))
+        d = {f: getattr(rep, f) for f, _ in kscf_scf_report._fields_}
+        d["lam"] = lam
+        d["resid"] = res
         return d
 
     def run(self, max_steps: int = 40):

@@ -43,15 +43,24 @@ def sih4():
 R_SIH4, H_SIH4, K_SIH4, M_SIH4 = 8.0, 0.5, 8, 10
 
 
-@pytest.fixture(scope="module")
-def oracle_scf(species):
+def oracle_run(species, kT):
     from oracle.grid import sphere_grid
     from oracle.scf import scf
     from workloads import random_block_lex
     pos, z = sih4()
     g = sphere_grid(pos[0], R_SIH4, H_SIH4)
     X0 = random_block_lex(1, g.n, K_SIH4)
-    return scf(pos, z, species, R_SIH4, H_SIH4, K_SIH4, M_SIH4, X0, max_steps=40)
+    return scf(pos, z, species, R_SIH4, H_SIH4, K_SIH4, M_SIH4, X0, max_steps=40, kT=kT)
+
+
+@pytest.fixture(scope="module")
+def oracle_scf(species):
+    return oracle_run(species, 0.0)
+
+
+@pytest.fixture(scope="module")
+def oracle_scf_smeared(species):
+    return oracle_run(species, 0.01)
 
 
 def test_lda_matches_oracle(kscf, species):
@@ -103,38 +112,80 @@ def test_hartree_matches_oracle(kscf, species, brick):
     S.free()
 
 
-def run_gpu_scf(kscf, species, dtype, mode):
+def run_gpu_scf(kscf, species, dtype, mode, kT=0.0, system=None, evaluate=False):
     pos, z = sih4()
-    g, H = kscf.build_cluster(pos, z, species, R_SIH4, H_SIH4)
-    params = kscf.scf_params(K_SIH4, M_SIH4, dtype=dtype, gemm_mode=mode)
+    g, H = system if system is not None else kscf.build_cluster(pos, z, species, R_SIH4, H_SIH4)
+    params = kscf.scf_params(K_SIH4, M_SIH4, dtype=dtype, gemm_mode=mode, kT=kT)
     S = kscf.Scf(H, pos, z, species, params)
     S.start(seed=1)
     reps = S.run(40)
     lex, _ = g.slots()
     rho = from_slots(S.get(kscf.KSCF_FIELD_RHO).cpu().numpy(), lex, g.info["n_points"])
+    ev = S.evaluate() if evaluate else None
     S.free()
-    return reps, rho
+    return (reps, rho, ev) if evaluate else (reps, rho)
 
 
-def test_scf_fp64_matches_oracle(kscf, species, oracle_scf):
-    reps, rho = run_gpu_scf(kscf, species, kscf.KSCF_F64, kscf.KSCF_GEMM_NATIVE)
-    ref = oracle_scf["reports"]
+def compare_steps(reps, ref):
     assert len(reps) == len(ref), (len(reps), len(ref))
     for a, b in zip(reps, ref):
         assert a["step"] == b["step"]
         assert a["chefsi_iters"] == (4 if a["step"] == 1 else 1)
         assert abs(a["e_total"] - b["e_total"]) < 1e-8, (a["step"], a["e_total"], b["e_total"])
         assert abs(a["e_band"] - b["e_band"]) < 1e-8
+        assert abs(a["mu"] - b["mu"]) < 1e-8
+        assert abs(a["minus_ts"] - b["minus_ts"]) < 1e-10
         assert np.max(np.abs(a["lam"] - b["lam"])) < 1e-8
         assert abs(a["sre_ry"] - b["sre_ry"]) < 1e-6 * b["sre_ry"] + 1e-10
         assert abs(a["electrons"] - 8.0) < 1e-9
+
+
+def test_scf_smeared_fp64_matches_oracle(kscf, species, oracle_scf_smeared):
+    reps, rho = run_gpu_scf(kscf, species, kscf.KSCF_F64, kscf.KSCF_GEMM_NATIVE, kT=0.01)
+    compare_steps(reps, oracle_scf_smeared["reports"])
+    assert reps[-1]["converged"] == 1 and reps[-1]["minus_ts"] < 0
+    assert 0 <= reps[-1]["occ_last"] < 1e-2
+    assert np.max(np.abs(rho - oracle_scf_smeared["rho"])) < 1e-8 * np.max(oracle_scf_smeared["rho"])
+
+
+def test_scf_reuses_hamiltonian(kscf, species):
+    # a second SCF on the same Hamiltonian starts from the as-built ionic potential, not
+    # from the potential the first one left in it
+    pos, z = sih4()
+    system = kscf.build_cluster(pos, z, species, R_SIH4, H_SIH4)
+    first, _ = run_gpu_scf(kscf, species, kscf.KSCF_F64, kscf.KSCF_GEMM_NATIVE, system=system)
+    second, _ = run_gpu_scf(kscf, species, kscf.KSCF_F64, kscf.KSCF_GEMM_NATIVE, system=system)
+    assert len(first) == len(second)
+    assert abs(first[0]["e_total"] - second[0]["e_total"]) < 1e-10
+    assert abs(first[-1]["e_total"] - second[-1]["e_total"]) < 1e-10
+
+
+def test_scf_fp64_matches_oracle(kscf, species, oracle_scf):
+    reps, rho = run_gpu_scf(kscf, species, kscf.KSCF_F64, kscf.KSCF_GEMM_NATIVE)
+    ref = oracle_scf["reports"]
+    compare_steps(reps, ref)
     assert reps[-1]["converged"] == 1 and reps[-1]["sre_ry"] < 1e-4
     assert np.max(np.abs(rho - oracle_scf["rho"])) < 1e-8 * np.max(oracle_scf["rho"])
 
 
+def test_scf_fp64_evaluate_agrees_with_ritz_values(kscf, species, oracle_scf):
+    reps, rho, ev = run_gpu_scf(kscf, species, kscf.KSCF_F64, kscf.KSCF_GEMM_NATIVE, evaluate=True)
+    last = reps[-1]
+    # FP64 Rayleigh quotients of the Ritz vectors are the Ritz values themselves
+    assert np.max(np.abs(ev["lam"] - last["lam"])) < 1e-10
+    assert abs(ev["e_total"] - last["e_total"]) < 1e-9
+    # residuals: occupied states converged by the SCF's subspace iterations
+    assert np.all(ev["resid"][:4] < 1e-2) and np.all(ev["resid"] >= 0)
+
+
 def test_scf_mixed_precision_accuracy(kscf, species, oracle_scf):
-    reps, rho = run_gpu_scf(kscf, species, kscf.KSCF_F32, kscf.KSCF_GEMM_TENSOR)
+    reps, rho, ev = run_gpu_scf(kscf, species, kscf.KSCF_F32, kscf.KSCF_GEMM_TENSOR, evaluate=True)
     ref = oracle_scf["reports"][-1]
+    n_atoms = 5
+    # final FP64 evaluation: eigenvalues, gap and total energy against the FP64 oracle
+    assert abs(ev["e_total"] - ref["e_total"]) < 1e-6 * n_atoms
+    assert np.max(np.abs(np.sort(ev["lam"])[:4] - ref["lam"][:4])) < 1e-5
+    assert abs((ev["lumo"] - ev["homo"]) - (ref["lumo"] - ref["homo"])) < 1e-5
     last = reps[-1]
     assert last["converged"] == 1 and last["sre_ry"] < 1e-4
     assert len(reps) <= len(oracle_scf["reports"]) + 3
@@ -145,3 +196,4 @@ def test_scf_mixed_precision_accuracy(kscf, species, oracle_scf):
     assert abs(gap - gap_ref) < 1e-5
     h3 = H_SIH4 ** 3
     assert h3 * np.sum(np.abs(rho - oracle_scf["rho"])) < 1e-4 * 8.0
+    assert abs(last["electrons"] - 8.0) < 1e-9      # normalised Ritz vectors

@@ -80,3 +80,44 @@ def test_scf_sih4_converges():
     assert abs(rep[-1]["electrons"] - 8.0) < 1e-9
     assert abs(rep[-1]["e_total"] - rep[-2]["e_total"]) < 1e-5
     assert rep[-1]["lumo"] > rep[-1]["homo"]
+
+
+def test_fermi_occupations_closed_forms():
+    from oracle.scf import occupations
+    # two levels symmetric about 0 holding 2 electrons: mu = 0, f1 + f2 = 1
+    d, kT = 0.03, 0.01
+    occ, mu, mts = occupations(np.array([-d, d]), 2, kT)
+    f1 = 1.0 / (1.0 + np.exp(-d / kT))
+    assert abs(mu) < 1e-14
+    assert np.allclose(occ, [2 * f1, 2 * (1 - f1)], rtol=0, atol=1e-14)
+    assert abs(mts - 4.0 * kT * (f1 * np.log(f1) + (1 - f1) * np.log(1 - f1))) < 1e-15
+    # Mermin identity on a random spectrum: sum f lam - T S = -2 kT sum ln(1 + e^{-(lam-mu)/kT}) + mu N
+    rng = np.random.default_rng(2)
+    lam = np.sort(rng.uniform(-1.0, 0.5, 40))
+    ne, kT = 30, 0.02
+    occ, mu, mts = occupations(lam, ne, kT)
+    assert abs(occ.sum() - ne) < 1e-11
+    assert np.all(np.diff(occ) <= 0) and np.all((occ >= 0) & (occ <= 2))
+    omega = -2.0 * kT * np.sum(np.log1p(np.exp(-(lam - mu) / kT)))
+    assert abs((occ @ lam + mts) - (omega + mu * ne)) < 1e-12
+    # kT -> 0 with a gap: integer aufbau occupations
+    lam = np.array([-0.5, -0.4, -0.3, 0.2, 0.3])
+    occ, mu, mts = occupations(lam, 6, 1e-4)
+    assert np.allclose(occ, [2, 2, 2, 0, 0], atol=1e-12) and -0.3 < mu < 0.2 and abs(mts) < 1e-12
+    occ0, mu0, mts0 = occupations(lam, 6, 0.0)
+    assert np.array_equal(occ0, [2, 2, 2, 0, 0]) and mu0 == -0.3 and mts0 == 0.0
+
+
+def test_scf_sih4_smeared_converges():
+    from workloads import pseudo_params, random_block_lex
+    dd = 1.48 / 0.529177210903 / np.sqrt(3.0)
+    pos = np.array([[0.0, 0.0, 0.0], [dd, dd, dd], [dd, -dd, -dd], [-dd, dd, -dd], [-dd, -dd, dd]]) + 0.05
+    z = np.array([14, 1, 1, 1, 1], dtype=np.int32)
+    g = sphere_grid(pos[0], 8.0, 0.5)
+    X0 = random_block_lex(1, g.n, 8)
+    r = scf(pos, z, pseudo_params(), 8.0, 0.5, 8, 10, X0, max_steps=40, kT=0.01)
+    rep = r["reports"]
+    assert rep[-1]["sre_ry"] < 1e-4
+    assert abs(rep[-1]["electrons"] - 8.0) < 1e-9
+    assert rep[-1]["minus_ts"] < 0.0
+    assert rep[-1]["homo"] < rep[-1]["mu"] < rep[-1]["lumo"]
