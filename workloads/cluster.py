@@ -91,3 +91,27 @@ def n_occupied(z: np.ndarray) -> int:
     """Doubly occupied states (spin-degenerate, closed shell)."""
     ne = n_electrons(z)
     return (ne + 1) // 2
+
+
+def random_rotation(seed: int) -> np.ndarray:
+    """A seeded rotation matrix (QR of a Gaussian 3x3 with the signs fixed, det +1)."""
+    rng = np.random.default_rng(seed)
+    q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+    q = q * np.sign(np.diag(r))[None, :]
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+def training_clusters(n: int = 30, seed0: int = 1000, d_min_nm: float = 1.0, d_max_nm: float = 3.0):
+    """Seeded H-passivated Si clusters for training the learned SCF start: diameter drawn
+    uniformly in [d_min, d_max] nm, lattice rotated by a seeded rotation about the central
+    atom.  Returns a list of (seed, d_nm, positions_bohr, Z)."""
+    out = []
+    for i in range(n):
+        seed = seed0 + i
+        rng = np.random.default_rng(seed)
+        d = float(rng.uniform(d_min_nm, d_max_nm))
+        pos, z = cluster_for_diameter(d)
+        out.append((seed, d, pos @ random_rotation(seed).T, z))
+    return out
