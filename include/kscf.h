@@ -216,9 +216,12 @@ int kscf_chebyshev_filter(const kscf_ham* ham, void* X, int64_t ld, int k, int d
 /* In place Cholesky-QR (orthonormalisation step of CheFSI):
  *   S = h^3 X^T X (k x k, FP64 sums), S = R^T R (FP64 Cholesky), X <- X R^-1,
  * so that h^3 X^T X = I.  For F32 X the step is repeated once (CholeskyQR2,
- * Yamamoto et al. 2015), the second rotation applied as X + X (R2^-1 - I).  Returns KSCF_ERR_NOT_SPD if the Cholesky factorisation
- * fails (X rank-deficient); X is then left unchanged.  Synchronises on `stream` to
- * read the factorisation status. */
+ * Yamamoto et al. 2015), the second rotation applied as X + X (R2^-1 - I).  If the first
+ * factorisation fails (X numerically rank-deficient in its precision), the Gram matrix
+ * is recomputed with its diagonal raised by 16 k u max_i S_ii (u = 2^-24 for F32, 2^-53
+ * for F64) and factorised again (shifted Cholesky-QR, Fukaya et al. 2020), followed by
+ * one extra unshifted pass.  Returns KSCF_ERR_NOT_SPD if that fails too; X is then left
+ * unchanged.  Synchronises on `stream` to read the factorisation status. */
 int kscf_orthonormalize(const kscf_ham* ham, void* X, int64_t ld, int k, int dtype, int mode,
                         void* work, size_t work_bytes, void* stream);
 
@@ -294,7 +297,8 @@ int kscf_check_status(void);
  *          + h^3 sum rho eps_xc (- T S when kT > 0)   (band energy minus double counting)
  *   mixing Anderson mixing of V_in: F = V_out - V_in, history of the last `history`
  *          differences (dV_j, dF_j), g = argmin |F - sum_j g_j dF_j| by the normal
- *          equations, V_in <- V_in + alpha F - sum_j g_j (dV_j + alpha dF_j).
+ *          equations, V_in <- V_in + alpha P F - sum_j g_j (dV_j + alpha P dF_j) with P the
+ *          identity or the Kerker preconditioner (kerker_q0).
  *          (The paper names no mixing scheme; Anderson's is the Broyden-type method
  *          used here.)
  *   start  rho_0 = sum_a Z_a / (pi^{3/2} r_a^3) exp(-|r - R_a|^2 / r_a^2) (neutral-atom
@@ -325,6 +329,10 @@ typedef struct kscf_scf_params {
   double kT;               /* electronic temperature (Ha): 0 = the n_e/2 lowest states doubly
                               occupied; > 0 = Fermi-Dirac occupations 2 f((lambda - mu)/kT),
                               mu from sum = n_e, and e_total is the free energy E - T S */
+  double kerker_q0;        /* 0: plain Anderson; > 0: the residuals in the update are
+                              preconditioned, P F = F - q0^2 u with (-Lap_h + q0^2) u = F on
+                              the domain (Kerker's q^2/(q^2 + q0^2) damping of slowly
+                              varying residuals; CG to poisson_rtol) */
 } kscf_scf_params;
 
 typedef struct kscf_scf_report {
@@ -340,6 +348,8 @@ typedef struct kscf_scf_report {
   double mu;               /* Fermi level (kT > 0), else lambda_{n_occ-1} */
   double minus_ts;         /* -T S = 2 kT sum_i [f_i ln f_i + (1 - f_i) ln(1 - f_i)], f = occ/2 */
   double occ_last;         /* occupation of the highest Ritz state (k too small if not ~0) */
+  int32_t kerker_iters;    /* CG iterations of this step's Kerker solve (0 without) */
+  int32_t reserved;
 } kscf_scf_report;
 
 /* Creates the SCF state for the atoms the Hamiltonian was built from.  atoms/species
@@ -404,6 +414,52 @@ int kscf_scf_free(kscf_scf* scf);
  *   g = -0.1423, b1 = 1.0529, b2 = 0.3334, A = 0.0311, B = -0.048, C = 0.0020, D = -0.0116;
  * rho <= 1e-14 gives 0.  rho, eps (may be NULL), vxc: device, n_slots doubles. */
 int kscf_lda_xc(const kscf_ham* ham, const double* rho, double* eps, double* vxc, void* stream);
+
+/* ---------------------------------------------------------------------------------
+ * Learned SCF start.  The paper has no learned part: this is the library's own
+ * correction dV of the superposition starting potential (passed to kscf_scf_start),
+ * predicted per grid point by a small network from radial descriptors of the nearby
+ * atoms, trained on converged SCF potentials by the kernels below.
+ *
+ * Descriptors (KSCF_MLP_N_IN = 32 per slot): for species s (0 = Si, 1 = H) and radial
+ * centres c_q = q r_c / 15 (q = 0..15, r_c = 8 bohr),
+ *   D[s][16 s + q] = sum over atoms of species s within r < r_c of
+ *                    exp(-(r - c_q)^2 / (2 sigma^2)) (1 + cos(pi r / r_c)) / 2,  sigma = r_c/15.
+ * Network: x = (D - mu) * inv_sd;  h1 = tanh(x W1 + b1) (32 -> 128);
+ *   h2 = tanh(h1 W2 + b2) (128 -> 128);  y = h2 . w3 + b3.
+ * Parameters: one float vector of KSCF_MLP_N_PARAMS = 20865 values in the order
+ *   W1 (32 x 128 row-major), b1 (128), W2 (128 x 128 row-major), b2 (128), w3 (128), b3 (1).
+ * All arrays are caller-owned device memory. */
+#define KSCF_MLP_N_IN 32
+#define KSCF_MLP_N_HID 128
+#define KSCF_MLP_N_RADIAL 16
+#define KSCF_MLP_R_CUT 8.0
+#define KSCF_MLP_N_PARAMS (32 * 128 + 128 + 128 * 128 + 128 + 128 + 1)
+#define KSCF_MLP_FP32 0   /* FP32 weights, activations and arithmetic */
+#define KSCF_MLP_BF16 1   /* inference with weights, inputs and activations rounded to bf16,
+                             products accumulated in FP32 */
+
+/* D (device float, n_slots x 32 row-major) for the atoms (host array, Si and H only;
+ * positions in bohr); padding rows are zero.  Synchronous. */
+int kscf_descriptors(const kscf_ham* ham, const kscf_atom* atoms, int n_atoms, float* D, void* stream);
+
+/* y[p] = network(D[p]) for p < n (D: n x 32 floats; mu, inv_sd: 32 floats each). */
+int kscf_mlp_forward(const float* params, const float* mu, const float* inv_sd, const float* D, int64_t n,
+                     int precision, float* y, void* stream);
+
+/* Mean squared error L = (1/n) sum_p (y_p - t_p)^2 over the n rows of D and its gradient
+ * grad (KSCF_MLP_N_PARAMS floats, layout of params), FP32 arithmetic with the per-block
+ * partial gradients added in FP64 in block order (deterministic).  loss: device double
+ * or NULL.  work: at least kscf_mlp_work_size(n) bytes. */
+int kscf_mlp_work_size(int64_t n, size_t* bytes);
+int kscf_mlp_loss_grad(const float* params, const float* mu, const float* inv_sd, const float* D, const float* t,
+                       int64_t n, float* grad, double* loss, void* work, size_t work_bytes, void* stream);
+
+/* One Adam step (Kingma & Ba 2015) on params with moment buffers m, v (step >= 1):
+ *   m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ *   params -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps). */
+int kscf_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1,
+                  float beta2, float eps, void* stream);
 
 /* Hilbert index of brick coordinates (x, y, z) on the 2^bits cube, as used to order the
  * bricks (Skilling 2004 transpose algorithm; bits interleaved most significant first,

@@ -10,7 +10,9 @@ parametrised by Perdew & Zunger 1981) at fixed ions:
          gradients in float64
   V_xc   Slater exchange + PZ81 correlation (unpolarised, Hartree units)
   mixing Anderson mixing of the input potential (the Broyden-type quasi-Newton scheme;
-         history m, linear step alpha)
+         history m, linear step alpha), optionally with the Kerker preconditioner
+         P = (-Lap_h) (-Lap_h + q0^2)^-1 on the residuals (zero outside the domain):
+         P f = f - q0^2 u with (-Lap_h + q0^2) u = f (conjugate gradients)
   SRE    sqrt(h^3 sum_p rho_p (V_out - V_in)_p^2), reported in Ry (x 2); stop below 1e-4 Ry
   CheFSI four filter/Cholesky-QR/Rayleigh-Ritz iterations in the first SCF step, one in
          every later step (the schedule the paper states)
@@ -173,35 +175,61 @@ class Poisson:
         return x
 
 
-class Anderson:
-    """Anderson mixing of the input potential: V_next = V_in + a F - sum_j g_j (dV_j + a dF_j),
-    g = argmin |F - sum_j g_j dF_j|, F = V_out - V_in, history of the last m differences."""
+class Kerker:
+    """P f = f - q0^2 (-Lap_h + q0^2)^-1 f on the domain (zero outside): damps the slowly
+    varying part of a residual, P = q^2 / (q^2 + q0^2) for a plane wave of wave number q."""
 
-    def __init__(self, alpha: float = 0.3, history: int = 8):
+    def __init__(self, grid, q0: float, M: int = 6):
+        self.q0 = q0
+        self.A = 2.0 * kinetic_matrix(grid, M) + q0 * q0 * sp_identity(grid.n)
+
+    def apply(self, f: np.ndarray, tol: float = 1e-12) -> np.ndarray:
+        u, info = spla.cg(self.A, f, rtol=tol, atol=0.0, maxiter=20000)
+        if info != 0:
+            raise RuntimeError("Kerker CG did not converge")
+        return f - self.q0 * self.q0 * u
+
+
+def sp_identity(n):
+    import scipy.sparse as sp
+    return sp.identity(n, format="csr")
+
+
+class Anderson:
+    """Anderson mixing of the input potential: V_next = V_in + a P F - sum_j g_j (dV_j + a P dF_j),
+    g = argmin |F - sum_j g_j dF_j|, F = V_out - V_in, history of the last m differences;
+    P = identity or the Kerker preconditioner."""
+
+    def __init__(self, alpha: float = 0.3, history: int = 8, precond=None):
         self.alpha = alpha
         self.m = history
-        self.prev = None          # (V_in, F) of the previous step
-        self.dV, self.dF = [], []
+        self.precond = precond
+        self.prev = None          # (V_in, F, P F) of the previous step
+        self.dV, self.dF, self.dPF = [], [], []
 
     def step(self, v_in: np.ndarray, f: np.ndarray) -> np.ndarray:
+        pf = self.precond.apply(f) if self.precond is not None else f
         if self.prev is not None:
             self.dV.append(v_in - self.prev[0])
             self.dF.append(f - self.prev[1])
+            self.dPF.append(pf - self.prev[2])
             if len(self.dV) > self.m:
                 self.dV.pop(0)
                 self.dF.pop(0)
-        self.prev = (v_in.copy(), f.copy())
-        nxt = v_in + self.alpha * f
+                self.dPF.pop(0)
+        self.prev = (v_in.copy(), f.copy(), pf.copy())
+        nxt = v_in + self.alpha * pf
         if self.dF:
             DF = np.stack(self.dF, 1)
             DV = np.stack(self.dV, 1)
+            DPF = np.stack(self.dPF, 1)
             g = np.linalg.solve(DF.T @ DF, DF.T @ f)
-            nxt = nxt - (DV + self.alpha * DF) @ g
+            nxt = nxt - (DV + self.alpha * DPF) @ g
         return nxt
 
 
 def scf(atom_pos, atom_z, species, radius, h, k, degree, X0, max_steps=40, sre_tol_ry=1e-4,
-        first_iters=4, alpha=0.3, history=8, center=None, kT=0.0):
+        first_iters=4, alpha=0.3, history=8, center=None, kT=0.0, kerker_q0=0.0):
     """Run the SCF; returns a dict with per-step reports and the final state."""
     from .grid import sphere_grid
     from .potential import kb_projectors, local_potential
@@ -223,7 +251,7 @@ def scf(atom_pos, atom_z, species, radius, h, k, degree, X0, max_steps=40, sre_t
     H = Hamiltonian(g, v_in, P, E)
     X, _ = cf.cholesky_qr(np.array(X0, dtype=np.float64), H.h3)
     lam, X, _ = cf.rayleigh_ritz(H, X, H.h3)
-    mixer = Anderson(alpha, history)
+    mixer = Anderson(alpha, history, Kerker(g, kerker_q0) if kerker_q0 > 0 else None)
     reports = []
     vh_prev = vh
     for step in range(1, max_steps + 1):

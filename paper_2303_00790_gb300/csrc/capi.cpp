@@ -248,9 +248,13 @@ int gram(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t rows, i
   return KSCF_OK;
 }
 
-// One Cholesky-QR pass: S = h^3 X^T X, S = R^T R, X <- X R^-1.
+// One Cholesky-QR pass: S = h^3 X^T X, S = R^T R, X <- X R^-1.  When the factorisation
+// fails and `shifted` is non-null, the Gram matrix is recomputed and its diagonal shifted
+// by 16 k u max_i S_ii (u the unit roundoff of X's type) before a second attempt (shifted
+// Cholesky-QR, Fukaya, Kannan, Nakatsukasa, Yamamoto & Yanagisawa 2020); *shifted then
+// reports that X is not yet orthonormal and needs further passes.
 int cholqr_pass(const Ham& H, void* X, int64_t ld, int k, int dtype, int mode, const OrthoPlan& p, Carver& cv,
-                bool second_pass, cudaStream_t st) {
+                bool second_pass, cudaStream_t st, bool* shifted = nullptr) {
   cusolverDnHandle_t hs;
   int rc = solver_handle(&hs);
   if (rc) return rc;
@@ -273,9 +277,22 @@ int cholqr_pass(const Ham& H, void* X, int64_t ld, int k, int dtype, int mode, c
   KSCF_CUDA_TRY(cudaStreamSynchronize(st));
   rc = check_tc(mode, "Cholesky-QR");
   if (rc) return rc;
+  if (hinfo > 0 && shifted) {
+    rc = gram(X, ld, X, ld, rows, k, k, dtype, mode, h3, S, k, tcw, p.tc, st);
+    if (rc) return rc;
+    const double u = dtype == KSCF_F64 ? 0x1.0p-53 : 0x1.0p-24;
+    KSCF_CUDA_TRY(launch_shift_diag(S, k, 16.0 * k * u, st));
+    SOLVER_TRY(cusolverDnDpotrf(hs, CUBLAS_FILL_MODE_UPPER, k, S, k, (double*)lwork, (int)(p.lwork_bytes / 8 - 32),
+                                info));
+    KSCF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KSCF_CUDA_TRY(cudaStreamSynchronize(st));
+    rc = check_tc(mode, "Cholesky-QR");
+    if (rc) return rc;
+    if (hinfo == 0) *shifted = true;
+  }
   if (hinfo != 0) {
     set_error("Cholesky-QR: Gram matrix not positive definite (potrf info %d%s)", hinfo,
-              second_pass ? ", second pass" : "");
+              second_pass ? ", second pass" : (shifted ? ", also with the diagonal shift" : ""));
     return KSCF_ERR_NOT_SPD;
   }
   std::vector<char> hostw(std::max<size_t>(p.host_bytes, 1));
@@ -425,8 +442,13 @@ extern "C" int kscf_orthonormalize(const kscf_ham* ham, void* X, int64_t ld, int
   cudaStream_t st = (cudaStream_t)stream;
   KSCF_CUDA_TRY(launch_zero_rows(H, X, ld, k, dtype, st));
   Carver cv(work);
-  rc = cholqr_pass(H, X, ld, k, dtype, mode, p, cv, false, st);
+  bool shifted = false;
+  rc = cholqr_pass(H, X, ld, k, dtype, mode, p, cv, false, st, &shifted);
   if (rc) return rc;
+  if (shifted) {
+    rc = cholqr_pass(H, X, ld, k, dtype, mode, p, cv, false, st);
+    if (rc) return rc;
+  }
   if (dtype == KSCF_F32) rc = cholqr_pass(H, X, ld, k, dtype, mode, p, cv, true, st);
   return rc;
 }

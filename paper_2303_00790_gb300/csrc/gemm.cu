@@ -186,6 +186,29 @@ cudaError_t launch_symmetrize(double* C, int k, int64_t ldc, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// S[i][i] += rel * max_i S[i][i]  (one block; S column-major k x k)
+__global__ void shift_diag_kernel(double* S, int k, double rel) {
+  __shared__ double sm[32];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) m = fmax(m, S[(int64_t)i * k + i]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t = fmax(t, sm[w]);
+    sm[0] = t;
+  }
+  __syncthreads();
+  const double s = rel * sm[0];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) S[(int64_t)i * k + i] += s;
+}
+
+cudaError_t launch_shift_diag(double* S, int k, double rel, cudaStream_t st) {
+  shift_diag_kernel<<<1, 256, 0, st>>>(S, k, rel), count_launch();
+  return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void upper_kernel(const double* R, int k, T* out) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

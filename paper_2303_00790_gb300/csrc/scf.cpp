@@ -34,6 +34,7 @@ struct kscf_scf {
          *eps = nullptr, *f = nullptr;
   double *cg_b = nullptr, *cg_r = nullptr, *cg_p = nullptr, *cg_q = nullptr;
   double *v_prev = nullptr, *f_prev = nullptr, *dv = nullptr, *df = nullptr;  // dv, df: history x n
+  double *pf = nullptr, *pf_prev = nullptr, *dpf = nullptr, *ku = nullptr;  // Kerker: P F, history, solve
   double* part = nullptr;     // kScfRedBlocks x 44 partial sums
   double* part_bb = nullptr;  // kScfRedBlocks
   double* part_rr[2] = {nullptr, nullptr};
@@ -73,7 +74,8 @@ void free_scf(kscf_scf* S) {
                  S->vxc,    S->eps,    S->f,      S->cg_b,    S->cg_r,       S->cg_p,       S->cg_q,
                  S->v_prev, S->f_prev, S->dv,     S->df,      S->part,       S->part_bb,    S->part_rr[0],
                  S->part_rr[1], S->part_pq, S->small, S->d_iters, S->P.d_grel, S->P.d_vghost, S->P.d_gptr,
-                 S->P.d_gidx, S->P.d_gw, S->work, S->part_col, S->colsq, S->d_occ};
+                 S->P.d_gidx, S->P.d_gw, S->work, S->part_col, S->colsq, S->d_occ,
+                 S->pf, S->pf_prev, S->dpf, S->ku};
   for (void* q : dev)
     if (q) cudaFree(q);
   if (S->host) cudaFreeHost(S->host);
@@ -163,16 +165,15 @@ int read_iters(kscf_scf* S, int* it) {
   return KSCF_OK;
 }
 
-// -Lap_h x = 4 pi rho (+ ghost terms) by CG from the guess in x.
-int hartree(kscf_scf* S, const double* rho, double* x, int* iters_out) {
+// CG on (-Lap_h + shift) x = b for the right-hand side already in S->cg_b (its partial
+// squares in S->part_bb), from the guess in x.
+int cg_solve(kscf_scf* S, double shift, double* x, int* iters_out, const char* what) {
   const Ham& H = S->ham->h;
   cudaStream_t st = S->st;
   KSCF_CUDA_TRY(launch_mask_v(H, x, x, st));
-  KSCF_CUDA_TRY(launch_ghost_values(H, rho, S->rel, S->P, S->part, S->small + kMom, st));
-  KSCF_CUDA_TRY(launch_poisson_rhs(H, rho, S->P, S->cg_b, S->part_bb, st));
   KSCF_CUDA_TRY(cudaMemsetAsync(S->d_iters, 0, sizeof(int), st));
   int cur = 0;
-  KSCF_CUDA_TRY(launch_cg_init(H, x, S->cg_b, S->cg_r, S->cg_p, S->part_rr[cur], st));
+  KSCF_CUDA_TRY(launch_cg_init(H, shift, x, S->cg_b, S->cg_r, S->cg_p, S->part_rr[cur], st));
   const double rtol = S->p.poisson_rtol;
   double cg[2];
   KSCF_CUDA_TRY(launch_finalize_partials(S->part_rr[cur], kScfRedBlocks, 1, S->small + kCg, st));
@@ -180,11 +181,11 @@ int hartree(kscf_scf* S, const double* rho, double* x, int* iters_out) {
   int rc = sync_read(S, S->small + kCg, 2, cg);
   if (rc) return rc;
   if (!std::isfinite(cg[0]) || !std::isfinite(cg[1])) {
-    set_error("kscf_scf: non-finite Poisson right-hand side or guess");
+    set_error("kscf_scf: non-finite %s right-hand side or guess", what);
     return KSCF_ERR_NONFINITE;
   }
   if (iters_out) *iters_out = 0;
-  if (cg[1] == 0.0) {  // rho = 0 and no boundary values: V_H = 0
+  if (cg[1] == 0.0) {  // zero right-hand side: zero solution
     KSCF_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * S->n, st));
     return KSCF_OK;
   }
@@ -196,12 +197,12 @@ int hartree(kscf_scf* S, const double* rho, double* x, int* iters_out) {
       rc = read_iters(S, &it);
       if (rc) return rc;
       if (iters_out) *iters_out = it;
-      set_error("kscf_scf: Poisson CG not converged after %d iterations (|r|/|b| = %.3e)", it,
+      set_error("kscf_scf: %s CG not converged after %d iterations (|r|/|b| = %.3e)", what, it,
                 std::sqrt(cg[0] / cg[1]));
       return KSCF_ERR_NO_CONVERGE;
     }
     for (int i = 0; i < batch; i++) {
-      KSCF_CUDA_TRY(launch_cg_iteration(H, S->part_bb, rtol, x, S->cg_r, S->cg_p, S->cg_q, S->part_rr[cur],
+      KSCF_CUDA_TRY(launch_cg_iteration(H, shift, S->part_bb, rtol, x, S->cg_r, S->cg_p, S->cg_q, S->part_rr[cur],
                                         S->part_pq, S->part_rr[cur ^ 1], S->d_iters, st));
       cur ^= 1;
     }
@@ -210,7 +211,7 @@ int hartree(kscf_scf* S, const double* rho, double* x, int* iters_out) {
     rc = sync_read(S, S->small + kCg, 1, cg);
     if (rc) return rc;
     if (!std::isfinite(cg[0])) {
-      set_error("kscf_scf: Poisson CG produced a non-finite residual");
+      set_error("kscf_scf: %s CG produced a non-finite residual", what);
       return KSCF_ERR_NONFINITE;
     }
   }
@@ -218,6 +219,27 @@ int hartree(kscf_scf* S, const double* rho, double* x, int* iters_out) {
   rc = read_iters(S, &it);
   if (rc) return rc;
   if (iters_out) *iters_out = it;
+  return KSCF_OK;
+}
+
+// -Lap_h x = 4 pi rho (+ ghost terms) by CG from the guess in x.
+int hartree(kscf_scf* S, const double* rho, double* x, int* iters_out) {
+  const Ham& H = S->ham->h;
+  cudaStream_t st = S->st;
+  KSCF_CUDA_TRY(launch_ghost_values(H, rho, S->rel, S->P, S->part, S->small + kMom, st));
+  KSCF_CUDA_TRY(launch_poisson_rhs(H, rho, S->P, S->cg_b, S->part_bb, st));
+  return cg_solve(S, 0.0, x, iters_out, "Poisson");
+}
+
+// Kerker preconditioner: pf = f - q0^2 u with (-Lap_h + q0^2) u = f (u warm-started
+// from the previous step's solution).
+int kerker(kscf_scf* S, const double* f, double* pf, int* iters_out) {
+  const Ham& H = S->ham->h;
+  const double q2 = S->p.kerker_q0 * S->p.kerker_q0;
+  KSCF_CUDA_TRY(launch_rhs_copy(H, f, S->cg_b, S->part_bb, S->st));
+  int rc = cg_solve(S, q2, S->ku, iters_out, "Kerker");
+  if (rc) return rc;
+  KSCF_CUDA_TRY(launch_lincomb(H, f, S->ku, -q2, pf, S->st));
   return KSCF_OK;
 }
 
@@ -334,7 +356,7 @@ extern "C" int kscf_scf_create(kscf_ham* ham, const kscf_atom* atoms, int n_atom
       (p.gemm_mode == KSCF_GEMM_TENSOR && p.dtype != KSCF_F32) || p.degree < 1 || p.first_iters < 1 ||
       p.history < 1 || p.history > kAndersonMax || !(p.mix_alpha > 0.0 && p.mix_alpha <= 1.0) ||
       !(p.sre_tol_ry > 0.0) || !(p.poisson_rtol > 0.0) || p.poisson_maxiter < 1 || p.block < 0 || ld < p.k ||
-      !(p.kT >= 0.0) || !std::isfinite(p.kT)) {
+      !(p.kT >= 0.0) || !std::isfinite(p.kT) || !(p.kerker_q0 >= 0.0) || !std::isfinite(p.kerker_q0)) {
     set_error("kscf_scf_create: invalid parameters");
     return KSCF_ERR_INVALID;
   }
@@ -388,6 +410,14 @@ extern "C" int kscf_scf_create(kscf_ham* ham, const kscf_atom* atoms, int n_atom
       if (e == cudaSuccess) e = dalloc(v, (size_t)n);
     if (e == cudaSuccess) e = dalloc(&S->dv, (size_t)p.history * n);
     if (e == cudaSuccess) e = dalloc(&S->df, (size_t)p.history * n);
+    if (p.kerker_q0 > 0.0) {
+      double** kv[] = {&S->pf, &S->pf_prev, &S->ku};
+      for (double** v : kv) {
+        if (e == cudaSuccess) e = dalloc(v, (size_t)n);
+        if (e == cudaSuccess) e = cudaMemsetAsync(*v, 0, sizeof(double) * n, S->st);
+      }
+      if (e == cudaSuccess) e = dalloc(&S->dpf, (size_t)p.history * n);
+    }
     if (e == cudaSuccess) e = dalloc(&S->rel, 3 * (size_t)n);
     if (e == cudaSuccess) e = dalloc(&S->atoms, at.size());
     if (e == cudaSuccess) e = dalloc(&S->part, (size_t)kScfRedBlocks * 48);
@@ -579,11 +609,17 @@ extern "C" int kscf_scf_step(kscf_scf* scf, kscf_scf_report* report, double* eig
   S->stepped = true;
   if (report->converged) return KSCF_OK;
 
-  // Anderson mixing of V_in
+  // Anderson mixing of V_in (with the Kerker-preconditioned residual when q0 > 0)
   const int m = p.history;
   const int slot = S->ring_next;
-  KSCF_CUDA_TRY(launch_anderson_push(S->n, S->v_in, S->f, S->v_prev, S->f_prev, S->dv + (size_t)slot * S->n,
-                                     S->df + (size_t)slot * S->n, S->have_prev, st));
+  const bool kerk = p.kerker_q0 > 0.0;
+  if (kerk) {
+    rc = kerker(S, S->f, S->pf, &report->kerker_iters);
+    if (rc) return rc;
+  }
+  KSCF_CUDA_TRY(launch_anderson_push(S->n, S->v_in, S->f, kerk ? S->pf : nullptr, S->v_prev, S->f_prev, S->pf_prev,
+                                     S->dv + (size_t)slot * S->n, S->df + (size_t)slot * S->n,
+                                     kerk ? S->dpf + (size_t)slot * S->n : nullptr, S->have_prev, st));
   if (S->have_prev) {
     if ((int)S->order.size() == m) S->order.erase(S->order.begin());
     S->order.push_back(slot);
@@ -611,7 +647,8 @@ extern "C" int kscf_scf_step(kscf_scf* scf, kscf_scf_report* report, double* eig
       return KSCF_ERR_NONFINITE;
     }
   }
-  KSCF_CUDA_TRY(launch_anderson_update(H, cols, p.mix_alpha, S->dv, S->df, S->f, S->v_in, st));
+  KSCF_CUDA_TRY(launch_anderson_update(H, cols, p.mix_alpha, S->dv, kerk ? S->dpf : S->df, kerk ? S->pf : S->f,
+                                       S->v_in, st));
   return KSCF_OK;
 }
 

@@ -37,12 +37,17 @@ cudaError_t launch_atomic_density(const Ham& H, const double* rel, const double*
 cudaError_t launch_lda(const Ham& H, const double* rho, double* eps, double* vxc, cudaStream_t st);
 cudaError_t launch_poisson_rhs(const Ham& H, const double* rho, const PoissonPlan& P, double* b, double* part_bb,
                                cudaStream_t st);
-cudaError_t launch_cg_init(const Ham& H, double* x, const double* b, double* r, double* p, double* part_rr,
-                           cudaStream_t st);
+// CG on A x = b with A = -Lap_h + shift (zero outside the domain)
+cudaError_t launch_cg_init(const Ham& H, double shift, double* x, const double* b, double* r, double* p,
+                           double* part_rr, cudaStream_t st);
 // one CG iteration (three kernels); every kernel returns at once when r.r < rtol^2 b.b
-cudaError_t launch_cg_iteration(const Ham& H, const double* part_bb, double rtol, double* x, double* r, double* p,
-                                double* q, const double* part_rr, double* part_pq, double* part_rr_next, int* iters,
-                                cudaStream_t st);
+cudaError_t launch_cg_iteration(const Ham& H, double shift, const double* part_bb, double rtol, double* x, double* r,
+                                double* p, double* q, const double* part_rr, double* part_pq, double* part_rr_next,
+                                int* iters, cudaStream_t st);
+// b = f on the domain, partial b.b
+cudaError_t launch_rhs_copy(const Ham& H, const double* f, double* b, double* part_bb, cudaStream_t st);
+// out = a + c b on the domain
+cudaError_t launch_lincomb(const Ham& H, const double* a, const double* b, double c, double* out, cudaStream_t st);
 cudaError_t launch_ghost_values(const Ham& H, const double* rho, const double* rel, const PoissonPlan& P,
                                 double* part, double* mom, cudaStream_t st);
 cudaError_t launch_residual(const Ham& H, const double* rho, const double* v_in, const double* v_ion, const double* vh,
@@ -62,11 +67,12 @@ cudaError_t launch_col_resid(const double* X, const double* HX, int64_t ld, int6
 cudaError_t launch_widen(const float* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int k,
                          cudaStream_t st);
 cudaError_t launch_add2(const Ham& H, const double* a, const double* b, double* out, cudaStream_t st);
-cudaError_t launch_anderson_push(int64_t n, const double* v_in, const double* f, double* v_prev, double* f_prev,
-                                 double* dv, double* df, bool have_prev, cudaStream_t st);
+cudaError_t launch_anderson_push(int64_t n, const double* v_in, const double* f, const double* pf, double* v_prev,
+                                 double* f_prev, double* pf_prev, double* dv, double* df, double* dpf, bool have_prev,
+                                 cudaStream_t st);
 cudaError_t launch_anderson_gram(const AndersonCols& cols, const double* df, const double* f, int64_t n,
                                  double* part, double* out, cudaStream_t st);
 cudaError_t launch_anderson_update(const Ham& H, const AndersonCols& cols, double alpha, const double* dv,
-                                   const double* df, const double* f, double* v, cudaStream_t st);
+                                   const double* dpf, const double* pf, double* v, cudaStream_t st);
 
 }  // namespace kscf

@@ -151,13 +151,15 @@ cudaError_t launch_lda(const Ham& H, const double* rho, double* eps, double* vxc
 }
 
 // ---------------------------------------------------------------------------
-// Poisson operator A x = -Lap_h x on the domain (zero outside: padding slots of x hold
-// zero and missing bricks read as zero).  cw[k] = -w_k / h^2 (k = 0..6); the centre
-// term uses 3 cw[0].  One thread per slot.
+// CG operator A x = -Lap_h x + shift x on the domain (zero outside: padding slots of x
+// hold zero and missing bricks read as zero): shift 0 for the Poisson problem, q0^2 for
+// the Kerker preconditioner.  cw[k] = -w_k / h^2 (k = 0..6); the centre term uses
+// 3 cw[0].  One thread per slot.
 struct LapArgs {
   const int32_t* nbr;
   const uint8_t* mask;
   double cw[7];
+  double shift;
   int64_t n;
 };
 
@@ -168,7 +170,7 @@ __device__ __forceinline__ double lap_at(const LapArgs& a, const double* __restr
   const int li = (int)(s - brick * B3);
   const int l[3] = {li % B, (li / B) % B, li / (B * B)};
   const int stride[3] = {1, B, B * B};
-  double acc = 3.0 * a.cw[0] * x[s];
+  double acc = (3.0 * a.cw[0] + a.shift) * x[s];
 #pragma unroll
   for (int ax = 0; ax < 3; ax++) {
 #pragma unroll
@@ -298,8 +300,9 @@ __global__ void __launch_bounds__(kScfThreads) cg_dir_kernel(CgState c, int64_t 
     p[s] = r[s] + beta * p[s];
 }
 
-static LapArgs lap_args(const Ham& H) {
+static LapArgs lap_args(const Ham& H, double shift) {
   LapArgs a;
+  a.shift = shift;
   a.nbr = H.d_nbr;
   a.mask = H.d_mask;
   // H.stencil[k] = -1/2 w_k / h^2, so -w_k / h^2 = 2 H.stencil[k]
@@ -316,9 +319,9 @@ cudaError_t launch_poisson_rhs(const Ham& H, const double* rho, const PoissonPla
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_init(const Ham& H, double* x, const double* b, double* r, double* p, double* part_rr,
-                           cudaStream_t st) {
-  const LapArgs a = lap_args(H);
+cudaError_t launch_cg_init(const Ham& H, double shift, double* x, const double* b, double* r, double* p,
+                           double* part_rr, cudaStream_t st) {
+  const LapArgs a = lap_args(H, shift);
   if (H.grid.B == 8)
     cg_init_kernel<8><<<kScfRedBlocks, kScfThreads, 0, st>>>(a, x, b, r, p, part_rr), count_launch();
   else
@@ -326,10 +329,10 @@ cudaError_t launch_cg_init(const Ham& H, double* x, const double* b, double* r, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_iteration(const Ham& H, const double* part_bb, double rtol, double* x, double* r, double* p,
-                                double* q, const double* part_rr, double* part_pq, double* part_rr_next, int* iters,
-                                cudaStream_t st) {
-  const LapArgs a = lap_args(H);
+cudaError_t launch_cg_iteration(const Ham& H, double shift, const double* part_bb, double rtol, double* x, double* r,
+                                double* p, double* q, const double* part_rr, double* part_pq, double* part_rr_next,
+                                int* iters, cudaStream_t st) {
+  const LapArgs a = lap_args(H, shift);
   CgState c;
   c.part_bb = part_bb;
   c.rtol2 = rtol * rtol;
@@ -341,6 +344,37 @@ cudaError_t launch_cg_iteration(const Ham& H, const double* part_bb, double rtol
   cg_update_kernel<<<kScfRedBlocks, kScfThreads, 0, st>>>(c, n, x, r, p, q, part_rr, part_pq, part_rr_next, iters),
       count_launch();
   cg_dir_kernel<<<kScfRedBlocks, kScfThreads, 0, st>>>(c, n, r, p, part_rr, part_rr_next), count_launch();
+  return cudaGetLastError();
+}
+
+// b = f on the domain (0 outside); partial b.b
+__global__ void __launch_bounds__(kScfThreads) rhs_copy_kernel(const double* __restrict__ f,
+                                                               const uint8_t* __restrict__ mask, int64_t n,
+                                                               double* __restrict__ b, double* __restrict__ part) {
+  double acc[1] = {0.0};
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    const double v = mask[s] ? f[s] : 0.0;
+    b[s] = v;
+    acc[0] += v * v;
+  }
+  block_partials<1>(acc, part);
+}
+
+cudaError_t launch_rhs_copy(const Ham& H, const double* f, double* b, double* part_bb, cudaStream_t st) {
+  rhs_copy_kernel<<<kScfRedBlocks, kScfThreads, 0, st>>>(f, H.d_mask, H.grid.n_slots, b, part_bb), count_launch();
+  return cudaGetLastError();
+}
+
+// out = a + c b (0 outside the domain)
+__global__ void lincomb_kernel(const uint8_t* __restrict__ mask, const double* __restrict__ a,
+                               const double* __restrict__ b, double c, int64_t n, double* __restrict__ out) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) out[s] = mask[s] ? a[s] + c * b[s] : 0.0;
+}
+
+cudaError_t launch_lincomb(const Ham& H, const double* a, const double* b, double c, double* out, cudaStream_t st) {
+  const int64_t n = H.grid.n_slots;
+  lincomb_kernel<<<nblk(n, 256), 256, 0, st>>>(H.d_mask, a, b, c, n, out), count_launch();
   return cudaGetLastError();
 }
 
@@ -550,10 +584,13 @@ cudaError_t launch_widen(const float* src, int64_t lds, double* dst, int64_t ldd
 
 // ---------------------------------------------------------------------------
 // Anderson mixing.
-// New history column: dV = V_in - V_prev, dF = F - F_prev; then V_prev = V_in, F_prev = F.
+// New history column: dV = V_in - V_prev, dF = F - F_prev (and dPF = PF - PF_prev when
+// the residual is preconditioned); then V_prev = V_in, F_prev = F, PF_prev = PF.
 __global__ void anderson_push_kernel(int64_t n, const double* __restrict__ v_in, const double* __restrict__ f,
-                                     double* __restrict__ v_prev, double* __restrict__ f_prev,
-                                     double* __restrict__ dv, double* __restrict__ df, int have_prev) {
+                                     const double* __restrict__ pf, double* __restrict__ v_prev,
+                                     double* __restrict__ f_prev, double* __restrict__ pf_prev,
+                                     double* __restrict__ dv, double* __restrict__ df, double* __restrict__ dpf,
+                                     int have_prev) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const double vi = v_in[s], fi = f[s];
@@ -563,12 +600,18 @@ __global__ void anderson_push_kernel(int64_t n, const double* __restrict__ v_in,
   }
   v_prev[s] = vi;
   f_prev[s] = fi;
+  if (pf) {
+    const double pi = pf[s];
+    if (have_prev) dpf[s] = pi - pf_prev[s];
+    pf_prev[s] = pi;
+  }
 }
 
-cudaError_t launch_anderson_push(int64_t n, const double* v_in, const double* f, double* v_prev, double* f_prev,
-                                 double* dv, double* df, bool have_prev, cudaStream_t st) {
-  anderson_push_kernel<<<nblk(n, 256), 256, 0, st>>>(n, v_in, f, v_prev, f_prev, dv, df, have_prev ? 1 : 0),
-      count_launch();
+cudaError_t launch_anderson_push(int64_t n, const double* v_in, const double* f, const double* pf, double* v_prev,
+                                 double* f_prev, double* pf_prev, double* dv, double* df, double* dpf, bool have_prev,
+                                 cudaStream_t st) {
+  anderson_push_kernel<<<nblk(n, 256), 256, 0, st>>>(n, v_in, f, pf, v_prev, f_prev, pf_prev, dv, df, dpf,
+                                                     have_prev ? 1 : 0), count_launch();
   return cudaGetLastError();
 }
 
@@ -606,7 +649,8 @@ cudaError_t launch_anderson_gram(const AndersonCols& cols, const double* df, con
   return launch_finalize_partials(part, kScfRedBlocks, NV, out, st);
 }
 
-// V_next = V_in + alpha F - sum_j g_j (dV_j + alpha dF_j)   (in place on v)
+// V_next = V_in + alpha PF - sum_j g_j (dV_j + alpha dPF_j)   (in place on v; PF = F and
+// dPF = dF without a preconditioner)
 __global__ void anderson_update_kernel(AndersonCols cols, double alpha, const uint8_t* __restrict__ mask, int64_t n,
                                        const double* __restrict__ dv, const double* __restrict__ df,
                                        const double* __restrict__ f, double* __restrict__ v) {
@@ -625,7 +669,9 @@ __global__ void anderson_update_kernel(AndersonCols cols, double alpha, const ui
 }
 
 cudaError_t launch_anderson_update(const Ham& H, const AndersonCols& cols, double alpha, const double* dv,
-                                   const double* df, const double* f, double* v, cudaStream_t st) {
+                                   const double* dpf, const double* pf, double* v, cudaStream_t st) {
+  const double* df = dpf;
+  const double* f = pf;
   const int64_t n = H.grid.n_slots;
   anderson_update_kernel<<<nblk(n, 256), 256, 0, st>>>(cols, alpha, H.d_mask, n, dv, df, f, v), count_launch();
   return cudaGetLastError();

@@ -58,14 +58,15 @@ class kscf_scf_params(C.Structure):
     _fields_ = [("k", C.c_int32), ("degree", C.c_int32), ("dtype", C.c_int32), ("gemm_mode", C.c_int32),
                 ("block", C.c_int32), ("first_iters", C.c_int32), ("history", C.c_int32),
                 ("poisson_maxiter", C.c_int32), ("mix_alpha", C.c_double), ("sre_tol_ry", C.c_double),
-                ("poisson_rtol", C.c_double), ("kT", C.c_double)]
+                ("poisson_rtol", C.c_double), ("kT", C.c_double), ("kerker_q0", C.c_double)]
 
 
 class kscf_scf_report(C.Structure):
     _fields_ = [("step", C.c_int32), ("converged", C.c_int32), ("poisson_iters", C.c_int32),
                 ("chefsi_iters", C.c_int32), ("sre_ry", C.c_double), ("e_band", C.c_double),
                 ("e_total", C.c_double), ("homo", C.c_double), ("lumo", C.c_double), ("electrons", C.c_double),
-                ("mu", C.c_double), ("minus_ts", C.c_double), ("occ_last", C.c_double)]
+                ("mu", C.c_double), ("minus_ts", C.c_double), ("occ_last", C.c_double),
+                ("kerker_iters", C.c_int32), ("reserved", C.c_int32)]
 
 
 KSCF_FIELD_RHO, KSCF_FIELD_V_IN, KSCF_FIELD_V_H, KSCF_FIELD_V_XC = 0, 1, 2, 3
@@ -117,6 +118,11 @@ _sigs = {
     "kscf_scf_hartree": ([_vp, _vp, _vp, C.POINTER(_i32)], _i32),
     "kscf_scf_free": ([_vp], _i32),
     "kscf_lda_xc": ([_vp, _vp, _vp, _vp, _vp], _i32),
+    "kscf_descriptors": ([_vp, C.POINTER(kscf_atom), _i32, _vp, _vp], _i32),
+    "kscf_mlp_forward": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp], _i32),
+    "kscf_mlp_work_size": ([_i64, C.POINTER(_sz)], _i32),
+    "kscf_mlp_loss_grad": ([_vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _sz, _vp], _i32),
+    "kscf_mlp_adam": ([_vp, _vp, _vp, _vp, _i32, C.c_float, C.c_float, C.c_float, C.c_float, _vp], _i32),
 }
 for _name, (_args, _res) in _sigs.items():
     _f = getattr(lib, _name)
@@ -424,9 +430,10 @@ def kscf_lda_xc(ham: Hamiltonian, rho, eps=None, vxc=None, stream=None):
 
 def scf_params(k: int, degree: int, dtype: int = KSCF_F64, gemm_mode: int = KSCF_GEMM_NATIVE, block: int = 0,
                first_iters: int = 4, history: int = 8, mix_alpha: float = 0.3, sre_tol_ry: float = 1e-4,
-               poisson_rtol: float = 1e-12, poisson_maxiter: int = 20000, kT: float = 0.0) -> kscf_scf_params:
+               poisson_rtol: float = 1e-12, poisson_maxiter: int = 20000, kT: float = 0.0,
+               kerker_q0: float = 0.0) -> kscf_scf_params:
     return kscf_scf_params(k, degree, dtype, gemm_mode, block, first_iters, history, poisson_maxiter, mix_alpha,
-                           sre_tol_ry, poisson_rtol, kT)
+                           sre_tol_ry, poisson_rtol, kT, kerker_q0)
 
 
 class Scf:
@@ -514,6 +521,58 @@ class Scf:
             self.free()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ learned start
+KSCF_MLP_N_IN, KSCF_MLP_N_HID = 32, 128
+KSCF_MLP_N_PARAMS = 32 * 128 + 128 + 128 * 128 + 128 + 128 + 1
+KSCF_MLP_FP32, KSCF_MLP_BF16 = 0, 1
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def kscf_descriptors(ham: Hamiltonian, atom_pos, atom_z, D=None, stream=None):
+    """(n_slots, 32) float32 device tensor of radial descriptors."""
+    torch = _torch()
+    if D is None:
+        D = torch.empty((ham.n_slots, KSCF_MLP_N_IN), dtype=torch.float32, device="cuda")
+    atoms, n = atom_array(atom_pos, atom_z)
+    _check(lib.kscf_descriptors(ham.handle, atoms, n, _p(D), _stream(stream)))
+    return D
+
+
+def kscf_mlp_forward(params, mu, inv_sd, D, precision: int = KSCF_MLP_FP32, y=None, stream=None):
+    torch = _torch()
+    n = D.shape[0]
+    if y is None:
+        y = torch.empty(n, dtype=torch.float32, device="cuda")
+    _check(lib.kscf_mlp_forward(_p(params), _p(mu), _p(inv_sd), _p(D), n, precision, _p(y), _stream(stream)))
+    return y
+
+
+def kscf_mlp_work_size(n: int) -> int:
+    b = C.c_size_t()
+    _check(lib.kscf_mlp_work_size(n, C.byref(b)))
+    return b.value
+
+
+def kscf_mlp_loss_grad(params, mu, inv_sd, D, t, grad=None, loss=None, work=None, stream=None):
+    torch = _torch()
+    n = D.shape[0]
+    if grad is None:
+        grad = torch.empty(KSCF_MLP_N_PARAMS, dtype=torch.float32, device="cuda")
+    if work is None:
+        work = torch.empty(kscf_mlp_work_size(n), dtype=torch.uint8, device="cuda")
+    _check(lib.kscf_mlp_loss_grad(_p(params), _p(mu), _p(inv_sd), _p(D), _p(t), n, _p(grad), _p(loss), _p(work),
+                                  work.numel(), _stream(stream)))
+    return grad
+
+
+def kscf_mlp_adam(params, grad, m, v, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                  eps: float = 1e-8, stream=None):
+    _check(lib.kscf_mlp_adam(_p(params), _p(grad), _p(m), _p(v), step, lr, beta1, beta2, eps, _stream(stream)))
 
 
 # ------------------------------------------------------------------ convenience

@@ -294,3 +294,22 @@ def test_f32_brick_kernel_paths(kscf, system, k, ldpad, block):
     ref = chebyshev_filter(system["OH"], X, 10, -0.5, b, -9.0)
     colmax = np.max(np.abs(ref), axis=0)
     assert np.all(np.max(np.abs(got - ref), axis=0) <= 1e-4 * colmax)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_orthonormalize_recovers_from_rank_deficiency(kscf, species, mode):
+    # two columns equal up to a 1e-6 perturbation: in FP32 the Gram matrix is singular to
+    # working precision, so plain Cholesky-QR fails; the shifted retry still returns an
+    # orthonormal basis of the span
+    pos, z = small_cluster()
+    g, H = kscf.build_cluster(pos, z, species, 8.0, 0.7)
+    k = 48
+    X = torch.zeros((g.info["n_slots"], 64), dtype=torch.float32, device="cuda")
+    kscf.kscf_random_subspace(H, X[:, :k], seed=3)
+    noise = torch.zeros_like(X[:, 0])
+    kscf.kscf_random_subspace(H, noise[:, None], seed=4)
+    X[:, 7] = X[:, 3] + 1e-6 * noise
+    kscf.kscf_orthonormalize(H, X[:, :k], mode=mode)
+    G = kscf.kscf_gram(X[:, :k], X[:, :k], scale=H.h3).cpu().numpy()
+    assert np.max(np.abs(G - np.eye(k))) < 1e-4
+    assert torch.all(torch.isfinite(X)).item()

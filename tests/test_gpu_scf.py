@@ -43,14 +43,20 @@ def sih4():
 R_SIH4, H_SIH4, K_SIH4, M_SIH4 = 8.0, 0.5, 8, 10
 
 
-def oracle_run(species, kT):
+def oracle_run(species, kT, kerker_q0=0.0, alpha=0.3):
     from oracle.grid import sphere_grid
     from oracle.scf import scf
     from workloads import random_block_lex
     pos, z = sih4()
     g = sphere_grid(pos[0], R_SIH4, H_SIH4)
     X0 = random_block_lex(1, g.n, K_SIH4)
-    return scf(pos, z, species, R_SIH4, H_SIH4, K_SIH4, M_SIH4, X0, max_steps=40, kT=kT)
+    return scf(pos, z, species, R_SIH4, H_SIH4, K_SIH4, M_SIH4, X0, max_steps=40, kT=kT, kerker_q0=kerker_q0,
+               alpha=alpha)
+
+
+@pytest.fixture(scope="module")
+def oracle_scf_kerker(species):
+    return oracle_run(species, 0.0, kerker_q0=0.8, alpha=0.6)
 
 
 @pytest.fixture(scope="module")
@@ -112,10 +118,11 @@ def test_hartree_matches_oracle(kscf, species, brick):
     S.free()
 
 
-def run_gpu_scf(kscf, species, dtype, mode, kT=0.0, system=None, evaluate=False):
+def run_gpu_scf(kscf, species, dtype, mode, kT=0.0, system=None, evaluate=False, kerker_q0=0.0, alpha=0.3):
     pos, z = sih4()
     g, H = system if system is not None else kscf.build_cluster(pos, z, species, R_SIH4, H_SIH4)
-    params = kscf.scf_params(K_SIH4, M_SIH4, dtype=dtype, gemm_mode=mode, kT=kT)
+    params = kscf.scf_params(K_SIH4, M_SIH4, dtype=dtype, gemm_mode=mode, kT=kT, kerker_q0=kerker_q0,
+                             mix_alpha=alpha)
     S = kscf.Scf(H, pos, z, species, params)
     S.start(seed=1)
     reps = S.run(40)
@@ -146,6 +153,13 @@ def test_scf_smeared_fp64_matches_oracle(kscf, species, oracle_scf_smeared):
     assert reps[-1]["converged"] == 1 and reps[-1]["minus_ts"] < 0
     assert 0 <= reps[-1]["occ_last"] < 1e-2
     assert np.max(np.abs(rho - oracle_scf_smeared["rho"])) < 1e-8 * np.max(oracle_scf_smeared["rho"])
+
+
+def test_scf_kerker_fp64_matches_oracle(kscf, species, oracle_scf_kerker):
+    reps, rho = run_gpu_scf(kscf, species, kscf.KSCF_F64, kscf.KSCF_GEMM_NATIVE, kerker_q0=0.8, alpha=0.6)
+    compare_steps(reps, oracle_scf_kerker["reports"])
+    assert reps[-1]["converged"] == 1
+    assert all(r["kerker_iters"] > 0 for r in reps[:-1])
 
 
 def test_scf_reuses_hamiltonian(kscf, species):

@@ -121,3 +121,43 @@ def test_scf_sih4_smeared_converges():
     assert abs(rep[-1]["electrons"] - 8.0) < 1e-9
     assert rep[-1]["minus_ts"] < 0.0
     assert rep[-1]["homo"] < rep[-1]["mu"] < rep[-1]["lumo"]
+
+
+def test_kerker_on_eigenvectors_of_the_laplacian():
+    # P multiplies an eigenvector of -Lap_h (zero outside the domain) with eigenvalue mu by
+    # mu / (mu + q0^2); eigenvectors from ARPACK
+    import scipy.sparse.linalg as spla2
+    from oracle.grid import box_grid
+    from oracle.hamiltonian import kinetic_matrix
+    from oracle.scf import Kerker
+    n, h, q0 = 10, 0.6, 0.8
+    g = box_grid(n, n, n, h)
+    A = 2.0 * kinetic_matrix(g)
+    mus, vecs = spla2.eigsh(A, k=3, sigma=0.0, which="LM")
+    P = Kerker(g, q0)
+    for mu, v in zip(mus, vecs.T):
+        assert np.allclose(P.apply(v), mu / (mu + q0 * q0) * v, atol=1e-9)
+    # and the defining equation on a random residual
+    f = np.random.default_rng(0).standard_normal(g.n)
+    pf = P.apply(f)
+    assert np.allclose((A + q0 * q0 * np.eye(g.n)) @ (f - pf), q0 * q0 * f, atol=1e-8)
+
+
+def test_anderson_with_preconditioner_solves_linear_fixed_point():
+    from oracle.scf import Anderson
+    rng = np.random.default_rng(5)
+    n = 40
+    M = rng.standard_normal((n, n)) * 0.1
+    J = -(M @ M.T) * 20.0              # strongly negative Jacobian: plain mixing with 0.3 diverges
+    c = rng.standard_normal(n)
+
+    class Damp:                         # P = (I - J)^-1, exact for this linear map
+        def apply(self, f):
+            return np.linalg.solve(np.eye(n) - J, f)
+
+    mix = Anderson(1.0, 8, Damp())
+    x = np.zeros(n)
+    for _ in range(6):
+        f = (J @ x + c) - x
+        x = mix.step(x, f)
+    assert np.linalg.norm((J @ x + c) - x) < 1e-10 * np.linalg.norm(c)

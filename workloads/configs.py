@@ -60,3 +60,13 @@ def pseudo_params(path: str | None = None) -> list[dict]:
     """Species parameter dicts of the synthetic pseudopotential set."""
     with open(path or os.path.join(_HERE, "synthetic_pseudo.json")) as f:
         return json.load(f)["species"]
+
+
+def cluster_scf_config(d_nm: float, z, h: float = 0.7, margin: float = 6.0, degree: int = 12) -> dict:
+    """SCF sizes for a cluster of nominal diameter d_nm: domain radius d/2 + margin,
+    spacing h, k = occupied states + the larger of 16 and 6 % of them (the 2.2 nm
+    workload's 850 = 804 + 46 is the same ratio), Chebyshev degree."""
+    from .cluster import n_occupied
+    nocc = n_occupied(z)
+    return {"radius": d_nm * 10.0 / 2.0 * ANG2BOHR + margin, "h": h,
+            "k": nocc + max(16, -(-6 * nocc // 100)), "degree": degree}
