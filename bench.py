@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--no-scf", action="store_true", help="skip the SCF wall-time comparison (mixed vs FP64)")
     p.add_argument("--scf-workload", default="si353h196")
     p.add_argument("--scf-max-steps", type=int, default=80)
+    p.add_argument("--gap-study", action="store_true",
+                   help="HOMO-LUMO gap and DOS (0.1 eV bins) vs cluster diameter from converged SCF runs")
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-start comparison (train on 30 clusters, SCF on a held-out one)")
     return p.parse_args()
@@ -316,6 +318,41 @@ def run_learned_start(args):
             "runs": runs}
 
 
+# ------------------------------------------------------------------ gap and DOS vs diameter
+def run_gap_study(args):
+    """Mixed-precision SCF of clusters of 1.0-2.4 nm; HOMO-LUMO gap and DOS (0.1 eV bins,
+    HOMO at 0, occupied area 1) from the FP64 Rayleigh quotients of the converged states;
+    least-squares fit E_gap(d) = a + b / d^c.  Prints one JSON line."""
+    from paper_2303_00790_gb300 import kscf, learned
+    from workloads import pseudo_params
+    from workloads.cluster import cluster_for_diameter, n_occupied
+    from workloads.configs import cluster_scf_config
+
+    species = pseudo_params()
+    rows = []
+    for d in (1.0, 1.3, 1.6, 1.9, 2.2, 2.4):
+        pos, z = cluster_for_diameter(d)
+        cfg = cluster_scf_config(d, z)
+        reps, wall, ex = learned.run_scf(pos, z, species, cfg, max_steps=100)
+        lam = ex["final"]["lam"]
+        nocc = n_occupied(z)
+        hist, edges, gap = kscf.kscf_dos(lam, nocc, 0.1, -15.0, 180)
+        rows.append({"d_nm": d, "n_si": int((z == 14).sum()), "n_h": int((z == 1).sum()), "k": cfg["k"],
+                     "steps": len(reps), "converged": bool(reps[-1]["converged"]), "wall_s": wall, "gap_ev": gap,
+                     "dos_0p1ev_from_-15ev": [round(float(x), 5) for x in hist]})
+    fit = None
+    try:
+        from scipy.optimize import curve_fit
+        dd = np.array([r["d_nm"] for r in rows])
+        gg = np.array([r["gap_ev"] for r in rows])
+        popt, _ = curve_fit(lambda x, a, b, c: a + b / x ** c, dd, gg, p0=(0.5, 4.0, 1.5),
+                            bounds=([0.0, 0.0, 0.5], [5.0, 50.0, 3.0]), maxfev=20000)
+        fit = {"a_ev": float(popt[0]), "b_ev": float(popt[1]), "c": float(popt[2])}
+    except Exception as exc:
+        fit = {"error": str(exc)}
+    print(json.dumps({"gap_study": rows, "fit_a_plus_b_over_d_pow_c": fit}), flush=True)
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_kscf(args):
     import torch
@@ -491,6 +528,9 @@ def main():
     args = parse()
     if args.alu_peaks:
         alu_peaks()
+        return
+    if args.gap_study:
+        run_gap_study(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -461,6 +461,18 @@ int kscf_mlp_loss_grad(const float* params, const float* mu, const float* inv_sd
 int kscf_mlp_adam(float* params, const float* grad, float* m, float* v, int step, float lr, float beta1,
                   float beta2, float eps, void* stream);
 
+/* Density of states and HOMO-LUMO gap (host function; the DOS paragraph and Fig. 1:
+ * eigenvalues histogrammed in bins of bin_ev (the paper uses 0.1 eV) with the highest
+ * occupied state at zero, all DOS scaled to the same area below the Fermi level; the
+ * band gap of Fig. 3 is the HOMO-LUMO gap).
+ *   eigvals: k Ritz values (Ha, any order); HOMO = the n_occ-th smallest.
+ *   hist[b] (b < n_bins) = (number of states with e = (lambda - HOMO) * 27.211386245988 eV
+ *   in [e_lo_ev + b bin_ev, e_lo_ev + (b+1) bin_ev)) / (n_occ * bin_ev), so the occupied
+ *   states integrate to one; states outside the bins are not counted.
+ *   gap_ev: (LUMO - HOMO) in eV, NaN when n_occ == k (may be NULL). */
+int kscf_dos(const double* eigvals, int k, int n_occ, double bin_ev, double e_lo_ev, int n_bins, double* hist,
+             double* gap_ev);
+
 /* Hilbert index of brick coordinates (x, y, z) on the 2^bits cube, as used to order the
  * bricks (Skilling 2004 transpose algorithm; bits interleaved most significant first,
  * x first).  Pure host function, exported for tests of the ordering. */

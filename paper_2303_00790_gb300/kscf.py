@@ -122,6 +122,7 @@ _sigs = {
     "kscf_mlp_forward": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp], _i32),
     "kscf_mlp_work_size": ([_i64, C.POINTER(_sz)], _i32),
     "kscf_mlp_loss_grad": ([_vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _sz, _vp], _i32),
+    "kscf_dos": ([_vp, _i32, _i32, _d, _d, _i32, _vp, C.POINTER(_d)], _i32),
     "kscf_mlp_adam": ([_vp, _vp, _vp, _vp, _i32, C.c_float, C.c_float, C.c_float, C.c_float, _vp], _i32),
 }
 for _name, (_args, _res) in _sigs.items():
@@ -521,6 +522,17 @@ class Scf:
             self.free()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ DOS
+def kscf_dos(eigvals, n_occ: int, bin_ev: float = 0.1, e_lo_ev: float = -15.0, n_bins: int = 200):
+    """(hist (n_bins,), bin left edges in eV, gap in eV) of the Ritz values (host arrays)."""
+    ev = np.ascontiguousarray(eigvals, dtype=np.float64)
+    hist = np.empty(n_bins, dtype=np.float64)
+    gap = C.c_double()
+    _check(lib.kscf_dos(ev.ctypes.data_as(C.c_void_p), len(ev), n_occ, bin_ev, e_lo_ev, n_bins,
+                        hist.ctypes.data_as(C.c_void_p), C.byref(gap)))
+    return hist, e_lo_ev + bin_ev * np.arange(n_bins), gap.value
 
 
 # ------------------------------------------------------------------ learned start
