@@ -167,6 +167,19 @@ int kscf_get_potential(const kscf_ham* ham, double* v_slots, void* stream);
  * with E+ = max(E, 0), E- = max(-E, 0).  upper is the filter's upper bound b. */
 int kscf_spectral_bounds(const kscf_ham* ham, double* lower, double* upper);
 
+/* Lanczos estimate of the spectral bounds (the filter interval; Zhou & Li 2011): `steps`
+ * (K) Lanczos steps in FP64 from the unit vector of kscf_random_subspace(seed, k = 1),
+ * inner products h^3-weighted; T_K = tridiag(beta; alpha; beta).  upper = theta_max(T_K)
+ * + beta_K (a safe upper bound in practice), theta_max/theta_min: extreme Ritz values
+ * (lower estimate of the spectrum), alpha_out/beta_out: K values each (host, may be NULL;
+ * fewer when an invariant subspace ends the recurrence early).  Synchronous; allocates
+ * five n_slots FP64 vectors for the call.  For the order-12 FD Hamiltonians here the
+ * Weyl + Gershgorin bound of kscf_spectral_bounds is usually the tighter upper bound
+ * (the kinetic term's Gershgorin radius equals the symbol maximum), so callers take the
+ * minimum of the two. */
+int kscf_lanczos_bounds(const kscf_ham* ham, int steps, uint64_t seed, double* upper, double* theta_max,
+                        double* theta_min, double* alpha_out, double* beta_out, void* stream);
+
 /* Bytes of device work buffer needed by `op` for k vectors of `dtype` in GEMM `mode`,
  * streaming `block` columns at a time (0 = all k). */
 int kscf_workspace_size(const kscf_ham* ham, int op, int k, int dtype, int mode, int block,
@@ -333,6 +346,22 @@ typedef struct kscf_scf_params {
                               preconditioned, P F = F - q0^2 u with (-Lap_h + q0^2) u = F on
                               the domain (Kerker's q^2/(q^2 + q0^2) damping of slowly
                               varying residuals; CG to poisson_rtol) */
+  int32_t degree_max;      /* 0: every filter uses `degree`.  > 0: adaptive degrees (per-vector
+                              degrees of ChASE, Winkelmann, Springer & Di Napoli 2019): before
+                              each filter, lambda_i = <x_i, H x_i> and r_i = |H x_i - lambda_i x_i|
+                              with the current H; with t_i = (c - lambda_i)/e and
+                              rho_i = 1/(t_i + sqrt(t_i^2 - 1)), m_i = ceil(log(tol/r_i)/log rho_i)
+                              (degree_min if r_i <= tol, degree_max if t_i <= 1), clamped to
+                              [degree_min, degree_max]; each group of degree_group columns is
+                              filtered with its largest m_i.  tol = max(adapt_tol_floor,
+                              adapt_reduction * r_i): every vector is asked for the same
+                              reduction of its residual per filter */
+  int32_t degree_min;
+  int32_t degree_group;    /* columns per group (e.g. 64) */
+  int32_t upper_bound;     /* 0: b = Weyl + Gershgorin; 1: b = min(that, Lanczos estimate with
+                              12 steps, kscf_lanczos_bounds) */
+  double adapt_reduction;  /* 0 < reduction < 1 */
+  double adapt_tol_floor;
 } kscf_scf_params;
 
 typedef struct kscf_scf_report {
@@ -350,6 +379,8 @@ typedef struct kscf_scf_report {
   double occ_last;         /* occupation of the highest Ritz state (k too small if not ~0) */
   int32_t kerker_iters;    /* CG iterations of this step's Kerker solve (0 without) */
   int32_t reserved;
+  double filter_work;      /* sum over this step's filters of the column-averaged degree */
+  double upper_bound;      /* the filter's b in this step */
 } kscf_scf_report;
 
 /* Creates the SCF state for the atoms the Hamiltonian was built from.  atoms/species

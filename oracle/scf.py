@@ -16,6 +16,15 @@ parametrised by Perdew & Zunger 1981) at fixed ions:
   SRE    sqrt(h^3 sum_p rho_p (V_out - V_in)_p^2), reported in Ry (x 2); stop below 1e-4 Ry
   CheFSI four filter/Cholesky-QR/Rayleigh-Ritz iterations in the first SCF step, one in
          every later step (the schedule the paper states)
+  degree the fixed degree m, or (degree_max > 0) a degree per group of columns from the
+         residuals of the current Ritz pairs (the per-vector degrees of ChASE, Winkelmann,
+         Springer & Di Napoli 2019): with e = (b - a)/2, c = (b + a)/2, t_i = (c - lambda_i)/e
+         and rho_i = 1/(t_i + sqrt(t_i^2 - 1)) the error of vector i shrinks by rho_i per
+         degree step, so m_i = ceil(log(tol / r_i) / log(rho_i)) (m_min if r_i <= tol,
+         m_max if t_i <= 1), clamped to [m_min, m_max]; a group of `group` columns takes
+         its largest m_i.  Each vector is asked for the same reduction of its residual per
+         filter, tol_i = max(tol_floor, reduction * r_i); lambda_i = <x_i, H x_i> and
+         r_i = |H x_i - lambda_i x_i| with the Hamiltonian of the current step.
   occupations  kT = 0: the n_e/2 lowest Ritz states doubly occupied.  kT > 0: Fermi-Dirac
          occupations 2 f((lambda - mu)/kT) with mu fixed by sum = n_e (bisection), and the
          energy reported is the Mermin free energy E - T S,
@@ -228,8 +237,36 @@ class Anderson:
         return nxt
 
 
+def rayleigh_residuals(H, X):
+    """(lambda_i = h^3 <x_i, H x_i>, r_i = sqrt(h^3 sum (H x_i - lambda_i x_i)^2)) for
+    h^3-orthonormal columns X."""
+    HX = H.apply(X)
+    lam = H.h3 * (X * HX).sum(0)
+    R = HX - X * lam[None, :]
+    return lam, np.sqrt(H.h3 * (R * R).sum(0))
+
+
+def group_degrees(lam, r, a, b, tol, m_min, m_max, group):
+    """Degree of every column group (see the module docstring); tol: one value per column."""
+    e = (b - a) / 2.0
+    c = (b + a) / 2.0
+    m = np.empty(len(lam), dtype=np.int64)
+    for i in range(len(lam)):
+        t = (c - lam[i]) / e
+        if t <= 1.0 + 1e-12:
+            m[i] = m_max
+        elif r[i] <= tol[i]:
+            m[i] = m_min
+        else:
+            rho = 1.0 / (t + math.sqrt(t * t - 1.0))
+            m[i] = math.ceil(math.log(tol[i] / r[i]) / math.log(rho))
+    m = np.clip(m, m_min, m_max)
+    return [int(m[g:g + group].max()) for g in range(0, len(lam), group)]
+
+
 def scf(atom_pos, atom_z, species, radius, h, k, degree, X0, max_steps=40, sre_tol_ry=1e-4,
-        first_iters=4, alpha=0.3, history=8, center=None, kT=0.0, kerker_q0=0.0):
+        first_iters=4, alpha=0.3, history=8, center=None, kT=0.0, kerker_q0=0.0, degree_min=0,
+        degree_max=0, reduction=0.1, tol_floor=1e-6, group=64):
     """Run the SCF; returns a dict with per-step reports and the final state."""
     from .grid import sphere_grid
     from .potential import kb_projectors, local_potential
@@ -254,11 +291,24 @@ def scf(atom_pos, atom_z, species, radius, h, k, degree, X0, max_steps=40, sre_t
     mixer = Anderson(alpha, history, Kerker(g, kerker_q0) if kerker_q0 > 0 else None)
     reports = []
     vh_prev = vh
+    adaptive = degree_max > 0
     for step in range(1, max_steps + 1):
         H = Hamiltonian(g, v_in, P, E)
         b = cf.spectral_upper_bound(H)
+        work = 0.0
         for _ in range(first_iters if step == 1 else 1):
-            Y = cf.chebyshev_filter(H, X, degree, lam[-1], b, lam[0])
+            if adaptive:
+                rq, resid = rayleigh_residuals(H, X)
+                tol = np.maximum(tol_floor, reduction * resid)
+                degs = group_degrees(rq, resid, lam[-1], b, tol, degree_min, degree_max, group)
+                Y = X.copy()
+                for gi, m_g in enumerate(degs):
+                    cols = slice(gi * group, min(k, (gi + 1) * group))
+                    Y[:, cols] = cf.chebyshev_filter(H, X[:, cols], m_g, lam[-1], b, lam[0])
+                    work += m_g * (cols.stop - cols.start) / k
+            else:
+                Y = cf.chebyshev_filter(H, X, degree, lam[-1], b, lam[0])
+                work += degree
             X, _ = cf.cholesky_qr(Y, H.h3)
             lam, X, _ = cf.rayleigh_ritz(H, X, H.h3)
         occ, mu, minus_ts = occupations(lam, ne, kT)
@@ -273,6 +323,7 @@ def scf(atom_pos, atom_z, species, radius, h, k, degree, X0, max_steps=40, sre_t
         e_tot = (e_band - H.h3 * float(np.dot(rho, v_in - v_ion)) + 0.5 * H.h3 * float(np.dot(rho, vh))
                  + H.h3 * float(np.dot(rho, eps)) + minus_ts)
         reports.append({"step": step, "sre_ry": sre, "e_band": e_band, "e_total": e_tot, "mu": mu,
+                        "filter_work": work,
                         "minus_ts": minus_ts,
                         "homo": float(lam[nocc - 1]), "lumo": float(lam[nocc]) if k > nocc else float("nan"),
                         "electrons": H.h3 * float(rho.sum()), "lam": lam.copy()})

@@ -35,6 +35,8 @@ struct kscf_scf {
   double *cg_b = nullptr, *cg_r = nullptr, *cg_p = nullptr, *cg_q = nullptr;
   double *v_prev = nullptr, *f_prev = nullptr, *dv = nullptr, *df = nullptr;  // dv, df: history x n
   double *pf = nullptr, *pf_prev = nullptr, *dpf = nullptr, *ku = nullptr;  // Kerker: P F, history, solve
+  void* hx = nullptr;         // adaptive degrees: H X (n_slots x ld of dtype)
+  double sre_prev = 0.0;      // SRE of the previous step (Ry), 0 before the first
   double* part = nullptr;     // kScfRedBlocks x 44 partial sums
   double* part_bb = nullptr;  // kScfRedBlocks
   double* part_rr[2] = {nullptr, nullptr};
@@ -75,7 +77,7 @@ void free_scf(kscf_scf* S) {
                  S->v_prev, S->f_prev, S->dv,     S->df,      S->part,       S->part_bb,    S->part_rr[0],
                  S->part_rr[1], S->part_pq, S->small, S->d_iters, S->P.d_grel, S->P.d_vghost, S->P.d_gptr,
                  S->P.d_gidx, S->P.d_gw, S->work, S->part_col, S->colsq, S->d_occ,
-                 S->pf, S->pf_prev, S->dpf, S->ku};
+                 S->pf, S->pf_prev, S->dpf, S->ku, S->hx};
   for (void* q : dev)
     if (q) cudaFree(q);
   if (S->host) cudaFreeHost(S->host);
@@ -311,14 +313,73 @@ void occupations(const std::vector<double>& lam, int n_e, double kT, std::vector
   *minus_ts = kT * 2.0 * s;
 }
 
-int eig_step(kscf_scf* S, bool filter, double b_upper) {
+// Degrees of the column groups from Rayleigh quotients and residuals with the current H
+// (the per-vector degrees of ChASE): see kscf_scf_params.degree_max.
+int adaptive_degrees(kscf_scf* S, double a, double b, std::vector<int>& degs) {
+  const kscf_scf_params& p = S->p;
+  const Ham& H = S->ham->h;
+  const int k = p.k;
+  const double h3 = H.grid.h * H.grid.h * H.grid.h;
+  cudaStream_t st = S->st;
+  int rc = kscf_hamiltonian_apply(S->ham, S->X, S->ld, S->hx, S->ld, k, p.dtype, S->work, S->work_bytes, st);
+  if (rc) return rc;
+  KSCF_CUDA_TRY(launch_col_dot(S->X, S->ld, S->hx, S->ld, S->n, k, p.dtype, S->part_col, S->colsq, st));
+  KSCF_CUDA_TRY(cudaMemcpyAsync(S->host_k, S->colsq, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+  KSCF_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<double> rq(k), r(k);
+  for (int i = 0; i < k; i++) rq[i] = h3 * S->host_k[i];
+  std::memcpy(S->host_k, rq.data(), sizeof(double) * k);
+  KSCF_CUDA_TRY(cudaMemcpyAsync(S->d_occ, S->host_k, sizeof(double) * k, cudaMemcpyHostToDevice, st));
+  KSCF_CUDA_TRY(launch_col_resid_t(S->X, S->hx, S->ld, S->n, k, p.dtype, S->d_occ, S->part_col, S->colsq, st));
+  KSCF_CUDA_TRY(cudaMemcpyAsync(S->host_k, S->colsq, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+  KSCF_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < k; i++) r[i] = std::sqrt(std::max(h3 * S->host_k[i], 0.0));
+  const double e = (b - a) / 2.0, c = (b + a) / 2.0;
+  const int G = p.degree_group;
+  degs.assign((k + G - 1) / G, p.degree_min);
+  for (int i = 0; i < k; i++) {
+    const double t = (c - rq[i]) / e;
+    const double tol = std::max(p.adapt_tol_floor, p.adapt_reduction * r[i]);
+    int m;
+    if (t <= 1.0 + 1e-12) {
+      m = p.degree_max;
+    } else if (r[i] <= tol) {
+      m = p.degree_min;
+    } else {
+      const double rho = 1.0 / (t + std::sqrt(t * t - 1.0));
+      const double mm = std::ceil(std::log(tol / r[i]) / std::log(rho));
+      m = mm > (double)p.degree_max ? p.degree_max : (int)mm;
+    }
+    m = std::min(std::max(m, p.degree_min), p.degree_max);
+    degs[i / G] = std::max(degs[i / G], m);
+  }
+  return KSCF_OK;
+}
+
+int eig_step(kscf_scf* S, bool filter, double b_upper, double* work_out = nullptr) {
   const kscf_scf_params& p = S->p;
   kscf_ham* ham = S->ham;
   if (filter) {
     const double a = S->lam[p.k - 1], a0 = S->lam[0];
-    int rc = kscf_chebyshev_filter(ham, S->X, S->ld, p.k, p.degree, a, b_upper, a0, p.dtype, p.block, S->work,
-                                   S->work_bytes, S->st);
-    if (rc) return rc;
+    if (p.degree_max > 0) {
+      std::vector<int> degs;
+      int rc = adaptive_degrees(S, a, b_upper, degs);
+      if (rc) return rc;
+      const size_t es = p.dtype == KSCF_F64 ? 8 : 4;
+      for (size_t g = 0; g < degs.size(); g++) {
+        const int c0 = (int)g * p.degree_group;
+        const int nc = std::min(p.degree_group, p.k - c0);
+        rc = kscf_chebyshev_filter(ham, (char*)S->X + (size_t)c0 * es, S->ld, nc, degs[g], a, b_upper, a0, p.dtype, 0,
+                                   S->work, S->work_bytes, S->st);
+        if (rc) return rc;
+        if (work_out) *work_out += (double)degs[g] * nc / p.k;
+      }
+    } else {
+      int rc = kscf_chebyshev_filter(ham, S->X, S->ld, p.k, p.degree, a, b_upper, a0, p.dtype, p.block, S->work,
+                                     S->work_bytes, S->st);
+      if (rc) return rc;
+      if (work_out) *work_out += p.degree;
+    }
   }
   int rc = kscf_orthonormalize(ham, S->X, S->ld, p.k, p.dtype, p.gemm_mode, S->work, S->work_bytes, S->st);
   if (rc) return rc;
@@ -356,7 +417,11 @@ extern "C" int kscf_scf_create(kscf_ham* ham, const kscf_atom* atoms, int n_atom
       (p.gemm_mode == KSCF_GEMM_TENSOR && p.dtype != KSCF_F32) || p.degree < 1 || p.first_iters < 1 ||
       p.history < 1 || p.history > kAndersonMax || !(p.mix_alpha > 0.0 && p.mix_alpha <= 1.0) ||
       !(p.sre_tol_ry > 0.0) || !(p.poisson_rtol > 0.0) || p.poisson_maxiter < 1 || p.block < 0 || ld < p.k ||
-      !(p.kT >= 0.0) || !std::isfinite(p.kT) || !(p.kerker_q0 >= 0.0) || !std::isfinite(p.kerker_q0)) {
+      !(p.kT >= 0.0) || !std::isfinite(p.kT) || !(p.kerker_q0 >= 0.0) || !std::isfinite(p.kerker_q0) ||
+      p.degree_max < 0 || (p.degree_max > 0 && (p.degree_min < 1 || p.degree_min > p.degree_max ||
+                                                  p.degree_group < 1 || !(p.adapt_reduction > 0.0 && p.adapt_reduction < 1.0) ||
+                                                  !(p.adapt_tol_floor > 0.0))) ||
+      (p.upper_bound != 0 && p.upper_bound != 1)) {
     set_error("kscf_scf_create: invalid parameters");
     return KSCF_ERR_INVALID;
   }
@@ -410,6 +475,8 @@ extern "C" int kscf_scf_create(kscf_ham* ham, const kscf_atom* atoms, int n_atom
       if (e == cudaSuccess) e = dalloc(v, (size_t)n);
     if (e == cudaSuccess) e = dalloc(&S->dv, (size_t)p.history * n);
     if (e == cudaSuccess) e = dalloc(&S->df, (size_t)p.history * n);
+    if (p.degree_max > 0 && e == cudaSuccess)
+      e = cudaMalloc(&S->hx, (size_t)n * ld * (p.dtype == KSCF_F64 ? 8 : 4));
     if (p.kerker_q0 > 0.0) {
       double** kv[] = {&S->pf, &S->pf_prev, &S->ku};
       for (double** v : kv) {
@@ -504,6 +571,7 @@ extern "C" int kscf_scf_start(kscf_scf* scf, const double* dv_start, int init_x,
   S->order.clear();
   S->started = false;
   S->stepped = false;
+  S->sre_prev = 0.0;
   if (init_x) {
     int rc = kscf_random_subspace(S->ham, S->X, S->ld, S->p.k, S->p.dtype, seed, st);
     if (rc) return rc;
@@ -552,9 +620,16 @@ extern "C" int kscf_scf_step(kscf_scf* scf, kscf_scf_report* report, double* eig
   double lower = 0.0, upper = 0.0;
   rc = kscf_spectral_bounds(S->ham, &lower, &upper);
   if (rc) return rc;
+  if (p.upper_bound == 1) {
+    double lz = 0.0;
+    rc = kscf_lanczos_bounds(S->ham, 12, 7, &lz, nullptr, nullptr, nullptr, nullptr, st);
+    if (rc) return rc;
+    upper = std::min(upper, lz);
+  }
+  report->upper_bound = upper;
   const int iters = S->step == 1 ? p.first_iters : 1;
   for (int it = 0; it < iters; it++) {
-    rc = eig_step(S, true, upper);
+    rc = eig_step(S, true, upper, &report->filter_work);
     if (rc) return rc;
   }
   rc = kscf_check_status();
@@ -605,6 +680,7 @@ extern "C" int kscf_scf_step(kscf_scf* scf, kscf_scf_report* report, double* eig
     return KSCF_ERR_NONFINITE;
   }
   report->converged = report->sre_ry < p.sre_tol_ry ? 1 : 0;
+  S->sre_prev = report->sre_ry;
   S->last = *report;
   S->stepped = true;
   if (report->converged) return KSCF_OK;

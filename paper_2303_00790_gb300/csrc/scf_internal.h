@@ -64,6 +64,9 @@ cudaError_t launch_col_dot(const void* A, int64_t lda, const void* B, int64_t ld
 // out[j] = sum_r (HX[r][j] - lam[j] X[r][j])^2, lam on the device
 cudaError_t launch_col_resid(const double* X, const double* HX, int64_t ld, int64_t rows, int k, const double* lam,
                              double* part, double* out, cudaStream_t st);
+// the same for X, HX of dtype (FP32 values, FP64 sums)
+cudaError_t launch_col_resid_t(const void* X, const void* HX, int64_t ld, int64_t rows, int k, int dtype,
+                               const double* lam, double* part, double* out, cudaStream_t st);
 cudaError_t launch_widen(const float* src, int64_t lds, double* dst, int64_t ldd, int64_t rows, int k,
                          cudaStream_t st);
 cudaError_t launch_add2(const Ham& H, const double* a, const double* b, double* out, cudaStream_t st);

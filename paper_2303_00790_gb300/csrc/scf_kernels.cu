@@ -522,7 +522,8 @@ __global__ void __launch_bounds__(kScfThreads) col_dot_kernel(const T* __restric
 }
 
 // part[j * gridDim.x + b] = this block's share of sum_r (HX[r][j] - lam[j] X[r][j])^2  (FP64)
-__global__ void __launch_bounds__(kScfThreads) col_resid_kernel(const double* __restrict__ X, const double* __restrict__ HX,
+template <typename T>
+__global__ void __launch_bounds__(kScfThreads) col_resid_kernel(const T* __restrict__ X, const T* __restrict__ HX,
                                                                 int64_t ld, int64_t rows, int k,
                                                                 const double* __restrict__ lam,
                                                                 double* __restrict__ part) {
@@ -533,7 +534,7 @@ __global__ void __launch_bounds__(kScfThreads) col_resid_kernel(const double* __
     const double l = lam[j];
     double a = 0.0;
     for (int64_t r = r0; r < r1; r++) {
-      const double d = HX[r * ld + j] - l * X[r * ld + j];
+      const double d = (double)HX[r * ld + j] - l * (double)X[r * ld + j];
       a += d * d;
     }
     part[(int64_t)j * gridDim.x + blockIdx.x] = a;
@@ -560,7 +561,17 @@ cudaError_t launch_col_sumsq(const void* X, int64_t ld, int64_t rows, int k, int
 
 cudaError_t launch_col_resid(const double* X, const double* HX, int64_t ld, int64_t rows, int k, const double* lam,
                              double* part, double* out, cudaStream_t st) {
-  col_resid_kernel<<<kScfRedBlocks, kScfThreads, 0, st>>>(X, HX, ld, rows, k, lam, part), count_launch();
+  return launch_col_resid_t(X, HX, ld, rows, k, KSCF_F64, lam, part, out, st);
+}
+
+cudaError_t launch_col_resid_t(const void* X, const void* HX, int64_t ld, int64_t rows, int k, int dtype,
+                               const double* lam, double* part, double* out, cudaStream_t st) {
+  if (dtype == KSCF_F64)
+    col_resid_kernel<double><<<kScfRedBlocks, kScfThreads, 0, st>>>((const double*)X, (const double*)HX, ld, rows, k,
+                                                                    lam, part), count_launch();
+  else
+    col_resid_kernel<float><<<kScfRedBlocks, kScfThreads, 0, st>>>((const float*)X, (const float*)HX, ld, rows, k,
+                                                                   lam, part), count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_finalize_partials(part, kScfRedBlocks, k, out, st);

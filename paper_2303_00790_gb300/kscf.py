@@ -58,7 +58,9 @@ class kscf_scf_params(C.Structure):
     _fields_ = [("k", C.c_int32), ("degree", C.c_int32), ("dtype", C.c_int32), ("gemm_mode", C.c_int32),
                 ("block", C.c_int32), ("first_iters", C.c_int32), ("history", C.c_int32),
                 ("poisson_maxiter", C.c_int32), ("mix_alpha", C.c_double), ("sre_tol_ry", C.c_double),
-                ("poisson_rtol", C.c_double), ("kT", C.c_double), ("kerker_q0", C.c_double)]
+                ("poisson_rtol", C.c_double), ("kT", C.c_double), ("kerker_q0", C.c_double),
+                ("degree_max", C.c_int32), ("degree_min", C.c_int32), ("degree_group", C.c_int32),
+                ("upper_bound", C.c_int32), ("adapt_reduction", C.c_double), ("adapt_tol_floor", C.c_double)]
 
 
 class kscf_scf_report(C.Structure):
@@ -66,7 +68,8 @@ class kscf_scf_report(C.Structure):
                 ("chefsi_iters", C.c_int32), ("sre_ry", C.c_double), ("e_band", C.c_double),
                 ("e_total", C.c_double), ("homo", C.c_double), ("lumo", C.c_double), ("electrons", C.c_double),
                 ("mu", C.c_double), ("minus_ts", C.c_double), ("occ_last", C.c_double),
-                ("kerker_iters", C.c_int32), ("reserved", C.c_int32)]
+                ("kerker_iters", C.c_int32), ("reserved", C.c_int32), ("filter_work", C.c_double),
+                ("upper_bound", C.c_double)]
 
 
 KSCF_FIELD_RHO, KSCF_FIELD_V_IN, KSCF_FIELD_V_H, KSCF_FIELD_V_XC = 0, 1, 2, 3
@@ -122,6 +125,8 @@ _sigs = {
     "kscf_mlp_forward": ([_vp, _vp, _vp, _vp, _i64, _i32, _vp, _vp], _i32),
     "kscf_mlp_work_size": ([_i64, C.POINTER(_sz)], _i32),
     "kscf_mlp_loss_grad": ([_vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _sz, _vp], _i32),
+    "kscf_lanczos_bounds": ([_vp, _i32, C.c_uint64, C.POINTER(_d), C.POINTER(_d), C.POINTER(_d), _vp, _vp, _vp],
+                            _i32),
     "kscf_dos": ([_vp, _i32, _i32, _d, _d, _i32, _vp, C.POINTER(_d)], _i32),
     "kscf_mlp_adam": ([_vp, _vp, _vp, _vp, _i32, C.c_float, C.c_float, C.c_float, C.c_float, _vp], _i32),
 }
@@ -271,6 +276,16 @@ def kscf_spectral_bounds(ham: Hamiltonian):
     lo, hi = C.c_double(), C.c_double()
     _check(lib.kscf_spectral_bounds(ham.handle, C.byref(lo), C.byref(hi)))
     return lo.value, hi.value
+
+
+def kscf_lanczos_bounds(ham: Hamiltonian, steps: int = 12, seed: int = 7, stream=None):
+    """(upper, theta_max, theta_min, alpha, beta) of a K-step Lanczos run."""
+    up, tmax, tmin = C.c_double(), C.c_double(), C.c_double()
+    a = np.zeros(steps)
+    b = np.zeros(steps)
+    _check(lib.kscf_lanczos_bounds(ham.handle, steps, int(seed), C.byref(up), C.byref(tmax), C.byref(tmin),
+                                   a.ctypes.data_as(C.c_void_p), b.ctypes.data_as(C.c_void_p), _stream(stream)))
+    return up.value, tmax.value, tmin.value, a, b
 
 
 def kscf_set_potential(ham: Hamiltonian, v_slots, stream=None):
@@ -432,9 +447,11 @@ def kscf_lda_xc(ham: Hamiltonian, rho, eps=None, vxc=None, stream=None):
 def scf_params(k: int, degree: int, dtype: int = KSCF_F64, gemm_mode: int = KSCF_GEMM_NATIVE, block: int = 0,
                first_iters: int = 4, history: int = 8, mix_alpha: float = 0.3, sre_tol_ry: float = 1e-4,
                poisson_rtol: float = 1e-12, poisson_maxiter: int = 20000, kT: float = 0.0,
-               kerker_q0: float = 0.0) -> kscf_scf_params:
+               kerker_q0: float = 0.0, degree_max: int = 0, degree_min: int = 0, degree_group: int = 64,
+               upper_bound: int = 0, adapt_reduction: float = 0.1, adapt_tol_floor: float = 1e-6) -> kscf_scf_params:
     return kscf_scf_params(k, degree, dtype, gemm_mode, block, first_iters, history, poisson_maxiter, mix_alpha,
-                           sre_tol_ry, poisson_rtol, kT, kerker_q0)
+                           sre_tol_ry, poisson_rtol, kT, kerker_q0, degree_max, degree_min, degree_group, upper_bound,
+                           adapt_reduction, adapt_tol_floor)
 
 
 class Scf:

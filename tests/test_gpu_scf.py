@@ -43,7 +43,7 @@ def sih4():
 R_SIH4, H_SIH4, K_SIH4, M_SIH4 = 8.0, 0.5, 8, 10
 
 
-def oracle_run(species, kT, kerker_q0=0.0, alpha=0.3):
+def oracle_run(species, kT, kerker_q0=0.0, alpha=0.3, **kw):
     from oracle.grid import sphere_grid
     from oracle.scf import scf
     from workloads import random_block_lex
@@ -51,7 +51,12 @@ def oracle_run(species, kT, kerker_q0=0.0, alpha=0.3):
     g = sphere_grid(pos[0], R_SIH4, H_SIH4)
     X0 = random_block_lex(1, g.n, K_SIH4)
     return scf(pos, z, species, R_SIH4, H_SIH4, K_SIH4, M_SIH4, X0, max_steps=40, kT=kT, kerker_q0=kerker_q0,
-               alpha=alpha)
+               alpha=alpha, **kw)
+
+
+@pytest.fixture(scope="module")
+def oracle_scf_adaptive(species):
+    return oracle_run(species, 0.0, degree_min=4, degree_max=16, group=2, reduction=0.1)
 
 
 @pytest.fixture(scope="module")
@@ -118,11 +123,11 @@ def test_hartree_matches_oracle(kscf, species, brick):
     S.free()
 
 
-def run_gpu_scf(kscf, species, dtype, mode, kT=0.0, system=None, evaluate=False, kerker_q0=0.0, alpha=0.3):
+def run_gpu_scf(kscf, species, dtype, mode, kT=0.0, system=None, evaluate=False, kerker_q0=0.0, alpha=0.3, **kw):
     pos, z = sih4()
     g, H = system if system is not None else kscf.build_cluster(pos, z, species, R_SIH4, H_SIH4)
     params = kscf.scf_params(K_SIH4, M_SIH4, dtype=dtype, gemm_mode=mode, kT=kT, kerker_q0=kerker_q0,
-                             mix_alpha=alpha)
+                             mix_alpha=alpha, **kw)
     S = kscf.Scf(H, pos, z, species, params)
     S.start(seed=1)
     reps = S.run(40)
@@ -160,6 +165,34 @@ def test_scf_kerker_fp64_matches_oracle(kscf, species, oracle_scf_kerker):
     compare_steps(reps, oracle_scf_kerker["reports"])
     assert reps[-1]["converged"] == 1
     assert all(r["kerker_iters"] > 0 for r in reps[:-1])
+
+
+def test_scf_adaptive_degree_fp64_matches_oracle(kscf, species, oracle_scf_adaptive):
+    reps, rho = run_gpu_scf(kscf, species, kscf.KSCF_F64, kscf.KSCF_GEMM_NATIVE, degree_max=16, degree_min=4,
+                            degree_group=2, adapt_reduction=0.1)
+    ref = oracle_scf_adaptive["reports"]
+    compare_steps(reps, ref)
+    for a, b in zip(reps, ref):
+        assert abs(a["filter_work"] - b["filter_work"]) < 1e-12, (a["step"], a["filter_work"], b["filter_work"])
+    assert reps[-1]["converged"] == 1
+
+
+def test_lanczos_bounds_match_oracle(kscf, species):
+    from oracle.lanczos import lanczos
+    from oracle.system import cluster_hamiltonian
+    from workloads import random_block_lex
+    pos, z = sih4()
+    g, H = kscf.build_cluster(pos, z, species, 6.0, 0.7)
+    up, tmax, tmin, a, b = kscf.kscf_lanczos_bounds(H, steps=12, seed=7)
+    OH = cluster_hamiltonian(pos, z, species, 6.0, 0.7)
+    x0 = random_block_lex(7, OH.grid.n, 1)[:, 0]
+    ar, br, upr, lor = lanczos(OH, x0, 12)
+    assert np.allclose(a, ar, rtol=1e-9, atol=1e-9) and np.allclose(b, br, rtol=1e-9, atol=1e-9)
+    assert abs(up - upr) < 1e-8 * abs(upr) and abs(tmin - lor) < 1e-8
+    lam = np.linalg.eigvalsh(OH.dense())
+    assert up >= lam[-1] and tmin >= lam[0] - 1e-9
+    lo, hi = kscf.kscf_spectral_bounds(H)
+    assert hi >= lam[-1]
 
 
 def test_scf_reuses_hamiltonian(kscf, species):

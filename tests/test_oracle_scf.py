@@ -161,3 +161,54 @@ def test_anderson_with_preconditioner_solves_linear_fixed_point():
         f = (J @ x + c) - x
         x = mix.step(x, f)
     assert np.linalg.norm((J @ x + c) - x) < 1e-10 * np.linalg.norm(c)
+
+
+def test_group_degree_reaches_the_requested_damping():
+    # a diagonal operator: the wanted eigenvalue lam_w below the cut a, unwanted ones in
+    # [a, b].  The degree chosen for residual r and tolerance tol damps the unwanted
+    # components relative to the wanted one by at least tol / r (up to the factor 2 of
+    # T_m(t) >= (t + sqrt(t^2 - 1))^m / 2), and one degree less does not reach tol / r.
+    from oracle import chefsi as orc
+    from oracle.scf import group_degrees
+
+    class Diag:
+        def __init__(self, d):
+            self.d = np.asarray(d, dtype=np.float64)
+            self.h3 = 1.0
+
+        def apply(self, Y):
+            return self.d[:, None] * Y
+
+    a, b = 0.0, 20.0
+    for lam_w, r, tol in ((-0.3, 1.0, 1e-3), (-1.0, 0.1, 1e-5), (-0.05, 1e-2, 1e-4)):
+        m = group_degrees(np.array([lam_w]), np.array([r]), a, b, np.array([tol]), 1, 500, 1)[0]
+        H = Diag([lam_w, a, 0.5 * (a + b), b])
+        x = np.ones((4, 1))
+        y = orc.chebyshev_filter(H, x, m, a, b, lam_w - 1.0)[:, 0]
+        assert np.max(np.abs(y[1:])) / abs(y[0]) <= 2.0 * tol / r
+        if m > 1:
+            y1 = orc.chebyshev_filter(H, x, m - 1, a, b, lam_w - 1.0)[:, 0]
+            assert np.max(np.abs(y1[1:])) / abs(y1[0]) > tol / r
+    # limits: converged vectors take m_min, vectors at the cut take m_max; groups take the max
+    degs = group_degrees(np.array([-1.0, -0.5, -0.2, 0.0]), np.array([1e-9, 1.0, 1.0, 1.0]), 0.0, 20.0,
+                         np.full(4, 1e-6), 3, 40, 2)
+    assert degs[1] == 40
+    d_single = group_degrees(np.array([-1.0, -0.5]), np.array([1e-9, 1.0]), 0.0, 20.0, np.full(2, 1e-6), 3, 40, 1)
+    assert d_single[0] == 3 and degs[0] == d_single[1]
+
+
+def test_scf_sih4_adaptive_degree_converges():
+    from workloads import pseudo_params, random_block_lex
+    dd = 1.48 / 0.529177210903 / np.sqrt(3.0)
+    pos = np.array([[0.0, 0.0, 0.0], [dd, dd, dd], [dd, -dd, -dd], [-dd, dd, -dd], [-dd, -dd, dd]]) + 0.05
+    z = np.array([14, 1, 1, 1, 1], dtype=np.int32)
+    g = sphere_grid(pos[0], 8.0, 0.5)
+    X0 = random_block_lex(1, g.n, 8)
+    fixed = scf(pos, z, pseudo_params(), 8.0, 0.5, 8, 10, X0, max_steps=40)
+    adapt = scf(pos, z, pseudo_params(), 8.0, 0.5, 8, 10, X0, max_steps=40, degree_min=4, degree_max=16, group=2,
+                reduction=0.1)
+    rep = adapt["reports"]
+    assert rep[-1]["sre_ry"] < 1e-4
+    assert abs(rep[-1]["e_total"] - fixed["reports"][-1]["e_total"]) < 1e-6 * 5
+    # the degrees really vary: some iteration filtered with less than the maximum
+    assert min(r["filter_work"] for r in rep[1:]) < 16 and rep[0]["filter_work"] > 16
