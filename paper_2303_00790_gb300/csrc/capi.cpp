@@ -319,6 +319,7 @@ int cholqr_pass(const Ham& H, void* X, int64_t ld, int k, int dtype, int mode, c
 
 extern "C" int kscf_workspace_size(const kscf_ham* ham, int op, int k, int dtype, int mode, int block,
                                    size_t* bytes) {
+  mode &= ~KSCF_ORTHO_ALLOW_SHIFT;
   if (!ham || !bytes || k < 1 || (dtype != KSCF_F64 && dtype != KSCF_F32)) {
     set_error("kscf_workspace_size: invalid argument");
     return KSCF_ERR_INVALID;
@@ -429,6 +430,8 @@ extern "C" int kscf_chebyshev_filter(const kscf_ham* ham, void* X, int64_t ld, i
 
 extern "C" int kscf_orthonormalize(const kscf_ham* ham, void* X, int64_t ld, int k, int dtype, int mode, void* work,
                                    size_t work_bytes, void* stream) {
+  const bool allow_shift = (mode & KSCF_ORTHO_ALLOW_SHIFT) != 0;
+  mode &= ~KSCF_ORTHO_ALLOW_SHIFT;
   int rc = check_common(ham, X, ld, k, dtype, "kscf_orthonormalize");
   if (rc) return rc;
   rc = check_mode(dtype, mode, "kscf_orthonormalize");
@@ -443,7 +446,7 @@ extern "C" int kscf_orthonormalize(const kscf_ham* ham, void* X, int64_t ld, int
   KSCF_CUDA_TRY(launch_zero_rows(H, X, ld, k, dtype, st));
   Carver cv(work);
   bool shifted = false;
-  rc = cholqr_pass(H, X, ld, k, dtype, mode, p, cv, false, st, &shifted);
+  rc = cholqr_pass(H, X, ld, k, dtype, mode, p, cv, false, st, allow_shift ? &shifted : nullptr);
   if (rc) return rc;
   if (shifted) {
     rc = cholqr_pass(H, X, ld, k, dtype, mode, p, cv, false, st);

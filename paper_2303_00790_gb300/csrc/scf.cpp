@@ -381,7 +381,8 @@ int eig_step(kscf_scf* S, bool filter, double b_upper, double* work_out = nullpt
       if (work_out) *work_out += p.degree;
     }
   }
-  int rc = kscf_orthonormalize(ham, S->X, S->ld, p.k, p.dtype, p.gemm_mode, S->work, S->work_bytes, S->st);
+  int rc = kscf_orthonormalize(ham, S->X, S->ld, p.k, p.dtype, p.gemm_mode | KSCF_ORTHO_ALLOW_SHIFT, S->work,
+                               S->work_bytes, S->st);
   if (rc) return rc;
   return kscf_rayleigh_ritz(ham, S->X, S->ld, p.k, p.dtype, p.gemm_mode, S->lam.data(), S->work, S->work_bytes,
                             S->st);

@@ -28,6 +28,7 @@ KSCF_ERR_TIMEOUT = -9
 KSCF_F64, KSCF_F32 = 0, 1
 KSCF_GEMM_NATIVE, KSCF_GEMM_TENSOR = 0, 1
 KSCF_OP_APPLY, KSCF_OP_FILTER, KSCF_OP_ORTHO, KSCF_OP_RR = 0, 1, 2, 3
+KSCF_ORTHO_ALLOW_SHIFT = 0x100
 
 
 class KscfError(RuntimeError):
@@ -338,11 +339,12 @@ def kscf_chebyshev_filter(ham: Hamiltonian, X, degree: int, a: float, b: float, 
 
 
 def kscf_orthonormalize(ham: Hamiltonian, X, mode: int = KSCF_GEMM_NATIVE, k: int | None = None, work=None,
-                        stream=None):
+                        stream=None, allow_shift: bool = False):
     k = X.shape[1] if k is None else k
     dt = _dtype_code(X)
     work, need = _work(ham, KSCF_OP_ORTHO, k, dt, mode=mode, work=work)
-    _check(lib.kscf_orthonormalize(ham.handle, C.c_void_p(X.data_ptr()), _rows(X, k), k, dt, mode,
+    _check(lib.kscf_orthonormalize(ham.handle, C.c_void_p(X.data_ptr()), _rows(X, k), k, dt,
+                                   mode | (KSCF_ORTHO_ALLOW_SHIFT if allow_shift else 0),
                                    C.c_void_p(work.data_ptr()), work.numel(), _stream(stream)))
     return X
 

@@ -299,8 +299,8 @@ def test_f32_brick_kernel_paths(kscf, system, k, ldpad, block):
 @pytest.mark.parametrize("mode", [0, 1])
 def test_orthonormalize_recovers_from_rank_deficiency(kscf, species, mode):
     # two columns equal up to a 1e-6 perturbation: in FP32 the Gram matrix is singular to
-    # working precision, so plain Cholesky-QR fails; the shifted retry still returns an
-    # orthonormal basis of the span
+    # working precision, so plain Cholesky-QR fails; with KSCF_ORTHO_ALLOW_SHIFT the shifted
+    # retry still returns an orthonormal basis of the span
     pos, z = small_cluster()
     g, H = kscf.build_cluster(pos, z, species, 8.0, 0.7)
     k = 48
@@ -309,7 +309,7 @@ def test_orthonormalize_recovers_from_rank_deficiency(kscf, species, mode):
     noise = torch.zeros_like(X[:, 0])
     kscf.kscf_random_subspace(H, noise[:, None], seed=4)
     X[:, 7] = X[:, 3] + 1e-6 * noise
-    kscf.kscf_orthonormalize(H, X[:, :k], mode=mode)
+    kscf.kscf_orthonormalize(H, X[:, :k], mode=mode, allow_shift=True)
     G = kscf.kscf_gram(X[:, :k], X[:, :k], scale=H.h3).cpu().numpy()
     assert np.max(np.abs(G - np.eye(k))) < 1e-4
     assert torch.all(torch.isfinite(X)).item()
