@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "kscf_internal.h"
@@ -297,6 +298,214 @@ __global__ void __launch_bounds__(NV * 32, NV == 8 ? 3 : 2)
       } else {
         if (st0) o[0] = res.x;
         if (st1) o[1] = res.y;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Wide brick kernel (FP32, 8^3 bricks): one CTA per (brick, 32 vectors), 512 threads,
+// eight lanes per line and four vectors per lane (16-byte loads and stores), so that
+// every address computation, load and store serves four vectors.  Same three line passes
+// as the kernel above; in addition, every neighbour brick gets one 64-bit base pointer
+// per CTA and rows inside a brick are addressed with 32-bit offsets; halo loads are
+// branch-free (a missing neighbour is read from this brick and the value discarded);
+// padding rows of the core are zero-filled instead of read.  Shared memory: core and
+// accumulator, 512 point slots of 128 bytes each (a line's eight lanes cover all 32
+// banks, so no swizzle is needed).
+namespace {
+__device__ __forceinline__ float4 f4_add(float4 a, float4 b) {
+  const float2 lo = f2_add(make_float2(a.x, a.y), make_float2(b.x, b.y));
+  const float2 hi = f2_add(make_float2(a.z, a.w), make_float2(b.z, b.w));
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+// c * a + b (c broadcast)
+__device__ __forceinline__ float4 f4_fma(float2 c, float4 a, float4 b) {
+  const float2 lo = f2_fma(c, make_float2(a.x, a.y), make_float2(b.x, b.y));
+  const float2 hi = f2_fma(c, make_float2(a.z, a.w), make_float2(b.z, b.w));
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+__device__ __forceinline__ float4 f4_mul(float2 c, float4 a) {
+  const float2 lo = f2_mul(c, make_float2(a.x, a.y));
+  const float2 hi = f2_mul(c, make_float2(a.z, a.w));
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+template <bool WITH_CENTRE>
+__device__ __forceinline__ float4 line_terms4(const float4* w, int i, const float2* c2) {
+  float4 s = WITH_CENTRE ? f4_mul(c2[0], w[i]) : f4_mul(c2[1], f4_add(w[i + 1], w[i - 1]));
+  if (WITH_CENTRE) s = f4_fma(c2[1], f4_add(w[i + 1], w[i - 1]), s);
+#pragma unroll
+  for (int k = 2; k <= 6; k++) s = f4_fma(c2[k], f4_add(w[i + k], w[i - k]), s);
+  return s;
+}
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldg((const float4*)p); }
+}  // namespace
+
+__global__ void __launch_bounds__(512, 1)
+    cheb_step_brick8w(StepArgs<float> a, int nchunk, const uint16_t* __restrict__ entry_lslot) {
+  extern __shared__ float4 sw4[];
+  float4* core4 = sw4;          // [512][8]
+  float4* acc4 = sw4 + 4096;    // [512][8]
+  const int brick = blockIdx.x / nchunk, chunk = blockIdx.x - (blockIdx.x / nchunk) * nchunk;
+  const int tid = threadIdx.x, vp = tid & 7, line = tid >> 3;
+  const int vl = chunk * 32 + 4 * vp;
+  const int64_t b0 = (int64_t)brick * 512;
+  const int ld = (int)a.ld_in;  // 512 * ld < 2^31 (checked by the launcher)
+  const float* __restrict__ in = a.in;
+  const float* own = in + b0 * a.ld_in + vl;
+  const float* nbp[6];
+  bool nbv[6];
+#pragma unroll
+  for (int f = 0; f < 6; f++) {
+    const int q = __ldg(a.nbr + b0 / 512 * 6 + f);
+    nbv[f] = q >= 0;
+    nbp[f] = q >= 0 ? in + (int64_t)q * 512 * a.ld_in + vl : own;
+  }
+  // ---- core: 512 rows x 128 bytes, padding rows zero-filled ----
+  {
+    const float* src = in + b0 * a.ld_in + chunk * 32 + 4 * vp;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      const int r = line + 64 * i;
+      const uint32_t live = __ldg(a.mask + b0 + r);
+      const uint32_t d = (uint32_t)__cvta_generic_to_shared(&core4[r * 8 + vp]);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src + r * ld), "r"(live ? 16 : 0)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  // z-pass operands of this thread's (x, y) line
+  const int zx = line & 7, zy = line >> 3;
+  float vv[8];
+  uint32_t mk = 0;
+#pragma unroll
+  for (int z = 0; z < 8; z++) {
+    const int64_t s = b0 + z * 64 + zy * 8 + zx;
+    mk |= (uint32_t)__ldg(a.mask + s) << z;
+    vv[z] = __ldg(a.V + s);
+  }
+  float2 c2[7];
+  c2[0] = f2(3.0f * a.st[0]);
+#pragma unroll
+  for (int k = 1; k < 7; k++) c2[k] = f2(a.st[k]);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+
+  // ---- x pass: line (y, z) ----
+  {
+    const int y = line & 7, z = line >> 3;
+    const int rb = ((z * 8 + y) * 8) * ld;
+    float4 w[20];
+#pragma unroll
+    for (int xx = 0; xx < 6; xx++) {
+      const float4 m = ld4(nbp[0] + rb + (2 + xx) * ld);
+      const float4 p = ld4(nbp[1] + rb + xx * ld);
+      w[xx] = nbv[0] ? m : z4;
+      w[14 + xx] = nbv[1] ? p : z4;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+#pragma unroll
+    for (int x = 0; x < 8; x++) w[6 + x] = core4[((z * 8 + y) * 8 + x) * 8 + vp];
+#pragma unroll
+    for (int x = 0; x < 8; x++) acc4[((z * 8 + y) * 8 + x) * 8 + vp] = line_terms4<true>(w, 6 + x, c2);
+  }
+  // ---- y pass: line (x, z) ----
+  {
+    const int x = line & 7, z = line >> 3;
+    float4 w[20];
+#pragma unroll
+    for (int yy = 0; yy < 6; yy++) {
+      const float4 m = ld4(nbp[2] + ((z * 8 + 2 + yy) * 8 + x) * ld);
+      const float4 p = ld4(nbp[3] + ((z * 8 + yy) * 8 + x) * ld);
+      w[yy] = nbv[2] ? m : z4;
+      w[14 + yy] = nbv[3] ? p : z4;
+    }
+#pragma unroll
+    for (int y = 0; y < 8; y++) w[6 + y] = core4[((z * 8 + y) * 8 + x) * 8 + vp];
+    __syncthreads();  // x-pass accumulator writes are visible
+#pragma unroll
+    for (int y = 0; y < 8; y++) {
+      const int q = ((z * 8 + y) * 8 + x) * 8 + vp;
+      acc4[q] = f4_add(acc4[q], line_terms4<false>(w, 6 + y, c2));
+    }
+  }
+  __syncthreads();
+  // ---- nonlocal scatter over the brick's contiguous entry range ----
+  {
+    const int64_t cld = a.cld;
+    const int64_t e0 = __ldg(a.kb_ptr + b0), e1 = __ldg(a.kb_ptr + b0 + 512);
+    for (int64_t eb = e0 + line; eb < e1; eb += 2 * 64) {
+      int ls[2];
+      float4 ch[2];
+      const float* cf[2];
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        const int64_t e = eb + u * 64;
+        const bool ok = e < e1;
+        ls[u] = ok ? __ldg(entry_lslot + e) : -1;
+        ch[u] = ok ? __ldg((const float4*)(a.kb_chi + 4 * e)) : z4;
+        cf[u] = a.coef + (ok ? (int64_t)__ldg(a.kb_atom + e) * 4 * cld : 0) + vl;
+      }
+      float4 cv[2][4];
+#pragma unroll
+      for (int u = 0; u < 2; u++)
+#pragma unroll
+        for (int l = 0; l < 4; l++) cv[u][l] = ld4(cf[u] + l * cld);
+#pragma unroll
+      for (int u = 0; u < 2; u++) {
+        if (ls[u] < 0) continue;
+        float4 c = f4_mul(f2(ch[u].x), cv[u][0]);
+        c = f4_fma(f2(ch[u].y), cv[u][1], c);
+        c = f4_fma(f2(ch[u].z), cv[u][2], c);
+        c = f4_fma(f2(ch[u].w), cv[u][3], c);
+        float* acc = (float*)&acc4[ls[u] * 8 + vp];
+        atomicAdd(acc, c.x);
+        atomicAdd(acc + 1, c.y);
+        atomicAdd(acc + 2, c.z);
+        atomicAdd(acc + 3, c.w);
+      }
+    }
+  }
+  // ---- z pass: line (x, y); potential, recurrence, store ----
+  {
+    const int x = zx, y = zy;
+    float4 w[20];
+#pragma unroll
+    for (int zz = 0; zz < 6; zz++) {
+      const float4 m = ld4(nbp[4] + ((2 + zz) * 64 + y * 8 + x) * ld);
+      const float4 p = ld4(nbp[5] + (zz * 64 + y * 8 + x) * ld);
+      w[zz] = nbv[4] ? m : z4;
+      w[14 + zz] = nbv[5] ? p : z4;
+    }
+#pragma unroll
+    for (int z = 0; z < 8; z++) w[6 + z] = core4[(z * 64 + y * 8 + x) * 8 + vp];
+    __syncthreads();  // scatter atomics are complete
+    const bool full = vl + 3 < a.w;
+    const float2 alpha = f2(a.alpha), beta = f2(a.beta), negc = f2(-a.c);
+    const float* prevp = a.prev ? a.prev + b0 * a.ld_prev + vl : nullptr;
+    float* outp = a.out + b0 * a.ld_out + vl;
+    const int ldp = (int)a.ld_prev, ldo = (int)a.ld_out;
+#pragma unroll
+    for (int z = 0; z < 8; z++) {
+      const int r = z * 64 + y * 8 + x;
+      // padding rows are left untouched: they are zero in every buffer of the recurrence
+      if (!((mk >> z) & 1u)) continue;
+      const float4 yc = w[6 + z];
+      float4 hy = f4_add(acc4[r * 8 + vp], line_terms4<false>(w, 6 + z, c2));
+      hy = f4_fma(f2(vv[z]), yc, hy);
+      float4 res = f4_mul(alpha, f4_fma(negc, yc, hy));
+      if (prevp) {
+        // plain load: prev may be the output buffer (read here, then written by this thread)
+        const float4 pv = *(const float4*)(prevp + r * ldp);
+        res = f4_fma(beta, pv, res);
+      }
+      float* o = outp + r * ldo;
+      if (full) {
+        *(float4*)o = res;
+      } else {
+        if (vl < a.w) o[0] = res.x;
+        if (vl + 1 < a.w) o[1] = res.y;
+        if (vl + 2 < a.w) o[2] = res.z;
       }
     }
   }
@@ -622,6 +831,7 @@ cudaError_t launch_kb_gather(const Ham& H, const void* Y, int64_t ld, int w, int
 
 
 static bool g_brick16_attr[64] = {false};
+static bool g_brick32_attr[64] = {false};
 
 template <typename T>
 static cudaError_t step_t(const Ham& H, const void* in, int64_t ld_in, const void* prev, int64_t ld_prev,
@@ -650,6 +860,30 @@ static cudaError_t step_t(const Ham& H, const void* in, int64_t ld_in, const voi
   a.n_slots = H.grid.n_slots;
   const int w8 = (w + 7) / 8 * 8;
   StepArgs<float>& af = *reinterpret_cast<StepArgs<float>*>(&a);
+  // 0) wide brick kernel: 32-vector chunks, 16-byte rows, 32-bit row offsets inside a brick
+  {
+    const int w32 = (w + 31) / 32 * 32;
+    const bool ok = sizeof(T) == 4 && H.grid.B == 8 && w >= 32 && wavail >= w32 && cld >= w32 && cld % 4 == 0 &&
+                    ld_in % 4 == 0 && ld_out % 4 == 0 && (!prev || ld_prev % 4 == 0) && ((uintptr_t)in % 16) == 0 &&
+                    ((uintptr_t)out % 16) == 0 && (!prev || ((uintptr_t)prev % 16) == 0) &&
+                    ((uintptr_t)coef % 16) == 0 && 512 * std::max(ld_in, std::max(ld_out, prev ? ld_prev : 0)) <
+                                                          ((int64_t)1 << 31);
+    if (ok) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (dev >= 0 && dev < 64 && !g_brick32_attr[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(cheb_step_brick8w, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             8192 * 16);
+        if (e != cudaSuccess) return e;
+        g_brick32_attr[dev] = true;
+      }
+      const int nchunk = w32 / 32;
+      cheb_step_brick8w<<<(unsigned)(H.grid.n_bricks * nchunk), 512, 8192 * 16, st>>>(af, nchunk,
+                                                                                      H.d_kb_entry_lslot),
+          count_launch();
+      return cudaGetLastError();
+    }
+  }
   // 1) brick kernel with register halos: rows must have room for whole 8-vector chunks
   if (sizeof(T) == 4 && H.grid.B == 8 && wavail >= w8 && cld >= w8 && cld % 2 == 0) {
     const bool vec = (ld_in % 4 == 0) && (ld_out % 4 == 0) && (!prev || ld_prev % 4 == 0) && (cld % 2 == 0) &&
