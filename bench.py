@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--scf-max-steps", type=int, default=80)
     p.add_argument("--gap-study", action="store_true",
                    help="HOMO-LUMO gap and DOS (0.1 eV bins) vs cluster diameter from converged SCF runs")
+    p.add_argument("--learned-full", action="store_true",
+                   help="learned start with training clusters of 1-3 nm and a held-out 3 nm cluster (prints its own "
+                        "JSON line; several minutes)")
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-start comparison (train on 30 clusters, SCF on a held-out one)")
     return p.parse_args()
@@ -262,9 +265,9 @@ def run_scf_pair(args):
 
 
 # ------------------------------------------------------------------ learned start
-def run_learned_start(args):
-    """Train the learned start on 30 seeded rotated clusters (1-2.3 nm) from their
-    converged SCF potentials, then run the SCF of a held-out rotated 2.4 nm cluster from
+def run_learned_start(args, d_max: float = 2.3, d_test: float = 2.4, scf_kw=None, max_steps: int = 100):
+    """Train the learned start on 30 seeded rotated clusters (1 nm to d_max) from their
+    converged SCF potentials, then run the SCF of a held-out rotated d_test cluster from
     the superposition start and from the learned start (bf16 and FP32 inference)."""
     import torch
 
@@ -276,8 +279,9 @@ def run_learned_start(args):
     species = pseudo_params()
     t0 = time.perf_counter()
     Ds, Ts, skipped = [], [], 0
-    for seed, d, pos, z in training_clusters(30, seed0=1000, d_min_nm=1.0, d_max_nm=2.3):
-        D, T, info = learned.sample_cluster(pos, z, species, cluster_scf_config(d, z))
+    scf_kw = scf_kw or {}
+    for seed, d, pos, z in training_clusters(30, seed0=1000, d_min_nm=1.0, d_max_nm=d_max):
+        D, T, info = learned.sample_cluster(pos, z, species, cluster_scf_config(d, z), **scf_kw)
         if D is None:
             skipped += 1
             continue
@@ -291,7 +295,7 @@ def run_learned_start(args):
     model, losses = learned.train(D, T, steps=4000, batch=32768, lr=2e-3, seed=0, log_every=1000)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t1
-    d = 2.4
+    d = d_test
     pos, z = cluster_for_diameter(d)
     pos = pos @ random_rotation(4242).T
     cfg = cluster_scf_config(d, z)
@@ -299,7 +303,7 @@ def run_learned_start(args):
     for name, dv in (("superposition", None),
                      ("learned_bf16", lambda H: model.correction(H, pos, z, kscf.KSCF_MLP_BF16)),
                      ("learned_fp32", lambda H: model.correction(H, pos, z, kscf.KSCF_MLP_FP32))):
-        reps, wall, ex = learned.run_scf(pos, z, species, cfg, dv=dv, max_steps=100)
+        reps, wall, ex = learned.run_scf(pos, z, species, cfg, dv=dv, max_steps=max_steps, **scf_kw)
         runs[name] = {"steps": len(reps), "converged": bool(reps[-1]["converged"]), "wall_s": wall,
                       "sre_first_ry": reps[0]["sre_ry"],
                       "steps_to_sre_1ry": next((i + 1 for i, r in enumerate(reps) if r["sre_ry"] < 1.0), None),
@@ -313,8 +317,11 @@ def run_learned_start(args):
             "data_s": data_s, "train_s": train_s, "train_steps": 4000, "batch": 32768,
             "loss_standardised": losses, "heldout": {"d_nm": d, "n_atoms": len(z), "k": cfg["k"],
                                                        "rotation_seed": 4242},
-            "scf": {"precision": "mixed", "mixing": f"Anderson alpha {learned.ALPHA_DEFAULT}, Kerker q0 "
-                    f"{learned.KERKER_DEFAULT}, kT {learned.KT_DEFAULT}", "sre_tol_ry": 1e-4},
+            "scf": {"precision": "mixed", "settings": {"alpha": scf_kw.get("alpha", learned.ALPHA_DEFAULT),
+                                                        "kerker_q0": scf_kw.get("kerker_q0", learned.KERKER_DEFAULT),
+                                                        "kT": scf_kw.get("kT", learned.KT_DEFAULT),
+                                                        "first_iters": scf_kw.get("first_iters", 4)},
+                    "sre_tol_ry": 1e-4, "max_steps": max_steps},
             "runs": runs}
 
 
@@ -531,6 +538,13 @@ def main():
         return
     if args.gap_study:
         run_gap_study(args)
+        return
+    if args.learned_full:
+        # the 2.5-3 nm synthetic clusters are nearly gapless: Fermi smearing 5e-3 Ha, a
+        # weaker Kerker cut-off and eight CheFSI iterations in the first SCF step
+        res = run_learned_start(args, d_max=3.0, d_test=3.0,
+                                scf_kw={"alpha": 0.5, "kerker_q0": 0.3, "kT": 5e-3, "first_iters": 8}, max_steps=90)
+        print(json.dumps({"learned_start_3nm": res}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -90,7 +90,7 @@ def scf_until(S, n_atoms: int, max_steps: int, e_tol_per_atom: float = 0.0, sett
 
 def run_scf(pos, z, species, cfg: dict, dv=None, seed: int = 1, max_steps: int = 100, dtype=None, mode=None,
             keep=False, kT: float = KT_DEFAULT, alpha: float = ALPHA_DEFAULT, e_tol_per_atom: float = 0.0,
-            kerker_q0: float = KERKER_DEFAULT):
+            kerker_q0: float = KERKER_DEFAULT, first_iters: int = 4):
     """SCF on one cluster (mixed precision by default).  Returns (reports, wall_s, extra)
     where extra holds the grid/Hamiltonian/handle when keep=True."""
     import torch
@@ -98,7 +98,7 @@ def run_scf(pos, z, species, cfg: dict, dv=None, seed: int = 1, max_steps: int =
     mode = (kscf.KSCF_GEMM_TENSOR if dtype == kscf.KSCF_F32 else kscf.KSCF_GEMM_NATIVE) if mode is None else mode
     g, H = kscf.build_cluster(pos, z, species, cfg["radius"], cfg["h"])
     params = kscf.scf_params(cfg["k"], cfg["degree"], dtype=dtype, gemm_mode=mode, kT=kT, mix_alpha=alpha,
-                             kerker_q0=kerker_q0)
+                             kerker_q0=kerker_q0, first_iters=first_iters)
     S = kscf.Scf(H, pos, z, species, params)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -120,12 +120,12 @@ def run_scf(pos, z, species, cfg: dict, dv=None, seed: int = 1, max_steps: int =
 SRE_ACCEPT_RY = 2e-3
 
 
-def sample_cluster(pos, z, species, cfg: dict, seed: int = 1):
+def sample_cluster(pos, z, species, cfg: dict, seed: int = 1, **scf_kw):
     """(D, dV, info) of the domain points of one self-consistent cluster (float32 device
     tensors); (None, None, info) when its SCF does not reach SRE < SRE_ACCEPT_RY in 100
     steps."""
     import torch
-    reps, wall, ex = run_scf(pos, z, species, cfg, seed=seed, keep=True)
+    reps, wall, ex = run_scf(pos, z, species, cfg, seed=seed, keep=True, **scf_kw)
     if not (reps[-1]["converged"] or reps[-1]["sre_ry"] < SRE_ACCEPT_RY):
         ex["scf"].free()
         return None, None, {"steps": len(reps), "wall_s": wall, "converged": False}
