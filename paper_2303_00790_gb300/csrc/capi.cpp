@@ -513,6 +513,10 @@ extern "C" int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int 
   KSCF_CUDA_TRY(launch_symmetrize(Hs, k, k, st));
   SOLVER_TRY(cusolverDnDsyevd(hs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, k, Hs, k, W, lwork,
                               (int)(p.lwork_bytes / 8 - 32), info));
+  // eigenvector signs chosen so that diag(Q) >= 0: for an input block already close to
+  // Ritz vectors Q is then close to the identity, and the tensor-core rotation is applied
+  // as X + X (Q - I), whose rounding error scales with |Q - I| instead of |Q|
+  if (mode == KSCF_GEMM_TENSOR) KSCF_CUDA_TRY(launch_sign_fix(Hs, k, st));
   if (mode != KSCF_GEMM_TENSOR) KSCF_CUDA_TRY(launch_f64_to_dtype(Hs, (int64_t)k * k, dtype, Qm, st));
   int hinfo = 0;
   KSCF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -529,7 +533,8 @@ extern "C" int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int 
       set_error("kscf_rayleigh_ritz: non-finite Ritz value");
       return KSCF_ERR_NONFINITE;
     }
-  return rotate_inplace(X, ld, rows, k, dtype, mode, Qm, Hs, false, panel, p.prows, tcw, p.tc, st);
+  return rotate_inplace(X, ld, rows, k, dtype, mode, Qm, Hs, mode == KSCF_GEMM_TENSOR, panel, p.prows, tcw, p.tc,
+                        st);
 }
 
 extern "C" int kscf_density(const kscf_ham* ham, const void* X, int64_t ld, int n_occ, int dtype, const double* occ,

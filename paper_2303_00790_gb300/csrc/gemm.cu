@@ -186,6 +186,23 @@ cudaError_t launch_symmetrize(double* C, int k, int64_t ldc, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Column j of the column-major k x k Q is negated when Q[j][j] < 0 (eigenvectors are
+// defined up to sign; this makes Q close to the identity when the input columns are
+// already close to eigenvectors).
+__global__ void sign_fix_kernel(double* Q, int k) {
+  const int j = blockIdx.x;
+  if (j >= k) return;
+  double* col = Q + (int64_t)j * k;
+  if (!(col[j] < 0.0)) return;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) col[i] = -col[i];
+}
+
+cudaError_t launch_sign_fix(double* Q, int k, cudaStream_t st) {
+  if (k == 0) return cudaSuccess;
+  sign_fix_kernel<<<k, 128, 0, st>>>(Q, k), count_launch();
+  return cudaGetLastError();
+}
+
 // S[i][i] += rel * max_i S[i][i]  (one block; S column-major k x k)
 __global__ void shift_diag_kernel(double* S, int k, double rel) {
   __shared__ double sm[32];

@@ -122,6 +122,8 @@ cudaError_t launch_rotate_native(const void* A, int64_t lda, const void* Q, int6
 cudaError_t launch_symmetrize(double* C, int k, int64_t ldc, cudaStream_t st);
 // S[i][i] += rel * max_i S[i][i]
 cudaError_t launch_shift_diag(double* S, int k, double rel, cudaStream_t st);
+// negate the columns of Q (column-major k x k) whose diagonal element is negative
+cudaError_t launch_sign_fix(double* Q, int k, cudaStream_t st);
 cudaError_t launch_upper_to_dtype(const double* R, int k, int dtype, void* out, cudaStream_t st);
 cudaError_t launch_f64_to_dtype(const double* src, int64_t n, int dtype, void* out, cudaStream_t st);
 

@@ -313,3 +313,31 @@ def test_orthonormalize_recovers_from_rank_deficiency(kscf, species, mode):
     G = kscf.kscf_gram(X[:, :k], X[:, :k], scale=H.h3).cpu().numpy()
     assert np.max(np.abs(G - np.eye(k))) < 1e-4
     assert torch.all(torch.isfinite(X)).item()
+
+
+def test_tensor_rayleigh_ritz_is_stable_on_ritz_vectors(kscf, species):
+    # a second Rayleigh-Ritz on Ritz vectors must leave them (nearly) unchanged: the
+    # eigenvector signs make Q ~ I and the rotation is applied as X + X (Q - I)
+    pos, z = small_cluster()
+    g, H = kscf.build_cluster(pos, z, species, 8.0, 0.7)
+    k = 64
+    X = torch.zeros((g.info["n_slots"], k), dtype=torch.float32, device="cuda")
+    kscf.kscf_random_subspace(H, X, seed=5)
+    lo, hi = kscf.kscf_spectral_bounds(H)
+    kscf.kscf_orthonormalize(H, X, mode=kscf.KSCF_GEMM_TENSOR)
+    lam = kscf.kscf_rayleigh_ritz(H, X, mode=kscf.KSCF_GEMM_TENSOR)
+    for _ in range(6):
+        kscf.kscf_chebyshev_filter(H, X, 10, lam[-1], hi, lam[0])
+        kscf.kscf_orthonormalize(H, X, mode=kscf.KSCF_GEMM_TENSOR)
+        lam = kscf.kscf_rayleigh_ritz(H, X, mode=kscf.KSCF_GEMM_TENSOR)
+    X1 = X.clone()
+    lam2 = kscf.kscf_rayleigh_ritz(H, X, mode=kscf.KSCF_GEMM_TENSOR)
+    assert np.max(np.abs(lam2 - lam)) < 1e-6 * np.max(np.abs(lam))
+    # columns with well separated Ritz values keep their direction and sign
+    sep = np.ones(k, dtype=bool)
+    gaps = np.diff(lam2)
+    sep[1:] &= gaps > 1e-3
+    sep[:-1] &= gaps > 1e-3
+    d = torch.max(torch.abs(X - X1), dim=0).values.cpu().numpy()
+    scale = torch.max(torch.abs(X1)).item()
+    assert np.max(d[sep]) < 1e-4 * scale, np.max(d[sep]) / scale
