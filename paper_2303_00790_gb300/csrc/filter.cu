@@ -304,15 +304,16 @@ __global__ void __launch_bounds__(NV * 32, NV == 8 ? 3 : 2)
 }
 
 // ---------------------------------------------------------------------------
-// Wide brick kernel (FP32, 8^3 bricks): one CTA per (brick, 32 vectors), 512 threads,
-// eight lanes per line and four vectors per lane (16-byte loads and stores), so that
+// Wide brick kernel (FP32, 8^3 bricks): one CTA per (brick, NV = 16 or 32 vectors),
+// NV/4 lanes per line and four vectors per lane (16-byte loads and stores), so that
 // every address computation, load and store serves four vectors.  Same three line passes
 // as the kernel above; in addition, every neighbour brick gets one 64-bit base pointer
 // per CTA and rows inside a brick are addressed with 32-bit offsets; halo loads are
 // branch-free (a missing neighbour is read from this brick and the value discarded);
 // padding rows of the core are zero-filled instead of read.  Shared memory: core and
-// accumulator, 512 point slots of 128 bytes each (a line's eight lanes cover all 32
-// banks, so no swizzle is needed).
+// accumulator, 512 point slots of 4*NV bytes each (NV = 32: a line's eight lanes cover all
+// 32 banks; NV = 16: slots XOR-swizzled like the 16-vector kernel above).  NV = 16 fits two
+// CTAs per SM at 128 registers, so that one CTA's loads overlap the other's arithmetic.
 namespace {
 __device__ __forceinline__ float4 f4_add(float4 a, float4 b) {
   const float2 lo = f2_add(make_float2(a.x, a.y), make_float2(b.x, b.y));
@@ -341,14 +342,19 @@ __device__ __forceinline__ float4 line_terms4(const float4* w, int i, const floa
 __device__ __forceinline__ float4 ld4(const float* p) { return __ldg((const float4*)p); }
 }  // namespace
 
-__global__ void __launch_bounds__(512, 1)
+template <int NV>
+__global__ void __launch_bounds__(NV * 16, NV == 16 ? 2 : 1)
     cheb_step_brick8w(StepArgs<float> a, int nchunk, const uint16_t* __restrict__ entry_lslot) {
+  static_assert(NV == 16 || NV == 32, "16 or 32 vectors per CTA");
+  constexpr int VPL = NV / 4;   // lanes per line (four vectors each)
   extern __shared__ float4 sw4[];
-  float4* core4 = sw4;          // [512][8]
-  float4* acc4 = sw4 + 4096;    // [512][8]
+  float4* core4 = sw4;                // [512][VPL]
+  float4* acc4 = sw4 + 512 * VPL;     // [512][VPL]
+  // 64-byte point slots (NV = 16): x ^ (y & 1) keeps the lines of a warp on distinct banks
+  auto sl = [](int x, int y, int z) { return (z * 8 + y) * 8 + (NV == 16 ? (x ^ (y & 1)) : x); };
   const int brick = blockIdx.x / nchunk, chunk = blockIdx.x - (blockIdx.x / nchunk) * nchunk;
-  const int tid = threadIdx.x, vp = tid & 7, line = tid >> 3;
-  const int vl = chunk * 32 + 4 * vp;
+  const int tid = threadIdx.x, vp = tid % VPL, line = tid / VPL;
+  const int vl = chunk * NV + 4 * vp;
   const int64_t b0 = (int64_t)brick * 512;
   const int ld = (int)a.ld_in;  // 512 * ld < 2^31 (checked by the launcher)
   const float* __restrict__ in = a.in;
@@ -363,12 +369,12 @@ __global__ void __launch_bounds__(512, 1)
   }
   // ---- core: 512 rows x 128 bytes, padding rows zero-filled ----
   {
-    const float* src = in + b0 * a.ld_in + chunk * 32 + 4 * vp;
+    const float* src = in + b0 * a.ld_in + chunk * NV + 4 * vp;
 #pragma unroll
     for (int i = 0; i < 8; i++) {
       const int r = line + 64 * i;
       const uint32_t live = __ldg(a.mask + b0 + r);
-      const uint32_t d = (uint32_t)__cvta_generic_to_shared(&core4[r * 8 + vp]);
+      const uint32_t d = (uint32_t)__cvta_generic_to_shared(&core4[sl(r & 7, (r >> 3) & 7, r >> 6) * VPL + vp]);
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src + r * ld), "r"(live ? 16 : 0)
                    : "memory");
     }
@@ -405,9 +411,9 @@ __global__ void __launch_bounds__(512, 1)
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
 #pragma unroll
-    for (int x = 0; x < 8; x++) w[6 + x] = core4[((z * 8 + y) * 8 + x) * 8 + vp];
+    for (int x = 0; x < 8; x++) w[6 + x] = core4[sl(x, y, z) * VPL + vp];
 #pragma unroll
-    for (int x = 0; x < 8; x++) acc4[((z * 8 + y) * 8 + x) * 8 + vp] = line_terms4<true>(w, 6 + x, c2);
+    for (int x = 0; x < 8; x++) acc4[sl(x, y, z) * VPL + vp] = line_terms4<true>(w, 6 + x, c2);
   }
   // ---- y pass: line (x, z) ----
   {
@@ -421,11 +427,11 @@ __global__ void __launch_bounds__(512, 1)
       w[14 + yy] = nbv[3] ? p : z4;
     }
 #pragma unroll
-    for (int y = 0; y < 8; y++) w[6 + y] = core4[((z * 8 + y) * 8 + x) * 8 + vp];
+    for (int y = 0; y < 8; y++) w[6 + y] = core4[sl(x, y, z) * VPL + vp];
     __syncthreads();  // x-pass accumulator writes are visible
 #pragma unroll
     for (int y = 0; y < 8; y++) {
-      const int q = ((z * 8 + y) * 8 + x) * 8 + vp;
+      const int q = sl(x, y, z) * VPL + vp;
       acc4[q] = f4_add(acc4[q], line_terms4<false>(w, 6 + y, c2));
     }
   }
@@ -458,7 +464,7 @@ __global__ void __launch_bounds__(512, 1)
         c = f4_fma(f2(ch[u].y), cv[u][1], c);
         c = f4_fma(f2(ch[u].z), cv[u][2], c);
         c = f4_fma(f2(ch[u].w), cv[u][3], c);
-        float* acc = (float*)&acc4[ls[u] * 8 + vp];
+        float* acc = (float*)&acc4[sl(ls[u] & 7, (ls[u] >> 3) & 7, ls[u] >> 6) * VPL + vp];
         atomicAdd(acc, c.x);
         atomicAdd(acc + 1, c.y);
         atomicAdd(acc + 2, c.z);
@@ -478,7 +484,7 @@ __global__ void __launch_bounds__(512, 1)
       w[14 + zz] = nbv[5] ? p : z4;
     }
 #pragma unroll
-    for (int z = 0; z < 8; z++) w[6 + z] = core4[(z * 64 + y * 8 + x) * 8 + vp];
+    for (int z = 0; z < 8; z++) w[6 + z] = core4[sl(x, y, z) * VPL + vp];
     __syncthreads();  // scatter atomics are complete
     const bool full = vl + 3 < a.w;
     const float2 alpha = f2(a.alpha), beta = f2(a.beta), negc = f2(-a.c);
@@ -491,7 +497,7 @@ __global__ void __launch_bounds__(512, 1)
       // padding rows are left untouched: they are zero in every buffer of the recurrence
       if (!((mk >> z) & 1u)) continue;
       const float4 yc = w[6 + z];
-      float4 hy = f4_add(acc4[r * 8 + vp], line_terms4<false>(w, 6 + z, c2));
+      float4 hy = f4_add(acc4[sl(x, y, z) * VPL + vp], line_terms4<false>(w, 6 + z, c2));
       hy = f4_fma(f2(vv[z]), yc, hy);
       float4 res = f4_mul(alpha, f4_fma(negc, yc, hy));
       if (prevp) {
@@ -860,10 +866,12 @@ static cudaError_t step_t(const Ham& H, const void* in, int64_t ld_in, const voi
   a.n_slots = H.grid.n_slots;
   const int w8 = (w + 7) / 8 * 8;
   StepArgs<float>& af = *reinterpret_cast<StepArgs<float>*>(&a);
-  // 0) wide brick kernel: 32-vector chunks, 16-byte rows, 32-bit row offsets inside a brick
+  // 0) wide brick kernel: 16-vector chunks (two CTAs per SM), 16-byte rows, 32-bit row offsets
+  //    inside a brick
   {
-    const int w32 = (w + 31) / 32 * 32;
-    const bool ok = sizeof(T) == 4 && H.grid.B == 8 && w >= 32 && wavail >= w32 && cld >= w32 && cld % 4 == 0 &&
+    constexpr int WNV = 16;
+    const int wn = (w + WNV - 1) / WNV * WNV;
+    const bool ok = sizeof(T) == 4 && H.grid.B == 8 && w >= WNV && wavail >= wn && cld >= wn && cld % 4 == 0 &&
                     ld_in % 4 == 0 && ld_out % 4 == 0 && (!prev || ld_prev % 4 == 0) && ((uintptr_t)in % 16) == 0 &&
                     ((uintptr_t)out % 16) == 0 && (!prev || ((uintptr_t)prev % 16) == 0) &&
                     ((uintptr_t)coef % 16) == 0 && 512 * std::max(ld_in, std::max(ld_out, prev ? ld_prev : 0)) <
@@ -871,15 +879,16 @@ static cudaError_t step_t(const Ham& H, const void* in, int64_t ld_in, const voi
     if (ok) {
       int dev = 0;
       cudaGetDevice(&dev);
+      const int smem = 2 * 512 * (WNV / 4) * 16;
       if (dev >= 0 && dev < 64 && !g_brick32_attr[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(cheb_step_brick8w, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             8192 * 16);
+        cudaError_t e = cudaFuncSetAttribute(cheb_step_brick8w<WNV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem);
         if (e != cudaSuccess) return e;
         g_brick32_attr[dev] = true;
       }
-      const int nchunk = w32 / 32;
-      cheb_step_brick8w<<<(unsigned)(H.grid.n_bricks * nchunk), 512, 8192 * 16, st>>>(af, nchunk,
-                                                                                      H.d_kb_entry_lslot),
+      const int nchunk = wn / WNV;
+      cheb_step_brick8w<WNV><<<(unsigned)(H.grid.n_bricks * nchunk), WNV * 16, smem, st>>>(af, nchunk,
+                                                                                           H.d_kb_entry_lslot),
           count_launch();
       return cudaGetLastError();
     }
