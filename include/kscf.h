@@ -230,11 +230,15 @@ int kscf_chebyshev_filter(const kscf_ham* ham, void* X, int64_t ld, int k, int d
  *   S = h^3 X^T X (k x k, FP64 sums), S = R^T R (FP64 Cholesky), X <- X R^-1,
  * so that h^3 X^T X = I.  For F32 X the step is repeated once (CholeskyQR2,
  * Yamamoto et al. 2015), the second rotation applied as X + X (R2^-1 - I).  Returns
- * KSCF_ERR_NOT_SPD if the Cholesky factorisation fails (X rank-deficient in its
- * precision); X is then left unchanged.
- * With mode | KSCF_ORTHO_ALLOW_SHIFT, a failed first factorisation is retried with the
- * Gram diagonal raised by 16 k u max_i S_ii (u = 2^-24 for F32, 2^-53 for F64; shifted
- * Cholesky-QR, Fukaya et al. 2020) and followed by one extra unshifted pass: a block that
+ * KSCF_ERR_NOT_SPD if the Cholesky factorisation fails, i.e. a pivot c (0-based) is not
+ * above (c + 8) 2^-53 S_cc (X rank-deficient to working precision); X is then left
+ * unchanged.  KSCF_ERR_TIMEOUT if a bounded grid barrier of the factorisation kernel
+ * gave up.
+ * With mode | KSCF_ORTHO_ALLOW_SHIFT, the first factorisation also fails on a pivot not
+ * above 8 u S_cc (the Gram matrix's own rounding level), and a failed first factorisation
+ * is retried with the Gram diagonal raised by 16 k u max_i S_ii (u = 2^-24 for F32, 2^-53
+ * for F64; shifted Cholesky-QR, Fukaya et al. 2020) and followed by one extra unshifted
+ * pass: a block that
  * is rank-deficient only at its working precision then still yields an orthonormal
  * basis (its near-dependent directions filled from rounding-level components), which is
  * what subspace iteration needs; if a later pass fails, X may have been changed.

@@ -1,6 +1,9 @@
 // FP32 / packed FP32x2 / FP64 FMA throughput microbenchmark (standalone program):
 // eight independent FMA chains per thread, 8 CTAs of 256 threads per SM, result written
 // once per thread.  Used to state the ALU roofs that the copy/GEMM peaks do not cover.
+// A second part times FP64 instruction sequences inside one CTA (1, 4 or 8 warps; 1 or 32
+// active lanes) with clock64: the cost of one warp-wide FP64 instruction on one SM
+// sub-partition, which sets the length of the sequential chains of small dense kernels.
 #include <cstdio>
 #include <cuda_runtime.h>
 template <typename T> __global__ void fma_kernel(T* out, T a, T b, int iters) {
@@ -26,6 +29,36 @@ __global__ void fma2_kernel(float2* out, float a, float b, int iters) {
   for (int q = 0; q < 8; q++) { s.x += x[q].x; s.y += x[q].y; }
   out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
+// one CTA; lanes < active run n FP64 operations: 0 = dependent FMA chain, 1 = eight
+// independent FMA chains, 2 = dependent sqrt chain, 3 = dependent division chain
+__global__ void fp64_chain_kernel(double* out, long long* cyc, int n, int mode, int active) {
+  const int lane = threadIdx.x & 31;
+  double a[8];
+  for (int q = 0; q < 8; q++) a[q] = 1.0 + 1e-9 * threadIdx.x + 0.1 * q;
+  const double b = 0.999999, c = 1e-7;
+  __syncthreads();
+  const long long t0 = clock64();
+  if (lane < active) {
+    if (mode == 0) {
+      for (int i = 0; i < n; i++) a[0] = fma(a[0], b, c);
+    } else if (mode == 1) {
+      for (int i = 0; i < n; i += 8)
+#pragma unroll
+        for (int q = 0; q < 8; q++) a[q] = fma(a[q], b, c);
+    } else if (mode == 2) {
+      for (int i = 0; i < n; i++) a[0] = sqrt(a[0]) + c;
+    } else {
+      for (int i = 0; i < n; i++) a[0] = b / a[0] + c;
+    }
+  }
+  __syncthreads();
+  const long long t1 = clock64();
+  double s = 0.0;
+  for (int q = 0; q < 8; q++) s += a[q];
+  out[threadIdx.x] = s;
+  if (threadIdx.x == 0) *cyc = t1 - t0;
+}
+
 int main() {
   int sms; cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
   const int blocks = sms * 8, threads = 256, iters = 1 << 16;
@@ -47,6 +80,19 @@ int main() {
     cudaEventSynchronize(e1); cudaEventElapsedTime(&ms, e0, e1);
     printf("fp64 fma: %.3f TFLOP/s\n", fl / 16 / ms / 1e9);
   }
+  long long* cyc;
+  cudaMalloc(&cyc, sizeof(long long));
+  const char* names[] = {"dfma dependent", "dfma 8 independent", "sqrt dependent", "div dependent"};
+  for (int mode = 0; mode < 4; mode++)
+    for (int warps : {1, 4, 8})
+      for (int active : {1, 32}) {
+        const int n = mode < 2 ? 4096 : 256;
+        for (int rep = 0; rep < 2; rep++) fp64_chain_kernel<<<1, 32 * warps>>>((double*)out, cyc, n, mode, active);
+        long long c = 0;
+        cudaMemcpy(&c, cyc, sizeof(c), cudaMemcpyDeviceToHost);
+        printf("%-20s warps %d lanes %2d: %7.1f cycles per operation per warp\n", names[mode], warps, active,
+               (double)c / n);
+      }
   printf("sms %d err %s\n", sms, cudaGetErrorString(cudaGetLastError()));
   return 0;
 }

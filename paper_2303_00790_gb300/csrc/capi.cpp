@@ -1,6 +1,7 @@
 // C ABI drivers of the CheFSI hot path: Hamiltonian apply, Chebyshev filter,
 // Cholesky-QR, Rayleigh-Ritz, density and the initial subspace (arXiv 2303.00790,
-// CheFSI paragraph).  The k x k FP64 factorisations call cuSOLVER.
+// CheFSI paragraph).  The FP64 Cholesky factor and its inverse come from chol.cu; the
+// k x k FP64 symmetric eigensolver is cuSOLVER's.
 #include <cusolverDn.h>
 
 #include <algorithm>
@@ -118,24 +119,15 @@ int64_t panel_rows(int64_t n_slots, int k, int dtype) {
 }
 
 struct OrthoPlan {
-  size_t S, Rinv, info, lwork_bytes, host_bytes, panel, tc;
+  size_t S, Rinv, info, chol, panel, tc;
   int64_t prows;
 };
 
 int ortho_plan(const Ham& H, int k, int dtype, int mode, OrthoPlan* p) {
-  cusolverDnHandle_t hs;
-  int rc = solver_handle(&hs);
-  if (rc) return rc;
-  int lw_potrf = 0;
-  SOLVER_TRY(cusolverDnDpotrf_bufferSize(hs, CUBLAS_FILL_MODE_UPPER, k, nullptr, k, &lw_potrf));
-  size_t dev_tr = 0, host_tr = 0;
-  SOLVER_TRY(cusolverDnXtrtri_bufferSize(hs, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, k, CUDA_R_64F,
-                                         nullptr, k, &dev_tr, &host_tr));
   p->S = (size_t)k * k * 8;
   p->Rinv = (size_t)k * k * esize(dtype);
   p->info = 256;
-  p->lwork_bytes = std::max((size_t)lw_potrf * 8, dev_tr) + 256;
-  p->host_bytes = host_tr;
+  p->chol = chol_inv_work_bytes(k);
   p->prows = panel_rows(H.grid.n_slots, k, dtype);
   p->panel = (size_t)p->prows * k * esize(dtype);
   p->tc = 0;
@@ -145,7 +137,7 @@ int ortho_plan(const Ham& H, int k, int dtype, int mode, OrthoPlan* p) {
 }
 
 size_t ortho_bytes(const OrthoPlan& p) {
-  return kscf_align256(p.S) + kscf_align256(p.Rinv) + kscf_align256(p.info) + kscf_align256(p.lwork_bytes) +
+  return kscf_align256(p.S) + kscf_align256(p.Rinv) + kscf_align256(p.info) + kscf_align256(p.chol) +
          kscf_align256(p.panel) + kscf_align256(p.tc);
 }
 
@@ -248,71 +240,62 @@ int gram(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t rows, i
   return KSCF_OK;
 }
 
-// One Cholesky-QR pass: S = h^3 X^T X, S = R^T R, X <- X R^-1.  When the factorisation
-// fails and `shifted` is non-null, the Gram matrix is recomputed and its diagonal shifted
-// by 16 k u max_i S_ii (u the unit roundoff of X's type) before a second attempt (shifted
-// Cholesky-QR, Fukaya, Kannan, Nakatsukasa, Yamamoto & Yanagisawa 2020); *shifted then
-// reports that X is not yet orthonormal and needs further passes.
+// One Cholesky-QR pass: S = h^3 X^T X, S = R^T R, X <- X R^-1 (the factor and its inverse
+// from one FP64 kernel, chol.cu).  When the factorisation fails and `shifted` is non-null,
+// the Gram matrix is recomputed and its diagonal shifted by 16 k u max_i S_ii (u the unit
+// roundoff of X's type) before a second attempt (shifted Cholesky-QR, Fukaya, Kannan,
+// Nakatsukasa, Yamamoto & Yanagisawa 2020); *shifted then reports that X is not yet
+// orthonormal and needs further passes.  With `shifted` non-null the first attempt also
+// fails on a pivot at the Gram matrix's own rounding level (8 u S_cc), where the plain
+// factor would amplify rounding noise into the basis.
 int cholqr_pass(const Ham& H, void* X, int64_t ld, int k, int dtype, int mode, const OrthoPlan& p, Carver& cv,
                 bool second_pass, cudaStream_t st, bool* shifted = nullptr) {
-  cusolverDnHandle_t hs;
-  int rc = solver_handle(&hs);
-  if (rc) return rc;
-  SOLVER_TRY(cusolverDnSetStream(hs, st));
   Carver c = cv;
   double* S = (double*)c.take(p.S);
   void* Rinv = c.take(p.Rinv);
-  int* info = (int*)c.take(p.info);
-  void* lwork = c.take(p.lwork_bytes);
+  int* status = (int*)c.take(p.info);
+  void* cwork = c.take(p.chol);
   void* panel = c.take(p.panel);
   void* tcw = c.take(p.tc);
   const double h3 = H.grid.h * H.grid.h * H.grid.h;
   const int64_t rows = H.grid.n_slots;
-  rc = gram(X, ld, X, ld, rows, k, k, dtype, mode, h3, S, k, tcw, p.tc, st);
+  const double u = dtype == KSCF_F64 ? 0x1.0p-53 : 0x1.0p-24;
+  int hst[2] = {0, 0};
+  auto factor = [&](double floor_rel) -> int {
+    KSCF_CUDA_TRY(launch_chol_inv(S, k, k, floor_rel, S, k, cwork, status, st));
+    KSCF_CUDA_TRY(cudaMemcpyAsync(hst, status, sizeof(hst), cudaMemcpyDeviceToHost, st));
+    KSCF_CUDA_TRY(cudaStreamSynchronize(st));
+    int r = check_tc(mode, "Cholesky-QR");
+    if (r) return r;
+    if (hst[1] != 0) {
+      set_error("Cholesky-QR: a grid barrier of the factorisation kernel timed out");
+      return KSCF_ERR_TIMEOUT;
+    }
+    return KSCF_OK;
+  };
+  int rc = gram(X, ld, X, ld, rows, k, k, dtype, mode, h3, S, k, tcw, p.tc, st);
   if (rc) return rc;
-  SOLVER_TRY(cusolverDnDpotrf(hs, CUBLAS_FILL_MODE_UPPER, k, S, k, (double*)lwork, (int)(p.lwork_bytes / 8 - 32),
-                              info));
-  int hinfo = 0;
-  KSCF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
-  KSCF_CUDA_TRY(cudaStreamSynchronize(st));
-  rc = check_tc(mode, "Cholesky-QR");
+  rc = factor(shifted ? 8.0 * u : 0.0);
   if (rc) return rc;
-  if (hinfo > 0 && shifted) {
+  if (hst[0] > 0 && shifted) {
     rc = gram(X, ld, X, ld, rows, k, k, dtype, mode, h3, S, k, tcw, p.tc, st);
     if (rc) return rc;
-    const double u = dtype == KSCF_F64 ? 0x1.0p-53 : 0x1.0p-24;
     KSCF_CUDA_TRY(launch_shift_diag(S, k, 16.0 * k * u, st));
-    SOLVER_TRY(cusolverDnDpotrf(hs, CUBLAS_FILL_MODE_UPPER, k, S, k, (double*)lwork, (int)(p.lwork_bytes / 8 - 32),
-                                info));
-    KSCF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
-    KSCF_CUDA_TRY(cudaStreamSynchronize(st));
-    rc = check_tc(mode, "Cholesky-QR");
+    rc = factor(0.0);
     if (rc) return rc;
-    if (hinfo == 0) *shifted = true;
+    if (hst[0] == 0) *shifted = true;
   }
-  if (hinfo != 0) {
-    set_error("Cholesky-QR: Gram matrix not positive definite (potrf info %d%s)", hinfo,
+  if (hst[0] != 0) {
+    set_error("Cholesky-QR: Gram matrix not positive definite (pivot %d%s)", hst[0],
               second_pass ? ", second pass" : (shifted ? ", also with the diagonal shift" : ""));
     return KSCF_ERR_NOT_SPD;
   }
-  std::vector<char> hostw(std::max<size_t>(p.host_bytes, 1));
-  SOLVER_TRY(cusolverDnXtrtri(hs, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT, k, CUDA_R_64F, S, k, lwork,
-                              p.lwork_bytes - 256, hostw.data(), p.host_bytes, info));
-  // S now holds R^-1 in its upper triangle; zero the rest (and convert for the native path)
-  KSCF_CUDA_TRY(launch_upper_to_dtype(S, k, KSCF_F64, S, st));
+  // S now holds R^-1 (upper triangular, zero below); the native path takes it in X's type
   if (mode != KSCF_GEMM_TENSOR) KSCF_CUDA_TRY(launch_upper_to_dtype(S, k, dtype, Rinv, st));
   rc = rotate_inplace(X, ld, rows, k, dtype, mode, Rinv, S, second_pass, panel, p.prows, tcw, p.tc, st);
   if (rc) return rc;
-  // the trtri status is read together with the next synchronisation
-  KSCF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
   KSCF_CUDA_TRY(cudaStreamSynchronize(st));
-  rc = check_tc(mode, "Cholesky-QR");
-  if (rc) return rc;
-  if (hinfo != 0) {
-    set_error("Cholesky-QR: triangular inverse failed (info %d)", hinfo);
-    return KSCF_ERR_NOT_SPD;
-  }
-  return KSCF_OK;
+  return check_tc(mode, "Cholesky-QR");
 }
 
 }  // namespace

@@ -127,6 +127,28 @@ def test_orthonormalize_matches_oracle(kscf, system):
     assert np.max(np.abs(h3 * got.T @ got - np.eye(k))) < 1e-12
 
 
+@pytest.mark.parametrize("k", [33, 100, 200])
+def test_orthonormalize_many_tiles_matches_oracle(kscf, system, k):
+    # the FP64 factorisation runs on 32 x 32 tiles: blocks spanning several tiles with a
+    # ragged last tile, against the oracle's Cholesky-QR (columns of very different norms)
+    from oracle.chefsi import cholesky_qr
+    from workloads import random_block_lex
+    X = random_block_lex(11, system["n"], k) * np.logspace(0, -2, k)[None, :]
+    X[:, k // 2:] += 0.3 * X[:, :k - k // 2]
+    Xd = dev(to_slots(X, system["lex"]))
+    kscf.kscf_orthonormalize(system["H"], Xd)
+    got = from_slots(Xd.cpu().numpy(), system["lex"], system["n"])
+    ref, _ = cholesky_qr(X, system["OH"].h3)
+    assert np.max(np.abs(got - ref)) <= 1e-9 * np.max(np.abs(ref))
+    h3 = system["OH"].h3
+    assert np.max(np.abs(h3 * got.T @ got - np.eye(k))) < 1e-11
+    Xf = dev(to_slots(X, system["lex"]), torch.float32)
+    kscf.kscf_orthonormalize(system["H"], Xf, mode=kscf.KSCF_GEMM_TENSOR)
+    gf = from_slots(Xf.double().cpu().numpy(), system["lex"], system["n"])
+    assert np.max(np.abs(h3 * gf.T @ gf - np.eye(k))) < 2e-6
+    assert subspace_gap(gf, X, h3) < 1e-4
+
+
 def test_orthonormalize_f32_is_orthonormal(kscf, system):
     from workloads import random_block_lex
     k = 24
