@@ -16,7 +16,7 @@ using namespace kscf;
 namespace kscf {
 cudaError_t launch_gram_tc(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t rows, int m, int n,
                            double scale, double* C, int64_t ldc, bool accumulate, void* work, size_t work_bytes,
-                           cudaStream_t st);
+                           cudaStream_t st, bool symmetric_result = false);
 cudaError_t launch_rotate_tc(const float* A, int64_t lda, const double* Q, int64_t ldq, int64_t rows, int kin,
                              int kout, bool add_identity_input, float* out, int64_t ldo, void* work,
                              size_t work_bytes, cudaStream_t st);
@@ -129,7 +129,7 @@ int ortho_plan(const Ham& H, int k, int dtype, int mode, OrthoPlan* p) {
   p->info = 256;
   p->chol = chol_inv_work_bytes(k);
   p->prows = panel_rows(H.grid.n_slots, k, dtype);
-  p->panel = (size_t)p->prows * k * esize(dtype);
+  p->panel = mode == KSCF_GEMM_TENSOR ? 0 : (size_t)p->prows * k * esize(dtype);
   p->tc = 0;
   if (mode == KSCF_GEMM_TENSOR)
     p->tc = std::max(gram_tc_work_bytes(H.grid.n_slots, k, k), rotate_tc_work_bytes(p->prows, k, k));
@@ -163,7 +163,7 @@ int rr_plan(const Ham& H, int k, int dtype, int mode, int block, RRPlan* p) {
   p->info = 256;
   p->lwork_bytes = (size_t)lw * 8 + 256;
   p->prows = panel_rows(H.grid.n_slots, k, dtype);
-  p->panel = (size_t)p->prows * k * esize(dtype);
+  p->panel = mode == KSCF_GEMM_TENSOR ? 0 : (size_t)p->prows * k * esize(dtype);
   p->tc = 0;
   if (mode == KSCF_GEMM_TENSOR)
     p->tc = std::max(gram_tc_work_bytes(H.grid.n_slots, k, p->w), rotate_tc_work_bytes(p->prows, k, k));
@@ -211,7 +211,9 @@ int check_mode(int dtype, int mode, const char* who) {
 }
 
 // X <- X Qm (Qm column-major k x k in the dtype of X for the native path, FP64 for the
-// tensor path) in row panels through the panel buffer.
+// tensor path) in row panels.  The tensor path writes each panel in place (its product
+// reads the panel's bf16 pieces, made before the launch); the native path goes through
+// the panel buffer.
 int rotate_inplace(void* X, int64_t ld, int64_t rows, int k, int dtype, int mode, const void* Qm, const double* Q64,
                    bool near_identity, void* panel, int64_t prows, void* tcwork, size_t tcbytes, cudaStream_t st) {
   const size_t es = esize(dtype);
@@ -219,21 +221,24 @@ int rotate_inplace(void* X, int64_t ld, int64_t rows, int k, int dtype, int mode
     const int64_t nr = std::min(prows, rows - r0);
     char* Xr = (char*)X + (size_t)r0 * ld * es;
     if (mode == KSCF_GEMM_TENSOR) {
-      KSCF_CUDA_TRY(launch_rotate_tc((const float*)Xr, ld, Q64, k, nr, k, k, near_identity, (float*)panel, k,
-                                     tcwork, tcbytes, st));
+      KSCF_CUDA_TRY(launch_rotate_tc((const float*)Xr, ld, Q64, k, nr, k, k, near_identity, (float*)Xr, ld, tcwork,
+                                     tcbytes, st));
     } else {
       KSCF_CUDA_TRY(launch_rotate_native(Xr, ld, Qm, k, nr, k, k, dtype, panel, k, st));
+      KSCF_CUDA_TRY(launch_copy_cols(panel, k, Xr, ld, nr, k, dtype, st));
     }
-    KSCF_CUDA_TRY(launch_copy_cols(panel, k, Xr, ld, nr, k, dtype, st));
   }
   return KSCF_OK;
 }
 
+// symmetric_result: A^T B is known to be symmetric (m == n), so the tensor path computes
+// the upper-triangle tiles only and mirrors them.
 int gram(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t rows, int m, int n, int dtype, int mode,
-         double scale, double* C, int64_t ldc, void* tcwork, size_t tcbytes, cudaStream_t st) {
+         double scale, double* C, int64_t ldc, void* tcwork, size_t tcbytes, cudaStream_t st,
+         bool symmetric_result = false) {
   if (mode == KSCF_GEMM_TENSOR) {
     KSCF_CUDA_TRY(launch_gram_tc((const float*)A, lda, (const float*)B, ldb, rows, m, n, scale, C, ldc, false,
-                                 tcwork, tcbytes, st));
+                                 tcwork, tcbytes, st, symmetric_result && m == n));
   } else {
     KSCF_CUDA_TRY(launch_gram_native(A, lda, B, ldb, rows, m, n, dtype, scale, C, ldc, false, st));
   }
@@ -489,8 +494,8 @@ extern "C" int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int 
     KSCF_CUDA_TRY(launch_kb_gather(H, Xb, ld, wb, dtype, coef, wpad, st));
     KSCF_CUDA_TRY(launch_cheb_step(H, Xb, ld, nullptr, 0, hxb, wpad, wb,
                                    (int)std::min<int64_t>(ld - c0, wpad), dtype, 1.0, 0.0, 0.0, coef, wpad, st));
-    // Hs[:, c0:c0+wb] = h^3 X^T (H X_b)
-    rc = gram(X, ld, hxb, wpad, rows, k, wb, dtype, mode, h3, Hs + (size_t)c0 * k, k, tcw, p.tc, st);
+    // Hs[:, c0:c0+wb] = h^3 X^T (H X_b); with a single block the product is symmetric (H is)
+    rc = gram(X, ld, hxb, wpad, rows, k, wb, dtype, mode, h3, Hs + (size_t)c0 * k, k, tcw, p.tc, st, wb == k);
     if (rc) return rc;
   }
   KSCF_CUDA_TRY(launch_symmetrize(Hs, k, k, st));

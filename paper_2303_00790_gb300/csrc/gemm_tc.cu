@@ -141,6 +141,8 @@ struct TcArgs {
   float* out;
   int64_t ldo;
   int64_t rows;                    // valid rows of out
+  const float* addsrc;             // if non-null: out = A Q + addsrc (same shape as out)
+  int64_t ldadd;
 };
 
 // products (A piece, B piece) kept: orders 2^0, 2^-8 (two), 2^-16 (three)
@@ -273,10 +275,20 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(TcArgs p) {
         const int jj = lane & 15, rh = lane >> 4;
         const int j = nt * TN + c0 + jj;
         if (j < p.n) {
-#pragma unroll 8
-          for (int r = 0; r < 32; r += 2) {
-            const int64_t ir = (int64_t)mt * TM + q * 32 + r + rh;
-            if (ir < p.rows) p.out[ir * p.ldo + j] = tr[(r + rh) * 17 + jj];
+          const int64_t ir0 = (int64_t)mt * TM + q * 32 + rh;
+          float add[16];
+          // the sixteen addends are loaded before any store (out may alias addsrc; each
+          // element is read and written by this lane only), so their latencies overlap
+#pragma unroll
+          for (int r = 0; r < 16; r++)
+            add[r] = (p.addsrc && ir0 + 2 * r < p.rows) ? p.addsrc[(ir0 + 2 * r) * p.ldadd + j] : 0.0f;
+#pragma unroll
+          for (int r = 0; r < 16; r++) {
+            const int64_t ir = ir0 + 2 * r;
+            if (ir < p.rows) {
+              const float v = tr[(2 * r + rh) * 17 + jj];
+              p.out[ir * p.ldo + j] = p.addsrc ? v + add[r] : v;
+            }
           }
         }
         __syncwarp();
@@ -580,16 +592,6 @@ __global__ void __launch_bounds__(256) split_Q_kernel(const double* __restrict__
   }
 }
 
-// out[r][j] += A[r][j]
-__global__ void add_rows_kernel(const float* __restrict__ A, int64_t lda, float* __restrict__ out, int64_t ldo,
-                                int64_t rows, int n) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= rows * n) return;
-  const int64_t r = idx / n;
-  const int j = (int)(idx - r * n);
-  out[r * ldo + j] += A[r * lda + j];
-}
-
 __global__ void mirror_upper_kernel(double* C, int k, int64_t ldc) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)k * k) return;
@@ -659,7 +661,7 @@ size_t rotate_tc_work_bytes(int64_t rows, int kin, int kout) {
 
 cudaError_t launch_gram_tc(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t rows, int m, int n,
                            double scale, double* C, int64_t ldc, bool accumulate, void* work, size_t work_bytes,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool symmetric_result) {
   const int64_t chunk = gram_chunk_for_work(rows, m, n, work_bytes);
   if (chunk < TK && rows > 0) return cudaErrorInvalidValue;
   cudaError_t e = prepare_kernel();
@@ -668,7 +670,10 @@ cudaError_t launch_gram_tc(const float* A, int64_t lda, const float* B, int64_t 
     zero_f64_kernel<<<cdiv((int64_t)m * n, 256), 256, 0, st>>>(C, m, n, ldc), count_launch();
   }
   if (rows == 0 || m == 0 || n == 0) return cudaGetLastError();
-  const bool sym = (A == B && lda == ldb && m == n);
+  // same operand: one set of split pieces; symmetric result (same operand, or a product
+  // the caller knows to be symmetric): upper-triangle tiles only, mirrored at the end
+  const bool same = (A == B && lda == ldb && m == n);
+  const bool sym = same || (symmetric_result && m == n && !accumulate);
   char* w = (char*)work;
   __nv_bfloat16* Ap[NPIECE];
   __nv_bfloat16* Bp[NPIECE];
@@ -683,7 +688,7 @@ cudaError_t launch_gram_tc(const float* A, int64_t lda, const float* B, int64_t 
   GramArgs a = {};
   for (int q = 0; q < NPIECE; q++) {
     a.A[q] = Ap[q];
-    a.B[q] = sym ? Ap[q] : Bp[q];
+    a.B[q] = same ? Ap[q] : Bp[q];
   }
   a.m_tiles = cdiv(m, TM);
   a.n_tiles = cdiv(n, GN);
@@ -700,7 +705,7 @@ cudaError_t launch_gram_tc(const float* A, int64_t lda, const float* B, int64_t 
     split_T_kernel<<<dim3(nkb, cdiv(pad_to(m, TN), 128)), 256, 0, st>>>(A, lda, r0, nr, 0, m, nkb, Ap[0], Ap[1],
                                                                          Ap[2]),
         count_launch();
-    if (!sym)
+    if (!same)
       split_T_kernel<<<dim3(nkb, cdiv(pad_to(n, TN), 128)), 256, 0, st>>>(B, ldb, r0, nr, 0, n, nkb, Bp[0], Bp[1],
                                                                            Bp[2]),
           count_launch();
@@ -777,6 +782,10 @@ cudaError_t launch_rotate_tc(const float* A, int64_t lda, const double* Q, int64
   a.out = out;
   a.ldo = ldo;
   a.rows = rows;
+  // out = A (Q - I) + A: the epilogue adds A's own element, so out may alias A (the
+  // product reads only the bf16 pieces, which are complete before the kernel starts)
+  a.addsrc = add_identity_input ? A : nullptr;
+  a.ldadd = lda;
   int sms = 152;
   {
     int dev = 0;
@@ -784,10 +793,6 @@ cudaError_t launch_rotate_tc(const float* A, int64_t lda, const double* Q, int64
   }
   const int ntiles = a.m_tiles * a.n_tiles;
   tc_gemm_kernel<<<std::min(ntiles, sms), 192, SMEM_BYTES, st>>>(a), count_launch();
-  if (add_identity_input) {
-    // out = A (Q - I) + A
-    add_rows_kernel<<<cdiv(rows * (int64_t)kout, 256), 256, 0, st>>>(A, lda, out, ldo, rows, kout), count_launch();
-  }
   return cudaGetLastError();
 }
 
