@@ -256,7 +256,9 @@ int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int k, int dtyp
                        double* eigvals_host, void* work, size_t work_bytes, void* stream);
 
 /* rho[s] = sum_{i < n_occ} f_i X[s][i]^2 in FP64 (electron density of the occupied
- * states; the density evolves together with the subspace, CheFSI paragraph).
+ * states; the density evolves together with the subspace, CheFSI paragraph).  For F32 X
+ * the sums run in double-float arithmetic (pairs of FP32 numbers; relative error ~1e-14)
+ * and only the result is converted to FP64.
  * occ: device array of n_occ occupations, or NULL for f_i = 2 (spin-degenerate).
  * rho: device, n_slots doubles. */
 int kscf_density(const kscf_ham* ham, const void* X, int64_t ld, int n_occ, int dtype,

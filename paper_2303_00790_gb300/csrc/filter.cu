@@ -791,28 +791,29 @@ __global__ void __launch_bounds__(256) kb_gather_kernel(const T* __restrict__ Y,
   }
 }
 
+// one warp per row: coalesced 128-byte stores, no per-element division
 template <typename T>
 __global__ void zero_rows_kernel(T* X, int64_t ld, int k, const int64_t* pad, int64_t n_pad) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n_pad * k) return;
-  const int64_t r = idx / k;
-  X[pad[r] * ld + (idx - r * k)] = T(0);
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= n_pad) return;
+  T* row = X + pad[r] * ld;
+  for (int j = threadIdx.x & 31; j < k; j += 32) row[j] = T(0);
 }
 
 template <typename T>
 __global__ void copy_cols_kernel(const T* src, int64_t ld_src, T* dst, int64_t ld_dst, int64_t rows, int w) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= rows * w) return;
-  const int64_t r = idx / w;
-  const int j = (int)(idx - r * w);
-  dst[r * ld_dst + j] = src[r * ld_src + j];
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= rows) return;
+  const T* s = src + r * ld_src;
+  T* d = dst + r * ld_dst;
+  for (int j = threadIdx.x & 31; j < w; j += 32) d[j] = s[j];
 }
 
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 cudaError_t launch_zero_rows(const Ham& H, void* X, int64_t ld, int k, int dtype, cudaStream_t st) {
   if (H.n_pad == 0 || k == 0) return cudaSuccess;
-  const int64_t n = H.n_pad * k;
+  const int64_t n = H.n_pad * 32;
   if (dtype == KSCF_F64)
     zero_rows_kernel<double><<<blocks_for(n, 256), 256, 0, st>>>((double*)X, ld, k, H.d_pad, H.n_pad), count_launch();
   else
@@ -970,8 +971,8 @@ cudaError_t launch_cheb_step(const Ham& H, const void* in, int64_t ld_in, const 
 
 cudaError_t launch_copy_cols(const void* src, int64_t ld_src, void* dst, int64_t ld_dst, int64_t rows, int w,
                              int dtype, cudaStream_t st) {
-  const int64_t n = rows * w;
-  if (n == 0) return cudaSuccess;
+  if (rows == 0 || w == 0) return cudaSuccess;
+  const int64_t n = rows * 32;
   if (dtype == KSCF_F64)
     copy_cols_kernel<double><<<blocks_for(n, 256), 256, 0, st>>>((const double*)src, ld_src, (double*)dst,
                                                                  ld_dst, rows, w), count_launch();

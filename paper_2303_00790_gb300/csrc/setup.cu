@@ -2,6 +2,8 @@
 // reductions.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cfloat>
 
 #include "kscf_internal.h"
@@ -176,13 +178,76 @@ __global__ void density_kernel(const T* X, int64_t ld, int n_occ, const double* 
   if (lane == 0) rho[s] = acc;
 }
 
+// FP32 X: the same sum in double-float arithmetic (pairs of FP32 numbers, Dekker 1971),
+// so that the FP64 pipe (about 1/70 of the FP32 rate on this part) only converts the final
+// pair.  x^2 = p + e exactly (TwoProduct with an FMA); f = fh + fl (the FP64 occupation as
+// an FP32 pair); each term fh p is split exactly, the small parts (fh e, fl p and the
+// product error) are summed in FP32, the leading parts with Knuth's TwoSum.  Relative
+// error about 2^-44 per slot, against ~2^-53 for plain FP64 sums.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__global__ void __launch_bounds__(256) density_f32_kernel(const float* __restrict__ X, int64_t ld, int n_occ,
+                                                          const double* __restrict__ occ, int64_t n_slots,
+                                                          double* __restrict__ rho) {
+  extern __shared__ float fpair[];   // [n_occ] high parts, then [n_occ] low parts
+  for (int i = threadIdx.x; i < n_occ; i += blockDim.x) {
+    const double f = occ ? occ[i] : 2.0;
+    const float fh = (float)f;
+    fpair[i] = fh;
+    fpair[n_occ + i] = (float)(f - (double)fh);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < n_slots; s += nw) {
+    const float* row = X + s * ld;
+    float sh = 0.0f, sl = 0.0f;
+    for (int i = lane; i < n_occ; i += 32) {
+      const float x = row[i];
+      const float p = x * x, pe = fmaf(x, x, -p);          // x^2 = p + pe
+      const float fh = fpair[i], fl = fpair[n_occ + i];
+      const float q = fh * p, qe = fmaf(fh, p, -q);         // fh p = q + qe
+      float t, te;
+      two_sum(sh, q, t, te);
+      sh = t;
+      sl += te + (qe + fmaf(fh, pe, fl * p));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
+      float t, te;
+      two_sum(sh, oh, t, te);
+      sh = t;
+      sl += te + ol;
+    }
+    if (lane == 0) rho[s] = (double)sh + (double)sl;
+  }
+}
+
 cudaError_t launch_density(const Ham& H, const void* X, int64_t ld, int n_occ, int dtype, const double* occ,
                            double* rho, cudaStream_t st) {
   const int64_t n = H.grid.n_slots;
-  if (dtype == KSCF_F64)
+  if (dtype == KSCF_F64) {
     density_kernel<double><<<blocks_for(n, 8), 256, 0, st>>>((const double*)X, ld, n_occ, occ, n, rho), count_launch();
-  else
-    density_kernel<float><<<blocks_for(n, 8), 256, 0, st>>>((const float*)X, ld, n_occ, occ, n, rho), count_launch();
+  } else {
+    // a few blocks per SM, each converting the occupations once
+    const unsigned grid = (unsigned)std::min<int64_t>(blocks_for(n, 8), 152 * 8);
+    const size_t smem = 2 * sizeof(float) * (size_t)std::max(n_occ, 1);
+    if (smem > 48 * 1024) {
+      static size_t attr = 0;
+      if (smem > attr) {
+        cudaError_t e = cudaFuncSetAttribute(density_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+      }
+    }
+    density_f32_kernel<<<grid, 256, smem, st>>>((const float*)X, ld, n_occ, occ, n, rho), count_launch();
+  }
   return cudaGetLastError();
 }
 
