@@ -283,7 +283,9 @@ int kscf_random_subspace(const kscf_ham* ham, void* X, int64_t ld, int k, int dt
  * kscf_rotate: out[r*ldo + j] = sum_{i < kin} A[r*lda + i] * Q'[i + j*ldq]  (r < rows,
  *   j < kout) with Q' = Q - I when minus_identity (then out += A, i.e. out = A Q
  *   evaluated as A + A (Q - I); tensor mode, kin == kout).  Q is FP64 column-major;
- *   the native mode needs ldq == kin.  out must not overlap A.
+ *   the native mode needs ldq == kin.  In tensor mode out may be A itself (the product
+ *   reads bf16 copies of A; minus_identity adds A's own element in the epilogue); in the
+ *   native mode out must not overlap A.
  * Work buffers: kscf_gemm_workspace_size(op = 0 gram / 1 rotate, rows, m|kin, n|kout,
  * dtype, mode, &bytes). */
 int kscf_gram(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t rows, int m, int n, int dtype,
@@ -299,6 +301,15 @@ int kscf_gemm_workspace_size(int op, int64_t rows, int m, int n, int dtype, int 
  * GEMMs, freed its tensor memory), else KSCF_OK.  Synchronising.  orthonormalize and
  * rayleigh_ritz check the GEMM word themselves; filter callers check after the filter. */
 int kscf_check_status(void);
+
+/* Self-test of the bounded grid barriers of the FP64 Cholesky kernel (orthonormalize):
+ * runs it on a 64 x 64 identity with a wait limit of 2e6 clock cycles (~1 ms) while one of
+ * its two CTAs returns before the first barrier, so that the other CTA's wait runs out.
+ * Returns KSCF_ERR_TIMEOUT when that wait gave up and the kernel returned with its timeout
+ * word set (the expected outcome; the context stays usable), KSCF_OK if the kernel finished
+ * without noticing, or another error code.  Allocates and frees ~70 KB of device memory;
+ * synchronising. */
+int kscf_selftest_barrier_timeout(void* stream);
 
 /* ---------------------------------------------------------------------------------
  * Self-consistent field (Computational details: Kohn-Sham DFT with the LDA,

@@ -612,6 +612,34 @@ extern "C" int kscf_gemm_workspace_size(int op, int64_t rows, int m, int n, int 
   return KSCF_OK;
 }
 
+extern "C" int kscf_selftest_barrier_timeout(void* stream) {
+  const int k = 64;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t sbytes = (size_t)k * k * 8, wbytes = chol_inv_work_bytes(k);
+  char* buf = nullptr;
+  KSCF_CUDA_TRY(cudaMalloc(&buf, kscf_align256(sbytes) + 256 + wbytes));
+  double* S = (double*)buf;
+  int* status = (int*)(buf + kscf_align256(sbytes));
+  void* work = buf + kscf_align256(sbytes) + 256;
+  std::vector<double> eye((size_t)k * k, 0.0);
+  for (int i = 0; i < k; i++) eye[(size_t)i * k + i] = 1.0;
+  int hst[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(S, eye.data(), sbytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_chol_inv(S, k, k, 0.0, S, k, work, status, st, 2000000LL, 1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hst, status, sizeof(hst), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (e != cudaSuccess) {
+    set_error("kscf_selftest_barrier_timeout: %s", cudaGetErrorString(e));
+    return KSCF_ERR_CUDA;
+  }
+  if (hst[1] != 0) {
+    set_error("kscf_selftest_barrier_timeout: the bounded grid barrier gave up as expected");
+    return KSCF_ERR_TIMEOUT;
+  }
+  return KSCF_OK;
+}
+
 extern "C" int kscf_check_status(void) {
   unsigned int st = 0, fs = 0;
   cudaError_t e = tc_status(true, &st);

@@ -47,6 +47,7 @@ struct CholArgs {
   int* status;    // [0] first failed pivot (1-based column) or 0, [1] barrier timeout
   double floor_rel;
   long long spin_limit;
+  int leave_cta;  // self-test only: this CTA returns before its first barrier (-1: none)
 };
 
 __device__ __forceinline__ double ld(const double* p) { return __ldcg(p); }
@@ -55,6 +56,7 @@ __device__ __forceinline__ double ld(const double* p) { return __ldcg(p); }
 // reported that it did).
 __device__ bool grid_sync(const CholArgs& a) {
   __shared__ int s_ok;
+  if ((int)blockIdx.x == a.leave_cta) return false;
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* gen = a.bar + 1;
@@ -333,7 +335,7 @@ size_t chol_inv_work_bytes(int k) {
 }
 
 cudaError_t launch_chol_inv(const double* S, int64_t lds, int k, double floor_rel, double* out, int64_t ldo,
-                            void* work, int* status, cudaStream_t st) {
+                            void* work, int* status, cudaStream_t st, long long spin_limit, int leave_cta) {
   CholArgs a;
   a.S = S;
   a.lds = lds;
@@ -350,7 +352,8 @@ cudaError_t launch_chol_inv(const double* S, int64_t lds, int k, double floor_re
   a.ldo = ldo;
   a.status = status;
   a.floor_rel = floor_rel;
-  a.spin_limit = 2000000000LL;
+  a.spin_limit = spin_limit;
+  a.leave_cta = leave_cta;
   cudaError_t e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(status, 0, 2 * sizeof(int), st);

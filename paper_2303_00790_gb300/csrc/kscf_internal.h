@@ -128,10 +128,13 @@ cudaError_t launch_upper_to_dtype(const double* R, int k, int dtype, void* out, 
 // S (k x k column-major, upper triangle read) = R^T R; out (may alias S) = R^-1, upper
 // triangular with zeros below.  status (2 device ints, zeroed here): [0] = 1-based column
 // of the first pivot not above S_cc max((c + 8) 2^-53, floor_rel) (out then unwritten),
-// [1] = 1 if a bounded grid barrier gave up.  work: chol_inv_work_bytes(k), 256-aligned.
+// [1] = 1 if a bounded grid barrier gave up (each wait gives up after spin_limit clock
+// cycles, ~1 s by default).  work: chol_inv_work_bytes(k), 256-aligned.  leave_cta >= 0
+// (self-test only) makes that CTA return before its first barrier.
 size_t chol_inv_work_bytes(int k);
 cudaError_t launch_chol_inv(const double* S, int64_t lds, int k, double floor_rel, double* out, int64_t ldo,
-                            void* work, int* status, cudaStream_t st);
+                            void* work, int* status, cudaStream_t st, long long spin_limit = 2000000000LL,
+                            int leave_cta = -1);
 cudaError_t launch_f64_to_dtype(const double* src, int64_t n, int dtype, void* out, cudaStream_t st);
 
 }  // namespace kscf

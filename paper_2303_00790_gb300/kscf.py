@@ -113,6 +113,7 @@ _sigs = {
     "kscf_rotate": ([_vp, _i64, _vp, _i64, _i64, _i32, _i32, _i32, _i32, _i32, _vp, _i64, _vp, _sz, _vp], _i32),
     "kscf_gemm_workspace_size": ([_i32, _i64, _i32, _i32, _i32, _i32, C.POINTER(_sz)], _i32),
     "kscf_check_status": ([], _i32),
+    "kscf_selftest_barrier_timeout": ([_vp], _i32),
     "kscf_scf_create": ([_vp, C.POINTER(kscf_atom), _i32, C.POINTER(kscf_species), _i32, C.POINTER(_d),
                          C.POINTER(kscf_scf_params), _vp, _i64, _vp, C.POINTER(_vp)], _i32),
     "kscf_scf_start": ([_vp, _vp, _i32, C.c_uint64, C.POINTER(_d)], _i32),
@@ -423,6 +424,11 @@ def kscf_rotate(A, Q, mode: int = KSCF_GEMM_NATIVE, minus_identity: bool = False
 
 def kscf_check_status():
     _check(lib.kscf_check_status())
+
+
+def kscf_selftest_barrier_timeout(stream=None):
+    """Raises KscfError(KSCF_ERR_TIMEOUT) when the bounded grid barrier works (see kscf.h)."""
+    _check(lib.kscf_selftest_barrier_timeout(_stream(stream)))
 
 
 def kscf_launch_counter() -> int:

@@ -318,6 +318,21 @@ def test_f32_brick_kernel_paths(kscf, system, k, ldpad, block):
     assert np.all(np.max(np.abs(got - ref), axis=0) <= 1e-4 * colmax)
 
 
+def test_bounded_barrier_times_out_and_context_survives(kscf, species):
+    # one CTA of the FP64 Cholesky kernel leaves before the first grid barrier; the other's
+    # wait (limit ~1 ms) must give up, report the timeout and leave the context usable
+    with pytest.raises(kscf.KscfError) as e:
+        kscf.kscf_selftest_barrier_timeout()
+    assert e.value.code == kscf.KSCF_ERR_TIMEOUT
+    pos, z = small_cluster()
+    g, H = kscf.build_cluster(pos, z, species, 8.0, 0.7)
+    X = torch.zeros((g.info["n_slots"], 40), dtype=torch.float64, device="cuda")
+    kscf.kscf_random_subspace(H, X, seed=8)
+    kscf.kscf_orthonormalize(H, X)
+    G = kscf.kscf_gram(X, X, scale=H.h3).cpu().numpy()
+    assert np.max(np.abs(G - np.eye(40))) < 1e-12
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_orthonormalize_recovers_from_rank_deficiency(kscf, species, mode):
     # two columns equal up to a 1e-6 perturbation: in FP32 the Gram matrix is singular to
