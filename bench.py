@@ -59,6 +59,9 @@ def parse():
     p.add_argument("--learned-full", action="store_true",
                    help="learned start with training clusters of 1-3 nm and a held-out 3 nm cluster (prints its own "
                         "JSON line; several minutes)")
+    p.add_argument("--filter-sweep", action="store_true",
+                   help="filter throughput and roofline fraction over brick size (8, 16) and column block width "
+                        "(32, 64, 128) on the first 1024 columns of --workload (default si3325h876)")
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-start comparison (train on 30 clusters, SCF on a held-out one)")
     return p.parse_args()
@@ -563,10 +566,59 @@ def alu_peaks():
     print(subprocess.run([exe], check=True, capture_output=True, text=True).stdout, end="")
 
 
+def run_filter_sweep(args):
+    """Filter-only sweep: Gpoint*vec/s and the algorithmic-bytes roofline fraction (12 B per
+    point*vector*degree step, as in the main line) for brick sizes 8 and 16 and column block
+    widths 32, 64 and 128, on a 1024-column sample of the workload's block (the column
+    blocks are independent, so the rate of a sample is the rate of the whole block)."""
+    import torch
+    from paper_2303_00790_gb300 import kscf
+    from workloads import pseudo_params, workload
+    name = args.workload if args.workload != "si353h196" else "si3325h876"
+    w = workload(name)
+    pos, z = w.atoms()
+    species = pseudo_params()
+    cols, m = min(w.k, 1024), w.degree
+    peak, peak_src = load_peaks()
+    results = []
+    for brick in (8, 16):
+        grid, H = kscf.build_cluster(pos, z, species, w.radius, w.h, brick=brick)
+        n_points, n_slots = grid.info["n_points"], grid.info["n_slots"]
+        X = torch.zeros((n_slots, cols), dtype=torch.float32, device="cuda")
+        kscf.kscf_random_subspace(H, X, seed=1)
+        lo, hi = kscf.kscf_spectral_bounds(H)
+        a0, a = lo, lo + 0.25 * (hi - lo)     # any a0 < a < b: the work does not depend on them
+        for block in (32, 64, 128):
+            wf = torch.empty(kscf.kscf_workspace_size(H, kscf.KSCF_OP_FILTER, cols, kscf.KSCF_F32, 0, block),
+                             dtype=torch.uint8, device="cuda")
+            kscf.kscf_chebyshev_filter(H, X, m, a, hi, a0, block=block, work=wf)
+            kscf.kscf_random_subspace(H, X, seed=1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 2
+            e0.record()
+            for _ in range(reps):
+                kscf.kscf_chebyshev_filter(H, X, m, a, hi, a0, block=block, work=wf)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gbs = 12.0 * n_points * cols * m / (ms * 1e-3) / 1e9
+            results.append({"brick": brick, "block": block, "ms": ms,
+                            "gpvs": n_points * cols * m / (ms * 1e-3) / 1e9, "gbs": gbs, "frac": gbs / peak})
+            del wf
+        del X, H, grid
+        torch.cuda.empty_cache()
+    print(json.dumps({"filter_sweep": {"workload": name, "n_points": n_points, "columns": cols, "degree": m,
+                                       "peak_gbs": peak, "peak_source": peak_src, "results": results}}), flush=True)
+
+
 def main():
     args = parse()
     if args.alu_peaks:
         alu_peaks()
+        return
+    if args.filter_sweep:
+        run_filter_sweep(args)
         return
     if args.gap_study:
         run_gap_study(args)
