@@ -466,16 +466,21 @@ def run_kscf(args):
         except Exception:
             traffic = None
 
-    # end-to-end through the C ABI from pinned host buffers: every step copies its input
-    # block in and its result block out; the copies run on a second stream into and out of
-    # a second device buffer, so that step i's compute overlaps step i-1's read-out and
-    # step i+1's upload (the first upload and the last read-outs are inside the timed region)
+    # end-to-end through the C ABI from pinned host buffers: the user's block has one row per
+    # grid point (lexicographic order, k columns); every step uploads its input block,
+    # converts it to the slot layout on the device (kscf_points_to_slots), runs the step,
+    # converts back (kscf_slots_to_points) and reads the result out.  The copies run on a
+    # second stream with double-buffered device blocks, so that step i's compute overlaps
+    # step i-1's read-out and step i+1's upload (the first upload and the last read-out are
+    # inside the timed region)
     e2e = None
     if not args.no_e2e:
-        Xh = torch.empty((n_slots, kpad), dtype=dt, pin_memory=True)
-        Xh.copy_(Xfull)
-        outh = torch.empty((n_slots, kpad), dtype=dt, pin_memory=True)
-        Xb = [Xfull, torch.zeros_like(Xfull)]
+        Pin = [torch.empty((n_points, k), dtype=dt, device="cuda") for _ in range(2)]
+        Pout = [torch.empty((n_points, k), dtype=dt, device="cuda") for _ in range(2)]
+        kscf.kscf_slots_to_points(H, X, Pin[0])
+        Xh = torch.empty((n_points, k), dtype=dt, pin_memory=True)
+        Xh.copy_(Pin[0])
+        outh = torch.empty((n_points, k), dtype=dt, pin_memory=True)
         cstream = torch.cuda.Stream()
         ev_copy = [torch.cuda.Event(), torch.cuda.Event()]
         ev_comp = [torch.cuda.Event(), torch.cuda.Event()]
@@ -486,27 +491,29 @@ def run_kscf(args):
         nE = max(1, min(args.steps, 5))
         s0.record(cstream)
         with torch.cuda.stream(cstream):
-            Xb[0].copy_(Xh, non_blocking=True)
+            Pin[0].copy_(Xh, non_blocking=True)
         ev_copy[0].record(cstream)
         for i in range(nE):
             cur, nxt = i % 2, (i + 1) % 2
             with torch.cuda.stream(cstream):
                 if i >= 1:
                     cstream.wait_event(ev_comp[nxt])
-                    outh.copy_(Xb[nxt], non_blocking=True)          # result of step i-1
+                    outh.copy_(Pout[nxt], non_blocking=True)        # result of step i-1
                 if i + 1 < nE:
-                    Xb[nxt].copy_(Xh, non_blocking=True)            # input of step i+1
+                    Pin[nxt].copy_(Xh, non_blocking=True)           # input of step i+1
                     ev_copy[nxt].record(cstream)
             stream.wait_event(ev_copy[cur])
-            step(False, Xb[cur][:, :k])
+            kscf.kscf_points_to_slots(H, Pin[cur], X)
+            step(False)
+            kscf.kscf_slots_to_points(H, X, Pout[cur])
             ev_comp[cur].record(stream)
         cstream.wait_event(ev_comp[(nE - 1) % 2])
         with torch.cuda.stream(cstream):
-            outh.copy_(Xb[(nE - 1) % 2], non_blocking=True)         # result of the last step
+            outh.copy_(Pout[(nE - 1) % 2], non_blocking=True)       # result of the last step
         s1.record(cstream)
         torch.cuda.synchronize()
         e_ms = max_over_ranks(s0.elapsed_time(s1) / nE, world)
-        del Xb[1]
+        del Pin, Pout
         e2e = {"value": world * units / (e_ms * 1e-3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size()),
                "d2h_bytes_per_step": int(outh.numel() * outh.element_size() + 8 * k)}

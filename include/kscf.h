@@ -255,6 +255,18 @@ int kscf_orthonormalize(const kscf_ham* ham, void* X, int64_t ld, int k, int dty
 int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int k, int dtype, int mode,
                        double* eigvals_host, void* work, size_t work_bytes, void* stream);
 
+/* Layout conversion between a compact point-major block P (n_points rows of k values,
+ * row p = the grid point with lexicographic index p, as kscf_grid_slots reports it, row
+ * stride ldp >= k) and the slot layout X (n_slots rows, stride ldx >= k) that every call
+ * above works on.  points_to_slots writes all n_slots rows of X (padding rows zero);
+ * slots_to_points writes the n_points rows of P.  Device pointers, dtype KSCF_F64 or
+ * KSCF_F32, asynchronous on `stream`.  For moving a user's block in and out of the library
+ * with n_points instead of n_slots rows (the brick padding is ~30 % of the slots). */
+int kscf_points_to_slots(const kscf_ham* ham, const void* P, int64_t ldp, void* X, int64_t ldx, int k, int dtype,
+                         void* stream);
+int kscf_slots_to_points(const kscf_ham* ham, const void* X, int64_t ldx, void* P, int64_t ldp, int k, int dtype,
+                         void* stream);
+
 /* rho[s] = sum_{i < n_occ} f_i X[s][i]^2 in FP64 (electron density of the occupied
  * states; the density evolves together with the subspace, CheFSI paragraph).  For F32 X
  * the sums run in double-float arithmetic (pairs of FP32 numbers; relative error ~1e-14)

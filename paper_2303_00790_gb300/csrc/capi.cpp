@@ -535,6 +535,30 @@ extern "C" int kscf_density(const kscf_ham* ham, const void* X, int64_t ld, int 
   return KSCF_OK;
 }
 
+extern "C" int kscf_points_to_slots(const kscf_ham* ham, const void* P, int64_t ldp, void* X, int64_t ldx, int k,
+                                    int dtype, void* stream) {
+  int rc = check_common(ham, X, ldx, k, dtype, "kscf_points_to_slots");
+  if (rc) return rc;
+  if (!P || ldp < k) {
+    set_error("kscf_points_to_slots: invalid argument");
+    return KSCF_ERR_INVALID;
+  }
+  KSCF_CUDA_TRY(launch_points_slots(ham->h, true, P, ldp, X, ldx, k, dtype, (cudaStream_t)stream));
+  return KSCF_OK;
+}
+
+extern "C" int kscf_slots_to_points(const kscf_ham* ham, const void* X, int64_t ldx, void* P, int64_t ldp, int k,
+                                    int dtype, void* stream) {
+  int rc = check_common(ham, X, ldx, k, dtype, "kscf_slots_to_points");
+  if (rc) return rc;
+  if (!P || ldp < k) {
+    set_error("kscf_slots_to_points: invalid argument");
+    return KSCF_ERR_INVALID;
+  }
+  KSCF_CUDA_TRY(launch_points_slots(ham->h, false, X, ldx, P, ldp, k, dtype, (cudaStream_t)stream));
+  return KSCF_OK;
+}
+
 extern "C" int kscf_random_subspace(const kscf_ham* ham, void* X, int64_t ld, int k, int dtype, uint64_t seed,
                                     void* stream) {
   int rc = check_common(ham, X, ld, k, dtype, "kscf_random_subspace");

@@ -106,6 +106,10 @@ cudaError_t launch_vloc(const Ham& H, const double* d_xyz /*n_slots*3*/, const d
 cudaError_t launch_v_to_f32(const Ham& H, cudaStream_t st);
 cudaError_t launch_random(const Ham& H, void* X, int64_t ld, int k, int dtype, uint64_t seed,
                           cudaStream_t st);
+// to_slots: dst (slot layout) row s = src row lex(s), padding rows zero; else dst row
+// lex(s) = src row s for the live slots
+cudaError_t launch_points_slots(const Ham& H, bool to_slots, const void* src, int64_t lds, void* dst, int64_t ldd,
+                                int k, int dtype, cudaStream_t st);
 cudaError_t launch_density(const Ham& H, const void* X, int64_t ld, int n_occ, int dtype,
                            const double* occ, double* rho, cudaStream_t st);
 cudaError_t launch_minmax_v(const Ham& H, double* d_out2, cudaStream_t st);

@@ -228,6 +228,58 @@ __global__ void __launch_bounds__(256) density_f32_kernel(const float* __restric
   }
 }
 
+// Layout conversions between a compact block (one row per grid point, lexicographic point
+// order) and the slot layout; one warp per slot row.
+template <typename T>
+__global__ void points_to_slots_kernel(const T* __restrict__ P, int64_t ldp, T* __restrict__ X, int64_t ldx, int k,
+                                       const int64_t* __restrict__ lex, int64_t n_slots) {
+  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (s >= n_slots) return;
+  const int64_t p = lex[s];
+  T* x = X + s * ldx;
+  if (p < 0) {
+    for (int j = threadIdx.x & 31; j < k; j += 32) x[j] = T(0);
+  } else {
+    const T* src = P + p * ldp;
+    for (int j = threadIdx.x & 31; j < k; j += 32) x[j] = src[j];
+  }
+}
+
+template <typename T>
+__global__ void slots_to_points_kernel(const T* __restrict__ X, int64_t ldx, T* __restrict__ P, int64_t ldp, int k,
+                                       const int64_t* __restrict__ lex, int64_t n_slots) {
+  const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (s >= n_slots) return;
+  const int64_t p = lex[s];
+  if (p < 0) return;
+  const T* x = X + s * ldx;
+  T* dst = P + p * ldp;
+  for (int j = threadIdx.x & 31; j < k; j += 32) dst[j] = x[j];
+}
+
+cudaError_t launch_points_slots(const Ham& H, bool to_slots, const void* src, int64_t lds, void* dst, int64_t ldd,
+                                int k, int dtype, cudaStream_t st) {
+  const int64_t n = H.grid.n_slots;
+  if (n == 0 || k == 0) return cudaSuccess;
+  const unsigned grid = blocks_for(n * 32, 256);
+  if (dtype == KSCF_F64) {
+    if (to_slots)
+      points_to_slots_kernel<double><<<grid, 256, 0, st>>>((const double*)src, lds, (double*)dst, ldd, k, H.d_lex, n),
+          count_launch();
+    else
+      slots_to_points_kernel<double><<<grid, 256, 0, st>>>((const double*)src, lds, (double*)dst, ldd, k, H.d_lex, n),
+          count_launch();
+  } else {
+    if (to_slots)
+      points_to_slots_kernel<float><<<grid, 256, 0, st>>>((const float*)src, lds, (float*)dst, ldd, k, H.d_lex, n),
+          count_launch();
+    else
+      slots_to_points_kernel<float><<<grid, 256, 0, st>>>((const float*)src, lds, (float*)dst, ldd, k, H.d_lex, n),
+          count_launch();
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_density(const Ham& H, const void* X, int64_t ld, int n_occ, int dtype, const double* occ,
                            double* rho, cudaStream_t st) {
   const int64_t n = H.grid.n_slots;

@@ -108,6 +108,8 @@ _sigs = {
     "kscf_rayleigh_ritz": ([_vp, _vp, _i64, _i32, _i32, _i32, C.POINTER(_d), _vp, _sz, _vp], _i32),
     "kscf_density": ([_vp, _vp, _i64, _i32, _i32, _vp, _vp, _vp], _i32),
     "kscf_random_subspace": ([_vp, _vp, _i64, _i32, _i32, C.c_uint64, _vp], _i32),
+    "kscf_points_to_slots": ([_vp, _vp, _i64, _vp, _i64, _i32, _i32, _vp], _i32),
+    "kscf_slots_to_points": ([_vp, _vp, _i64, _vp, _i64, _i32, _i32, _vp], _i32),
     "kscf_hilbert_index3": ([C.c_uint32, C.c_uint32, C.c_uint32, _i32], C.c_uint64),
     "kscf_gram": ([_vp, _i64, _vp, _i64, _i64, _i32, _i32, _i32, _i32, _d, _vp, _i64, _vp, _sz, _vp], _i32),
     "kscf_rotate": ([_vp, _i64, _vp, _i64, _i64, _i32, _i32, _i32, _i32, _i32, _vp, _i64, _vp, _sz, _vp], _i32),
@@ -377,6 +379,22 @@ def kscf_random_subspace(ham: Hamiltonian, X, seed: int, k: int | None = None, s
     _check(lib.kscf_random_subspace(ham.handle, C.c_void_p(X.data_ptr()), _rows(X, k), k, _dtype_code(X),
                                     int(seed), _stream(stream)))
     return X
+
+
+def kscf_points_to_slots(ham: Hamiltonian, P, X, k: int | None = None, stream=None):
+    """X (slot layout, n_slots rows) <- P (n_points rows in lexicographic point order)."""
+    k = P.shape[1] if k is None else k
+    _check(lib.kscf_points_to_slots(ham.handle, C.c_void_p(P.data_ptr()), _rows(P, k), C.c_void_p(X.data_ptr()),
+                                    _rows(X, k), k, _dtype_code(X), _stream(stream)))
+    return X
+
+
+def kscf_slots_to_points(ham: Hamiltonian, X, P, k: int | None = None, stream=None):
+    """P (n_points rows in lexicographic point order) <- X (slot layout)."""
+    k = X.shape[1] if k is None else k
+    _check(lib.kscf_slots_to_points(ham.handle, C.c_void_p(X.data_ptr()), _rows(X, k), C.c_void_p(P.data_ptr()),
+                                    _rows(P, k), k, _dtype_code(X), _stream(stream)))
+    return P
 
 
 def kscf_gemm_workspace_size(op: int, rows: int, m: int, n: int, dtype: int, mode: int) -> int:

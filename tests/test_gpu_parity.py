@@ -176,6 +176,25 @@ def test_rayleigh_ritz_matches_oracle(kscf, system):
     assert np.max(np.abs(got * sgn - ref_X)) <= 1e-8 * np.max(np.abs(ref_X))
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_points_slots_layout_round_trip(kscf, system, dtype):
+    # a permutation with zero padding rows: bit-exact in both directions, columns >= k and
+    # rows of P beyond the grid untouched
+    k = 13
+    rng = np.random.default_rng(21)
+    P = rng.standard_normal((system["n"], k))
+    Pd = torch.tensor(P, dtype=dtype, device="cuda")
+    X = torch.full((system["g"].info["n_slots"], 16), 7.0, dtype=dtype, device="cuda")
+    kscf.kscf_points_to_slots(system["H"], Pd, X[:, :k])
+    ref = to_slots(P.astype(np.float32) if dtype == torch.float32 else P, system["lex"])
+    assert np.array_equal(X[:, :k].cpu().numpy().astype(np.float64), ref.astype(np.float64))
+    assert torch.all(X[:, k:] == 7.0)
+    back = torch.full((system["n"] + 3, 20), -1.0, dtype=dtype, device="cuda")
+    kscf.kscf_slots_to_points(system["H"], X[:, :k], back[:, :k])
+    assert torch.equal(back[:system["n"], :k], Pd)
+    assert torch.all(back[system["n"]:] == -1.0) and torch.all(back[:, k:] == -1.0)
+
+
 def test_density_matches_oracle(kscf, system):
     from oracle.chefsi import density
     from workloads import random_block_lex
