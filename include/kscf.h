@@ -248,10 +248,11 @@ int kscf_orthonormalize(const kscf_ham* ham, void* X, int64_t ld, int k, int dty
                         void* work, size_t work_bytes, void* stream);
 
 /* In place Rayleigh-Ritz (CheFSI paragraph): HX = H X, Hs = h^3 X^T (HX) symmetrised
- * (FP64 k x k), Hs = Q Lambda Q^T (FP64 symmetric eigensolver, ascending),
- * X <- X Q.  In tensor mode the eigenvector signs are chosen with diag(Q) >= 0 and the
- * rotation is applied as X + X (Q - I).  Requires h^3 X^T X = I on entry.  eigvals_host (k doubles) receives
- * Lambda; synchronous on `stream`. */
+ * (FP64 k x k; in tensor mode with HX computed in one block, only the upper-triangle
+ * tiles are computed and mirrored), Hs = Q Lambda Q^T (FP64 symmetric eigensolver,
+ * ascending), X <- X Q.  In tensor mode the eigenvector signs are chosen with
+ * diag(Q) >= 0 and the rotation is applied as X + X (Q - I).  Requires h^3 X^T X = I on
+ * entry.  eigvals_host (k doubles) receives Lambda; synchronous on `stream`. */
 int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int k, int dtype, int mode,
                        double* eigvals_host, void* work, size_t work_bytes, void* stream);
 
