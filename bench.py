@@ -50,7 +50,6 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU seconds of the oracle sample")
-    p.add_argument("--alu-peaks", action="store_true", help="build and run the FP32/FP64 FMA microbenchmark")
     p.add_argument("--no-scf", action="store_true", help="skip the SCF wall-time comparison (mixed vs FP64)")
     p.add_argument("--scf-workload", default="si353h196")
     p.add_argument("--scf-max-steps", type=int, default=80)
@@ -566,15 +565,6 @@ def run_kscf(args):
         dist.destroy_process_group()
 
 
-def alu_peaks():
-    """Compile and run csrc/alu_peaks.cu (FP32, FP32x2 and FP64 FMA throughput)."""
-    import tempfile
-    src = os.path.join(ROOT, "paper_2303_00790_gb300", "csrc", "alu_peaks.cu")
-    exe = os.path.join(tempfile.mkdtemp(), "alu_peaks")
-    subprocess.run(["nvcc", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-o", exe, src], check=True)
-    print(subprocess.run([exe], check=True, capture_output=True, text=True).stdout, end="")
-
-
 def run_filter_sweep(args):
     """Filter-only sweep: Gpoint*vec/s and the algorithmic-bytes roofline fraction (12 B per
     point*vector*degree step, as in the main line) for brick sizes 8 and 16 and column block
@@ -623,9 +613,6 @@ def run_filter_sweep(args):
 
 def main():
     args = parse()
-    if args.alu_peaks:
-        alu_peaks()
-        return
     if args.filter_sweep:
         run_filter_sweep(args)
         return

@@ -206,7 +206,9 @@ int kscf_hamiltonian_apply(const kscf_ham* ham, void* Y, int64_t ld_y, void* HY,
  *     column blocks of Y instead.
  *   - Allocates nothing and calls no allocating routine.  The first call on each
  *     device looks up the array's device address (cudaGetSymbolAddress) with that
- *     device current; make that first call before any stream capture.
+ *     device current; make that first call before any stream capture.  The address is
+ *     kept for the life of the process: do not use this entry point on a device after
+ *     cudaDeviceReset (or any reset of its primary context) in the same process.
  *   - All calls share the one array and it keeps the last call's contents; calls whose
  *     work overlaps on the GPU (different streams, or threads without ordering) race
  *     on it and give wrong results.  Serialise them (e.g. one stream).

@@ -17,6 +17,10 @@ Everything is float64 numpy/scipy.  Pins against closed forms live in tests/.
 Parity pinned: FD weights, kinetic operator (box spectrum, polynomial exactness),
 KB operator (dense assembly), filter (Chebyshev closed form), Cholesky-QR
 (orthonormality), Rayleigh-Ritz (brute-force spectra, harmonic oscillator),
-density (electron count).  Parity unpinned: the absolute eigenvalues of the
-synthetic silicon Hamiltonian (the paper prints none for any reproducible system).
+density (electron count, analytic ground state of the harmonic oscillator), SCF
+total energy (the Kohn-Sham functional evaluated directly from the orbitals), LDA,
+Poisson, mixing and occupations (scf.py), learned-start descriptors, network forward
+pass (single-path closed form), gradients and Adam (learned.py).  Parity unpinned:
+the absolute eigenvalues of the synthetic silicon Hamiltonian (the paper prints none
+for any reproducible system).
 """

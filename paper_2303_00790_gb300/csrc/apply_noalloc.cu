@@ -80,8 +80,10 @@ extern "C" int kscf_hamiltonian_apply_noalloc(const kscf_ham* ham, void* Y, int6
   int rc = scratch_address(&coef);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  // every coefficient the step kernel reads is written by the gather first, so the
-  // array needs no clearing between calls
+  // The gather writes the coefficients of vectors v < k.  The brick kernels read whole
+  // vector chunks, so lanes v >= k may read values a previous call left in the array;
+  // those lanes are never stored (every output write is masked to v < k), which is why
+  // the array needs no clearing between calls.
   KSCF_CUDA_TRY(kscf::launch_zero_rows(H, Y, ld_y, k, dtype, st));
   KSCF_CUDA_TRY(kscf::launch_zero_rows(H, HY, ld_hy, k, dtype, st));
   KSCF_CUDA_TRY(kscf::launch_kb_gather(H, Y, ld_y, k, dtype, coef, kscf::coef_ld(k), st));

@@ -29,6 +29,7 @@ KSCF_F64, KSCF_F32 = 0, 1
 KSCF_GEMM_NATIVE, KSCF_GEMM_TENSOR = 0, 1
 KSCF_OP_APPLY, KSCF_OP_FILTER, KSCF_OP_ORTHO, KSCF_OP_RR = 0, 1, 2, 3
 KSCF_ORTHO_ALLOW_SHIFT = 0x100
+KSCF_NOALLOC_SCRATCH_BYTES = 4 << 20     # size of the fixed array of kscf_hamiltonian_apply_noalloc
 
 
 class KscfError(RuntimeError):

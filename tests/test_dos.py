@@ -1,5 +1,5 @@
 """DOS and gap: oracle pins (closed forms) and the library's host function against the
-oracle (bin counts exact)."""
+oracle (bin counts exact), on host values and on Ritz values computed on the GPU."""
 import numpy as np
 import pytest
 
@@ -29,3 +29,41 @@ def test_library_dos_matches_oracle():
         assert np.allclose(h, hr, rtol=1e-14, atol=0)
         assert np.allclose(edges, er)
         assert (np.isnan(gap) and np.isnan(gr)) or abs(gap - gr) < 1e-12
+
+
+@pytest.mark.gpu
+def test_dos_of_gpu_ritz_values_matches_oracle(species):
+    """Ritz values produced on the GPU (three CheFSI iterations on Si2H2, FP64) go through
+    kscf_dos; its histogram and gap equal the oracle's on the same values (counts exact),
+    and the values themselves match the oracle's CheFSI from the same X0 (1e-10)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_00790_gb300.build import build
+    build()
+    from paper_2303_00790_gb300 import kscf
+    from helpers import small_cluster, to_slots
+    from oracle.chefsi import chefsi
+    from oracle.system import cluster_hamiltonian
+    from workloads import random_block_lex
+    pos, z = small_cluster()
+    g, H = kscf.build_cluster(pos, z, species, 9.0, 0.7)
+    lex, _ = g.slots()
+    n, k, m, n_occ = g.info["n_points"], 24, 10, 5
+    X0 = random_block_lex(3, n, k)
+    X = torch.tensor(to_slots(X0, lex), device="cuda")
+    _, b = kscf.kscf_spectral_bounds(H)
+    kscf.kscf_orthonormalize(H, X)
+    lam = kscf.kscf_rayleigh_ritz(H, X)
+    for _ in range(3):
+        kscf.kscf_chebyshev_filter(H, X, m, lam[-1], b, lam[0])
+        kscf.kscf_orthonormalize(H, X)
+        lam = kscf.kscf_rayleigh_ritz(H, X)
+    ref = chefsi(cluster_hamiltonian(pos, z, species, 9.0, 0.7), X0, m, 3, b=b)["lam"]
+    assert np.max(np.abs(lam - ref)) < 1e-10 * np.max(np.abs(ref))
+    for bin_ev, lo, nb in ((0.1, -15.0, 200), (0.25, -30.0, 160)):
+        h, edges, gap = kscf.kscf_dos(lam, n_occ, bin_ev, lo, nb)
+        hr, er, gr = dos(lam, n_occ, bin_ev, lo, nb)
+        assert np.array_equal(np.rint(h * n_occ * bin_ev), np.rint(hr * n_occ * bin_ev))
+        assert np.allclose(h, hr, rtol=1e-14, atol=0) and np.allclose(edges, er)
+        assert abs(gap - gr) < 1e-12 and gap > 0

@@ -1,7 +1,8 @@
 """Pins of the oracle's CheFSI steps: the filter against the Chebyshev closed form,
 Cholesky-QR against orthonormality and a library QR, converged Rayleigh-Ritz against
 the box-Laplacian closed-form spectrum, the harmonic oscillator, a brute-force dense
-eigensolve, and the density against the electron count."""
+eigensolve, and the density against the electron count and the analytic ground state of
+the harmonic oscillator."""
 import math
 
 import numpy as np
@@ -78,17 +79,35 @@ def test_box_laplacian_chefsi_matches_closed_form():
     assert np.max(np.abs(r["lam"][:nwant] - allv[:nwant])) < 1e-9
 
 
-def test_harmonic_oscillator():
-    # V = omega^2 r^2 / 2: levels omega (n + 3/2) with degeneracies 1, 3, 6
+@pytest.fixture(scope="module")
+def oscillator():
+    # V = omega^2 r^2 / 2 on a sphere large enough that the low states vanish at the wall
     omega, h, R = 1.0, 0.3, 6.5
     g = sphere_grid((0.0, 0.0, 0.0), R, h)
     x = g.points()
     V = 0.5 * omega ** 2 * (x * x).sum(1)
     H = Hamiltonian(g, V)
     X0 = np.random.default_rng(7).standard_normal((g.n, 16))
-    r = chefsi_converged(H, X0, m=16, n_want=10, tol=1e-7)
+    return omega, g, chefsi_converged(H, X0, m=16, n_want=10, tol=1e-7)
+
+
+def test_harmonic_oscillator(oscillator):
+    # levels omega (n + 3/2) with degeneracies 1, 3, 6
+    omega, _, r = oscillator
     expect = np.array([1.5] + [2.5] * 3 + [3.5] * 6) * omega
     assert np.max(np.abs(r["lam"][:10] - expect)) < 1e-6
+
+
+def test_density_of_oscillator_ground_state(oscillator):
+    """rho of the doubly occupied ground state = 2 |psi_0|^2 with the analytic
+    psi_0(r) = (omega/pi)^(3/4) exp(-omega r^2 / 2).  Taking another column (an excited
+    state), dropping the occupation factor or squaring the wrong axis of X fails."""
+    omega, g, r = oscillator
+    x = g.points()
+    exact = 2.0 * (omega / math.pi) ** 1.5 * np.exp(-omega * (x * x).sum(1))
+    rho = density(r["X"], np.array([2.0]))
+    assert np.max(np.abs(rho - exact)) < 1e-5 * exact.max()
+    assert abs(g.h ** 3 * rho.sum() - 2.0) < 1e-10
 
 
 def _tiny_cluster(species):

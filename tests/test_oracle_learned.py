@@ -61,6 +61,27 @@ def test_network_zero_weights_and_parameter_layout():
     assert all(np.array_equal(back[k], q[k]) for k in q)
 
 
+def test_forward_single_path_closed_form():
+    """One non-zero weight per layer (input i -> hidden j -> hidden k -> output) gives
+    y = w3_k tanh(W2_jk tanh(W1_ij x_i + b1_j) + b2_k) + b3 exactly: every other hidden
+    unit sees tanh(0) = 0.  A different activation, a transposed W2 (j != k) or a dropped
+    bias changes y."""
+    p = L.init_params(0)
+    for key in p:
+        p[key] = np.zeros_like(p[key])
+    i, j, k = 5, 17, 90
+    p["W1"][i, j], p["b1"][j] = 0.8, -0.3
+    p["W2"][j, k], p["b2"][k] = -1.7, 0.25
+    p["w3"][k], p["b3"][0] = 2.5, 0.1
+    x = np.zeros((4, 32))
+    x[:, i] = [-2.0, -0.4, 0.0, 1.3]
+    x[:, 3] = 9.0                      # an input with no path to the output
+    y, (_, h1, h2) = L.forward(p, x)
+    expect = 2.5 * np.tanh(-1.7 * np.tanh(0.8 * x[:, i] - 0.3) + 0.25) + 0.1
+    assert np.allclose(y, expect, rtol=0, atol=1e-15)
+    assert np.count_nonzero(h1) == 4 and np.count_nonzero(h2) == 4
+
+
 def test_gradient_matches_finite_differences():
     rng = np.random.default_rng(4)
     p = L.init_params(11)

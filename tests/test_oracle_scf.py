@@ -1,7 +1,8 @@
 """Pins of the oracle's SCF pieces: LDA exchange-correlation (potential = derivative of
 the energy density, branch continuity of PZ81, the exchange constant), the Poisson
 solver against the analytic potential of Gaussian charges, Anderson mixing on a linear
-fixed-point problem, and a converged SCF of SiH4."""
+fixed-point problem, a converged SCF of SiH4, and the SCF's total-energy expression
+against the Kohn-Sham energy functional evaluated directly from the orbitals."""
 import math
 
 import numpy as np
@@ -67,19 +68,72 @@ def test_anderson_solves_linear_fixed_point():
     assert np.max(np.abs(v - exact)) < 1e-9
 
 
-def test_scf_sih4_converges():
-    from workloads import pseudo_params, random_block_lex
+def _sih4():
     dd = 1.48 / 0.529177210903 / np.sqrt(3.0)
     pos = np.array([[0.0, 0.0, 0.0], [dd, dd, dd], [dd, -dd, -dd], [-dd, dd, -dd], [-dd, -dd, dd]]) + 0.05
     z = np.array([14, 1, 1, 1, 1], dtype=np.int32)
+    return pos, z
+
+
+def _sih4_scf(**kw):
+    from workloads import pseudo_params, random_block_lex
+    pos, z = _sih4()
     g = sphere_grid(pos[0], 8.0, 0.5)
     X0 = random_block_lex(1, g.n, 8)
-    r = scf(pos, z, pseudo_params(), 8.0, 0.5, 8, 10, X0, max_steps=40)
-    rep = r["reports"]
+    return scf(pos, z, pseudo_params(), 8.0, 0.5, 8, 10, X0, max_steps=40, **kw)
+
+
+@pytest.fixture(scope="module")
+def sih4_fixed():
+    return _sih4_scf()
+
+
+@pytest.fixture(scope="module")
+def sih4_smeared():
+    return _sih4_scf(kT=0.01)
+
+
+def test_scf_sih4_converges(sih4_fixed):
+    rep = sih4_fixed["reports"]
     assert rep[-1]["sre_ry"] < 1e-4
     assert abs(rep[-1]["electrons"] - 8.0) < 1e-9
     assert abs(rep[-1]["e_total"] - rep[-2]["e_total"]) < 1e-5
     assert rep[-1]["lumo"] > rep[-1]["homo"]
+
+
+@pytest.mark.parametrize("which,kT", [("sih4_fixed", 0.0), ("sih4_smeared", 0.01)])
+def test_total_energy_equals_kohn_sham_functional(which, kT, request):
+    """The SCF's total energy (band energy minus the double-counting terms) against the
+    Kohn-Sham energy functional evaluated directly from the orbitals:
+        E = sum_i f_i <x_i| -1/2 Lap_h |x_i> + sum_i f_i <x_i| V_NL |x_i> + h^3 sum rho V_ion
+            + 1/2 h^3 sum rho V_H[rho] + h^3 sum rho eps_xc[rho]  (- T S)
+    with <u|v> = h^3 sum u v, the kinetic matrix, the KB projectors (V_NL = P E h^3 P^T)
+    and the ionic potential built separately; no Ritz value enters.  A sign error in the
+    double-counting term, a missing 1/2 on the Hartree energy or the exchange-correlation
+    potential in place of its energy density changes E by at least ~1e-1 Ha here."""
+    from oracle.hamiltonian import kinetic_matrix
+    from oracle.potential import kb_projectors, local_potential
+    from oracle.scf import occupations
+    from workloads import pseudo_params
+    r = request.getfixturevalue(which)
+    pos, z = _sih4()
+    g, X, rho = r["grid"], r["X"], r["rho"]
+    h3 = g.h ** 3
+    species = pseudo_params()
+    occ, _, minus_ts = occupations(r["lam"], 8, kT)
+    kin = h3 * float(np.sum(occ * np.einsum("pi,pi->i", X, kinetic_matrix(g) @ X)))
+    P, E, _ = kb_projectors(g, pos, z, species)
+    proj = P.T @ X                                   # <chi_j, x_i> without the h^3 weight
+    nl = h3 * float(np.sum(occ * np.einsum("j,ji->i", E * h3, proj * proj)))
+    v_ion = local_potential(g.points(), pos, z, species)
+    rho_direct = (X[:, :len(occ)] ** 2) @ occ
+    assert np.max(np.abs(rho_direct - rho)) < 1e-14 * np.max(rho)
+    vh = Poisson(g).solve(rho_direct)
+    eps, _ = lda_xc(rho_direct)
+    e_direct = (kin + nl + h3 * float(rho_direct @ v_ion) + 0.5 * h3 * float(rho_direct @ vh)
+                + h3 * float(rho_direct @ eps) + minus_ts)
+    e_scf = r["reports"][-1]["e_total"]
+    assert abs(e_scf - e_direct) < 1e-8 * abs(e_direct), (e_scf, e_direct)
 
 
 def test_fermi_occupations_closed_forms():
@@ -108,15 +162,8 @@ def test_fermi_occupations_closed_forms():
     assert np.array_equal(occ0, [2, 2, 2, 0, 0]) and mu0 == -0.3 and mts0 == 0.0
 
 
-def test_scf_sih4_smeared_converges():
-    from workloads import pseudo_params, random_block_lex
-    dd = 1.48 / 0.529177210903 / np.sqrt(3.0)
-    pos = np.array([[0.0, 0.0, 0.0], [dd, dd, dd], [dd, -dd, -dd], [-dd, dd, -dd], [-dd, -dd, dd]]) + 0.05
-    z = np.array([14, 1, 1, 1, 1], dtype=np.int32)
-    g = sphere_grid(pos[0], 8.0, 0.5)
-    X0 = random_block_lex(1, g.n, 8)
-    r = scf(pos, z, pseudo_params(), 8.0, 0.5, 8, 10, X0, max_steps=40, kT=0.01)
-    rep = r["reports"]
+def test_scf_sih4_smeared_converges(sih4_smeared):
+    rep = sih4_smeared["reports"]
     assert rep[-1]["sre_ry"] < 1e-4
     assert abs(rep[-1]["electrons"] - 8.0) < 1e-9
     assert rep[-1]["minus_ts"] < 0.0
@@ -197,18 +244,10 @@ def test_group_degree_reaches_the_requested_damping():
     assert d_single[0] == 3 and degs[0] == d_single[1]
 
 
-def test_scf_sih4_adaptive_degree_converges():
-    from workloads import pseudo_params, random_block_lex
-    dd = 1.48 / 0.529177210903 / np.sqrt(3.0)
-    pos = np.array([[0.0, 0.0, 0.0], [dd, dd, dd], [dd, -dd, -dd], [-dd, dd, -dd], [-dd, -dd, dd]]) + 0.05
-    z = np.array([14, 1, 1, 1, 1], dtype=np.int32)
-    g = sphere_grid(pos[0], 8.0, 0.5)
-    X0 = random_block_lex(1, g.n, 8)
-    fixed = scf(pos, z, pseudo_params(), 8.0, 0.5, 8, 10, X0, max_steps=40)
-    adapt = scf(pos, z, pseudo_params(), 8.0, 0.5, 8, 10, X0, max_steps=40, degree_min=4, degree_max=16, group=2,
-                reduction=0.1)
+def test_scf_sih4_adaptive_degree_converges(sih4_fixed):
+    adapt = _sih4_scf(degree_min=4, degree_max=16, group=2, reduction=0.1)
     rep = adapt["reports"]
     assert rep[-1]["sre_ry"] < 1e-4
-    assert abs(rep[-1]["e_total"] - fixed["reports"][-1]["e_total"]) < 1e-6 * 5
+    assert abs(rep[-1]["e_total"] - sih4_fixed["reports"][-1]["e_total"]) < 1e-6 * 5
     # the degrees really vary: some iteration filtered with less than the maximum
     assert min(r["filter_work"] for r in rep[1:]) < 16 and rep[0]["filter_work"] > 16
