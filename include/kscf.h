@@ -524,6 +524,30 @@ int kscf_mlp_work_size(int64_t n, size_t* bytes);
 int kscf_mlp_loss_grad(const float* params, const float* mu, const float* inv_sd, const float* D, const float* t,
                        int64_t n, float* grad, double* loss, void* work, size_t work_bytes, void* stream);
 
+/* Training data of one self-consistent cluster: for every domain point p (rows in
+ * lexicographic point order, n_points rows), D_out[p] = the 32 descriptors of its slot
+ * (D_slots from kscf_descriptors on the SCF's Hamiltonian) and t_out[p] = V_in - V_start
+ * at that slot (the correction the network learns), in FP32.  Device arrays; enqueued on
+ * the SCF's stream. */
+int kscf_mlp_training_data(const kscf_scf* scf, const float* D_slots, float* D_out, float* t_out);
+
+/* Standardisation of a training set (n >= 2 rows of D, targets t; device arrays):
+ *   mu_j = mean_p D[p][j],  sd_j = sqrt(sum_p (D[p][j] - mu_j)^2 / (n - 1)),
+ *   inv_sd_j = 1/sd_j, or 0 when sd_j <= 1e-6 (a constant feature is switched off),
+ *   t_shift = mean t,  t_scale = sample standard deviation of t (1 if it is 0),
+ *   t_norm = (t - t_shift) / t_scale.
+ * Sums in FP64 over a fixed partition of the rows, added in a fixed order (deterministic).
+ * mu, inv_sd: 32 floats; t_norm: n floats (device); t_shift_scale: 2 doubles (HOST).
+ * Synchronous. */
+int kscf_mlp_standardize(const float* D, const float* t, int64_t n, float* mu, float* inv_sd, float* t_norm,
+                         double* t_shift_scale, void* stream);
+
+/* The learned correction of the starting potential: dv[p] = y_p t_scale + t_shift (FP64)
+ * with y = kscf_mlp_forward(params, mu, inv_sd, D, n, precision), written first into
+ * y_work (n floats).  dv: n doubles (device), e.g. one per slot for kscf_scf_start. */
+int kscf_mlp_correction(const float* params, const float* mu, const float* inv_sd, double t_shift, double t_scale,
+                        const float* D, int64_t n, int precision, float* y_work, double* dv, void* stream);
+
 /* One Adam step (Kingma & Ba 2015) on params with moment buffers m, v (step >= 1):
  *   m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
  *   params -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps). */

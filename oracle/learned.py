@@ -12,6 +12,14 @@ centres c_q = q * r_c / 15 (q = 0..15, r_c = 8 bohr),
                      exp(-(r - c_q)^2 / (2 sigma^2)) * (1 + cos(pi r / r_c)) / 2,
     sigma = r_c / 15 (the centre spacing).
 
+Standardisation over a training set of rows D (n x 32) and targets t (n):
+    mu_j = mean_p D[p, j],  sd_j = sqrt(sum_p (D[p, j] - mu_j)^2 / (n - 1)),
+    inv_sd_j = 1/sd_j (0 when sd_j <= 1e-6: a constant feature is switched off),
+    t_shift = mean t,  t_scale = sqrt(sum (t - t_shift)^2 / (n - 1)) (1 when that is 0),
+    t_norm = (t - t_shift) / t_scale.
+Training target per domain point: dV = V_in(converged) - V_start.
+Correction: dV(p) = y(D[p]) t_scale + t_shift.
+
 Network (inputs standardised, x = (D - mu) / sd):
     h1 = tanh(x W1 + b1)      W1: 32 x 128
     h2 = tanh(h1 W2 + b2)     W2: 128 x 128
@@ -122,3 +130,33 @@ def unpack(flat):
 
 
 N_PARAMS = N_IN * N_HID + N_HID + N_HID * N_HID + N_HID + N_HID + 1
+
+
+SD_FLOOR = 1e-6
+
+
+def standardise(D, t):
+    """(mu, inv_sd, t_shift, t_scale, t_norm) of a training set (see the module docstring)."""
+    D = np.asarray(D, dtype=np.float64)
+    t = np.asarray(t, dtype=np.float64)
+    n = len(t)
+    mu = D.sum(0) / n
+    sd = np.sqrt(((D - mu) ** 2).sum(0) / (n - 1))
+    inv_sd = np.where(sd > SD_FLOOR, 1.0 / np.where(sd > SD_FLOOR, sd, 1.0), 0.0)
+    t_shift = t.sum() / n
+    t_scale = math.sqrt(((t - t_shift) ** 2).sum() / (n - 1))
+    if t_scale == 0.0:
+        t_scale = 1.0
+    return mu, inv_sd, t_shift, t_scale, (t - t_shift) / t_scale
+
+
+def training_target(v_in, v_start):
+    """dV = V_in(converged) - V_start per domain point."""
+    return np.asarray(v_in, dtype=np.float64) - np.asarray(v_start, dtype=np.float64)
+
+
+def correction(params, mu, inv_sd, t_shift, t_scale, D):
+    """dV per row of D: the network on the standardised descriptors, de-standardised."""
+    x = (np.asarray(D, dtype=np.float64) - mu) * inv_sd
+    y, _ = forward(params, x)
+    return y * t_scale + t_shift

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkscf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["grid.cpp", "ham.cpp", "capi.cpp", "setup.cu", "filter.cu", "gemm.cu", "gemm_tc.cu", "apply_noalloc.cu",
+SOURCES = ["grid.cpp", "ham.cpp", "capi.cpp", "setup.cu", "filter.cu", "filter_cm.cu", "gemm.cu", "gemm_tc.cu", "apply_noalloc.cu",
            "scf_kernels.cu", "scf.cpp", "learned.cu", "dos.cpp", "lanczos.cpp", "chol.cu"]
 
 

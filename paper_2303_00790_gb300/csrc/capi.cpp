@@ -176,10 +176,17 @@ size_t rr_bytes(const RRPlan& p) {
          kscf_align256(p.tc);
 }
 
+// FP32 on 8^3 bricks: the filter runs on two chunk-major working copies of the block
+bool filter_chunk_major(const Ham& H, int dtype) { return dtype == KSCF_F32 && H.grid.B == 8; }
+
 size_t filter_bytes(const Ham& H, int k, int dtype, int block) {
   const int w = block_width(k, block);
-  return kscf_align256((size_t)H.grid.n_slots * coef_ld(w) * esize(dtype)) +
-         kscf_align256((size_t)std::max(H.n_kb, 1) * 4 * coef_ld(w) * esize(dtype));
+  const size_t coef = kscf_align256((size_t)std::max(H.n_kb, 1) * 4 * coef_ld(w) * esize(dtype));
+  if (filter_chunk_major(H, dtype)) {
+    const size_t wpad = (size_t)(w + 15) / 16 * 16;   // covers chunk widths 8 and 16
+    return 2 * kscf_align256((size_t)H.grid.n_slots * wpad * 4) + coef + kscf_align256(KSCF_CM_ZERO_BYTES);
+  }
+  return kscf_align256((size_t)H.grid.n_slots * coef_ld(w) * esize(dtype)) + coef;
 }
 
 size_t apply_bytes(const Ham& H, int k, int dtype) {
@@ -265,8 +272,10 @@ int cholqr_pass(const Ham& H, void* X, int64_t ld, int k, int dtype, int mode, c
   const double h3 = H.grid.h * H.grid.h * H.grid.h;
   const int64_t rows = H.grid.n_slots;
   const double u = dtype == KSCF_F64 ? 0x1.0p-53 : 0x1.0p-24;
-  int hst[2] = {0, 0};
+  int hst[3] = {0, 0, 0};
   auto factor = [&](double floor_rel) -> int {
+    // status[2]: a NaN or Inf on the Gram diagonal (X itself is not finite)
+    KSCF_CUDA_TRY(launch_diag_finite(S, k, k, status + 2, st));
     KSCF_CUDA_TRY(launch_chol_inv(S, k, k, floor_rel, S, k, cwork, status, st));
     KSCF_CUDA_TRY(cudaMemcpyAsync(hst, status, sizeof(hst), cudaMemcpyDeviceToHost, st));
     KSCF_CUDA_TRY(cudaStreamSynchronize(st));
@@ -275,6 +284,10 @@ int cholqr_pass(const Ham& H, void* X, int64_t ld, int k, int dtype, int mode, c
     if (hst[1] != 0) {
       set_error("Cholesky-QR: a grid barrier of the factorisation kernel timed out");
       return KSCF_ERR_TIMEOUT;
+    }
+    if (hst[2] != 0) {
+      set_error("Cholesky-QR: the Gram matrix has a NaN or Inf on its diagonal (X is not finite)");
+      return KSCF_ERR_NONFINITE;
     }
     return KSCF_OK;
   };
@@ -360,6 +373,13 @@ extern "C" int kscf_hamiltonian_apply(const kscf_ham* ham, void* Y, int64_t ld_y
   KSCF_CUDA_TRY(launch_kb_gather(H, Y, ld_y, k, dtype, work, coef_ld(k), st));
   KSCF_CUDA_TRY(launch_cheb_step(H, Y, ld_y, nullptr, 0, HY, ld_hy, k, (int)std::min<int64_t>(ld_y, ld_hy), dtype,
                                  1.0, 0.0, 0.0, work, coef_ld(k), st));
+  // a NaN or Inf in Y or in the potential shows up in HY: flag it for kscf_check_status
+  unsigned int* flag = nonfinite_flag();
+  if (!flag) {
+    set_error("kscf_hamiltonian_apply: status word lookup failed");
+    return KSCF_ERR_CUDA;
+  }
+  KSCF_CUDA_TRY(launch_finite_rows(H, HY, ld_hy, k, dtype, flag, st));
   return KSCF_OK;
 }
 
@@ -379,11 +399,47 @@ extern "C" int kscf_chebyshev_filter(const kscf_ham* ham, void* X, int64_t ld, i
   const int w = block_width(k, block);
   const size_t es = esize(dtype);
   Carver cv(work);
+  const double e = (b - a) / 2.0, c = (b + a) / 2.0;
+  const double sigma1 = e / (a0 - c), tau = 2.0 / sigma1;
+  if (filter_chunk_major(H, dtype)) {
+    // two chunk-major working copies A, B: A = Y_0 (converted block), B = Y_1, then Y_j
+    // overwrites Y_{j-2}; the last step writes Y_m straight into the caller's block
+    const int cw = cm_chunk_width();
+    const size_t wpad16 = (size_t)(w + 15) / 16 * 16;
+    float* A = (float*)cv.take((size_t)H.grid.n_slots * wpad16 * 4);
+    float* B = (float*)cv.take((size_t)H.grid.n_slots * wpad16 * 4);
+    float* coef = (float*)cv.take((size_t)std::max(H.n_kb, 1) * 4 * coef_ld(w) * 4);
+    float* zero = (float*)cv.take(KSCF_CM_ZERO_BYTES);
+    const int64_t cld = coef_ld(w);
+    KSCF_CUDA_TRY(cudaMemsetAsync(zero, 0, KSCF_CM_ZERO_BYTES, st));
+    KSCF_CUDA_TRY(launch_zero_rows(H, X, ld, k, dtype, st));
+    for (int c0 = 0; c0 < k; c0 += w) {
+      const int wb = std::min(w, k - c0);
+      float* Xb = (float*)X + c0;
+      KSCF_CUDA_TRY(launch_to_chunk_major(H, Xb, ld, wb, cw, A, B, st));
+      KSCF_CUDA_TRY(launch_kb_gather_cm(H, A, cw, wb, coef, cld, st));
+      // Y_1 = (sigma_1/e)(H X - c X)
+      KSCF_CUDA_TRY(launch_cm_step(H, A, nullptr, degree == 1 ? Xb : B, degree == 1 ? ld : -1, wb, sigma1 / e, 0.0,
+                                   c, coef, cld, degree == 1, zero, st));
+      float* cur = B;
+      float* prv = A;
+      double sigma = sigma1;
+      for (int j = 2; j <= degree; j++) {
+        const double sigma_new = 1.0 / (tau - sigma);
+        const bool last = j == degree;
+        KSCF_CUDA_TRY(launch_kb_gather_cm(H, cur, cw, wb, coef, cld, st));
+        // Y_j overwrites Y_{j-2} (each element read before it is written)
+        KSCF_CUDA_TRY(launch_cm_step(H, cur, prv, last ? Xb : prv, last ? ld : -1, wb, 2.0 * sigma_new / e,
+                                     -sigma * sigma_new, c, coef, cld, last, zero, st));
+        std::swap(cur, prv);
+        sigma = sigma_new;
+      }
+    }
+    return KSCF_OK;
+  }
   const int64_t wpad = coef_ld(w);
   void* buf = cv.take((size_t)H.grid.n_slots * wpad * es);
   void* coef = cv.take((size_t)std::max(H.n_kb, 1) * 4 * wpad * es);
-  const double e = (b - a) / 2.0, c = (b + a) / 2.0;
-  const double sigma1 = e / (a0 - c), tau = 2.0 / sigma1;
   KSCF_CUDA_TRY(launch_zero_rows(H, X, ld, k, dtype, st));
   for (int c0 = 0; c0 < k; c0 += w) {
     const int wb = std::min(w, k - c0);
@@ -665,10 +721,11 @@ extern "C" int kscf_selftest_barrier_timeout(void* stream) {
 }
 
 extern "C" int kscf_check_status(void) {
-  unsigned int st = 0, fs = 0;
+  unsigned int st = 0, fs = 0, cs = 0, nf = 0;
   cudaError_t e = tc_status(true, &st);
   if (e == cudaSuccess) e = filter_status(true, &fs);
-  st |= fs << 1;
+  if (e == cudaSuccess) e = cm_status(true, &cs, &nf);
+  st |= (fs | cs) << 1;
   if (e != cudaSuccess) {
     set_error("kscf_check_status: %s", cudaGetErrorString(e));
     return KSCF_ERR_CUDA;
@@ -676,6 +733,10 @@ extern "C" int kscf_check_status(void) {
   if (st) {
     set_error("a bounded device wait timed out (status %u: bit 0 tensor-core GEMM, bit 1 filter)", st);
     return KSCF_ERR_TIMEOUT;
+  }
+  if (nf) {
+    set_error("a Chebyshev filter or Hamiltonian apply stored a NaN or Inf (non-finite input X or potential)");
+    return KSCF_ERR_NONFINITE;
   }
   return KSCF_OK;
 }

@@ -811,6 +811,31 @@ __global__ void copy_cols_kernel(const T* src, int64_t ld_src, T* dst, int64_t l
 
 static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// one warp per slot: sets *flag when a domain row holds a NaN or Inf in its first k values
+template <typename T>
+__global__ void finite_rows_kernel(const T* X, int64_t ld, int k, const uint8_t* mask, int64_t n_slots,
+                                   unsigned int* flag) {
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  bool bad = false;
+  if (r < n_slots && mask[r]) {
+    const T* row = X + r * ld;
+    for (int j = threadIdx.x & 31; j < k; j += 32) bad |= !(fabs((double)row[j]) <= 1.7976931348623157e308);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+cudaError_t launch_finite_rows(const Ham& H, const void* X, int64_t ld, int k, int dtype, unsigned int* flag,
+                               cudaStream_t st) {
+  const int64_t n = H.grid.n_slots * 32;
+  if (dtype == KSCF_F64)
+    finite_rows_kernel<double><<<blocks_for(n, 256), 256, 0, st>>>((const double*)X, ld, k, H.d_mask,
+                                                                    H.grid.n_slots, flag), count_launch();
+  else
+    finite_rows_kernel<float><<<blocks_for(n, 256), 256, 0, st>>>((const float*)X, ld, k, H.d_mask,
+                                                                   H.grid.n_slots, flag), count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_zero_rows(const Ham& H, void* X, int64_t ld, int k, int dtype, cudaStream_t st) {
   if (H.n_pad == 0 || k == 0) return cudaSuccess;
   const int64_t n = H.n_pad * 32;

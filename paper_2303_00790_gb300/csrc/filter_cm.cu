@@ -1,0 +1,508 @@
+// Chebyshev filter steps on chunk-major working buffers (FP32, 8^3 bricks).
+//
+// The filter (CheFSI paragraph of arXiv 2303.00790; three-term recurrence of Zhou,
+// Saad, Tiago & Chelikowsky 2006) runs m degree steps over one column block.  Its
+// working copies of the block are stored chunk-major: the block's columns are cut
+// into chunks of CW vectors, and chunk c holds every slot's CW values contiguously,
+//     element (c, s, v) at buf[(c * n_slots + s) * CW + v],
+// so that one brick of one chunk is one contiguous 512 * CW * 4-byte range.  The
+// degree-step launches walk the bricks chunk by chunk (within supertiles of
+// consecutive bricks), so the neighbour bricks whose faces a brick needs were read
+// from DRAM moments before and still sit in L2, and DRAM sees long sequential runs.
+//
+// One step computes, for every slot s and vector v,
+//   out = alpha (H in - c in) + beta prev,
+//   H in = -1/2 Lap_h in + V in + sum_i chi_i (E_i h^3 <chi_i, in>),
+// the nonlocal projections <chi_i, in> coming from kb_gather_cm launched just before.
+// cm_step_ldg16 does it for one brick and 16 vectors per CTA: the brick core is copied
+// into shared memory, the halo rows of each line come from the neighbour bricks in L2
+// into registers, lines that hold no domain point are skipped, and the nonlocal scatter
+// reads the brick's KB coefficients and entries from shared memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cstdlib>
+#include <mutex>
+
+#include "kscf_internal.h"
+
+namespace kscf {
+
+__device__ unsigned int g_cm_status;     // bit 0: a bounded wait gave up
+__device__ unsigned int g_nonfinite;     // set when a checked step stored a NaN or Inf
+
+namespace {
+
+struct CmArgs {
+  const float* in;        // chunk-major, chunk width CW
+  const float* prev;      // may alias out (each element read before it is written)
+  int64_t cs_prev, ld_prev;  // element (c, s, v) at prev[c * cs_prev + s * ld_prev + v]
+  float* out;
+  int64_t cs_out, ld_out;
+  int out_vec;            // out rows allow aligned vector stores
+  int w;                  // valid columns of the block
+  int nchunk, n_bricks, super;  // CTA order: supertiles of `super` bricks, chunk-major inside
+  float alpha, beta, c;
+  const float* coef;      // (n_kb*4) rows of cld, global column index
+  int64_t cld;
+  const float* V;
+  const int32_t* nbr;
+  const uint8_t* mask;
+  const int64_t* kb_ptr;
+  const int32_t* kb_atom;
+  const float* kb_chi;
+  const uint16_t* entry_lslot;
+  float st[7];
+  int64_t n_slots;
+  int check;              // flag non-finite stored values
+};
+
+// CTA -> (chunk, brick): supertiles of `super` consecutive bricks (Hilbert order); inside
+// a supertile all bricks of chunk 0, then of chunk 1, ...  Returns false for the idle
+// CTAs of a partial last supertile.
+__device__ __forceinline__ bool cta_item(const CmArgs& a, int* chunk, int* brick) {
+  const int per = a.nchunk * a.super;
+  const int t = blockIdx.x / per, rem = blockIdx.x - t * per;
+  const int c = rem / a.super, i = rem - c * a.super;
+  const int b = t * a.super + i;
+  *chunk = c;
+  *brick = b;
+  return b < a.n_bricks;
+}
+
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(*(uint64_t*)&a), "l"(*(uint64_t*)&b));
+  return *(float2*)&r;
+}
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(*(uint64_t*)&a), "l"(*(uint64_t*)&b), "l"(*(uint64_t*)&c));
+  return *(float2*)&r;
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(*(uint64_t*)&a), "l"(*(uint64_t*)&b));
+  return *(float2*)&r;
+}
+__device__ __forceinline__ float2 f2(float s) { return make_float2(s, s); }
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// 16 vectors per CTA, 256 threads (64 lines x 4 lanes x float4).  Core by cp.async, the
+// halo rows of each line loaded from the neighbour bricks (L2) into the register window.
+namespace {
+__device__ __forceinline__ float4 f4_add(float4 a, float4 b) {
+  const float2 lo = f2_add(make_float2(a.x, a.y), make_float2(b.x, b.y));
+  const float2 hi = f2_add(make_float2(a.z, a.w), make_float2(b.z, b.w));
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+__device__ __forceinline__ float4 f4_fma(float2 c, float4 a, float4 b) {
+  const float2 lo = f2_fma(c, make_float2(a.x, a.y), make_float2(b.x, b.y));
+  const float2 hi = f2_fma(c, make_float2(a.z, a.w), make_float2(b.z, b.w));
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+__device__ __forceinline__ float4 f4_mul(float2 c, float4 a) {
+  const float2 lo = f2_mul(c, make_float2(a.x, a.y));
+  const float2 hi = f2_mul(c, make_float2(a.z, a.w));
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+template <bool WITH_CENTRE>
+__device__ __forceinline__ float4 line4(const float4* w, int i, const float2* c2) {
+  float4 s = WITH_CENTRE ? f4_mul(c2[0], w[i]) : f4_mul(c2[1], f4_add(w[i + 1], w[i - 1]));
+  if (WITH_CENTRE) s = f4_fma(c2[1], f4_add(w[i + 1], w[i - 1]), s);
+#pragma unroll
+  for (int k = 2; k <= 6; k++) s = f4_fma(c2[k], f4_add(w[i + k], w[i - k]), s);
+  return s;
+}
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldg((const float4*)p); }
+__device__ __forceinline__ bool finite4(float4 v) {
+  return fabsf(v.x) <= FLT_MAX && fabsf(v.y) <= FLT_MAX && fabsf(v.z) <= FLT_MAX && fabsf(v.w) <= FLT_MAX;
+}
+}  // namespace
+
+// Shared memory of cm_step_ldg16 (bytes): core and accumulator (512 point slots x 16
+// floats each), the coefficients of the brick's KB atoms (KSCF_BRICK_ATOMS x 4 x 16
+// floats) and the first LDG_ENT entries of the brick (packed word + chi).
+constexpr int LDG_ENT = 512;
+constexpr int LDG_CORE = 0, LDG_ACC = 32768, LDG_KBC = 65536, LDG_EW = LDG_KBC + KSCF_BRICK_ATOMS * 4 * 64,
+              LDG_ECHI = LDG_EW + LDG_ENT * 4, LDG_SMEM = LDG_ECHI + LDG_ENT * 16;
+
+// Lines of a pass that hold no domain point are skipped: each pass takes its lines from
+// the brick's compacted list of live lines, and the threads past the list's end idle
+// (their points are padding and never stored).  The nonlocal scatter reads the
+// projection coefficients of the brick's KB atoms and the brick's entries from shared
+// memory, staged at the start together with the core (SMEM_KB; otherwise from global
+// memory).
+template <bool SMEM_KB>
+__global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t* __restrict__ lines,
+                                                        const uint8_t* __restrict__ nlines,
+                                                        const int32_t* __restrict__ batoms,
+                                                        const int32_t* __restrict__ bnat,
+                                                        const uint32_t* __restrict__ eword) {
+  extern __shared__ __align__(16) uint8_t smw[];
+  float4* core4 = (float4*)(smw + LDG_CORE);   // [512][4]
+  float4* acc4 = (float4*)(smw + LDG_ACC);     // [512][4]
+  float4* kbc = (float4*)(smw + LDG_KBC);      // [atom][l][4]
+  uint32_t* ew = (uint32_t*)(smw + LDG_EW);
+  float4* echi = (float4*)(smw + LDG_ECHI);
+  auto sl = [](int x, int y, int z) { return (z * 8 + y) * 8 + (x ^ (y & 1)); };
+  int c, brick;
+  if (!cta_item(a, &c, &brick)) return;
+  const int tid = threadIdx.x, vp = tid & 3, L = tid >> 2;
+  const int vl = 4 * vp;
+  const int64_t b0 = (int64_t)brick * 512;
+  const float* inc = a.in + (int64_t)c * a.n_slots * 16 + vl;   // row stride 16 floats
+  const float* own = inc + b0 * 16;
+  const float* nbp[6];
+  bool nbv[6];
+#pragma unroll
+  for (int f = 0; f < 6; f++) {
+    const int q = __ldg(a.nbr + (int64_t)brick * 6 + f);
+    nbv[f] = q >= 0;
+    nbp[f] = q >= 0 ? inc + (int64_t)q * 512 * 16 : own;
+  }
+  const uint8_t* bl = lines + (int64_t)brick * 192;
+  const int nlx = __ldg(nlines + brick * 3), nly = __ldg(nlines + brick * 3 + 1), nlz = __ldg(nlines + brick * 3 + 2);
+  const int lx = L < nlx ? __ldg(bl + L) : -1;
+  const int ly = L < nly ? __ldg(bl + 64 + L) : -1;
+  const int lz = L < nlz ? __ldg(bl + 128 + L) : -1;
+  // core: 512 rows x 64 B, padding rows zero-filled without a read
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    const int r = L + 64 * i;
+    const uint32_t live = __ldg(a.mask + b0 + r);
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(&core4[sl(r & 7, (r >> 3) & 7, r >> 6) * 4 + vp]);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(own + r * 16), "r"(live ? 16 : 0)
+                 : "memory");
+  }
+  const int64_t e0 = __ldg(a.kb_ptr + b0), e1 = __ldg(a.kb_ptr + b0 + 512);
+  const int ne = (int)(e1 - e0);
+  if (SMEM_KB) {
+    const int nat = __ldg(bnat + brick);
+    for (int t = tid; t < nat * 16; t += 256) {
+      const int at = __ldg(batoms + (int64_t)brick * KSCF_BRICK_ATOMS + (t >> 4));
+      const int l = (t >> 2) & 3, q = t & 3;
+      const float* src = a.coef + ((int64_t)at * 4 + l) * a.cld + c * 16 + 4 * q;
+      const uint32_t d = (uint32_t)__cvta_generic_to_shared(&kbc[((t >> 4) * 4 + l) * 4 + q]);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    }
+    for (int i = tid; i < min(ne, LDG_ENT); i += 256) {
+      const uint32_t dw = (uint32_t)__cvta_generic_to_shared(&ew[i]);
+      const uint32_t dc = (uint32_t)__cvta_generic_to_shared(&echi[i]);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dw), "l"(eword + e0 + i) : "memory");
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dc), "l"(a.kb_chi + 4 * (e0 + i)) : "memory");
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  float vv[8];
+  uint32_t mk = 0;
+  if (lz >= 0) {
+#pragma unroll
+    for (int z = 0; z < 8; z++) {
+      const int64_t s = b0 + z * 64 + lz;
+      mk |= (uint32_t)__ldg(a.mask + s) << z;
+      vv[z] = __ldg(a.V + s);
+    }
+  }
+  float2 c2[7];
+  c2[0] = f2(3.0f * a.st[0]);
+#pragma unroll
+  for (int k = 1; k < 7; k++) c2[k] = f2(a.st[k]);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  // ---- x pass: line (y, z) ----
+  {
+    const int y = lx & 7, z = lx >> 3;
+    const int rb = (z * 8 + y) * 8 * 16;
+    float4 w[20];
+    if (lx >= 0) {
+#pragma unroll
+      for (int xx = 0; xx < 6; xx++) {
+        const float4 m = ld4(nbp[0] + rb + (2 + xx) * 16);
+        const float4 p = ld4(nbp[1] + rb + xx * 16);
+        w[xx] = nbv[0] ? m : z4;
+        w[14 + xx] = nbv[1] ? p : z4;
+      }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    if (lx >= 0) {
+#pragma unroll
+      for (int x = 0; x < 8; x++) w[6 + x] = core4[sl(x, y, z) * 4 + vp];
+#pragma unroll
+      for (int x = 0; x < 8; x++) acc4[sl(x, y, z) * 4 + vp] = line4<true>(w, 6 + x, c2);
+    }
+  }
+  // ---- y pass: line (x, z) ----
+  {
+    const int x = ly & 7, z = ly >> 3;
+    float4 w[20];
+    if (ly >= 0) {
+#pragma unroll
+      for (int yy = 0; yy < 6; yy++) {
+        const float4 m = ld4(nbp[2] + ((z * 8 + 2 + yy) * 8 + x) * 16);
+        const float4 p = ld4(nbp[3] + ((z * 8 + yy) * 8 + x) * 16);
+        w[yy] = nbv[2] ? m : z4;
+        w[14 + yy] = nbv[3] ? p : z4;
+      }
+#pragma unroll
+      for (int y = 0; y < 8; y++) w[6 + y] = core4[sl(x, y, z) * 4 + vp];
+    }
+    __syncthreads();  // x-pass accumulator writes are visible
+    if (ly >= 0) {
+#pragma unroll
+      for (int y = 0; y < 8; y++) {
+        const int q = sl(x, y, z) * 4 + vp;
+        acc4[q] = f4_add(acc4[q], line4<false>(w, 6 + y, c2));
+      }
+    }
+  }
+  __syncthreads();
+  // ---- nonlocal scatter over the brick's entries ----
+  for (int i = L; i < ne; i += 64) {
+    uint32_t word;
+    float4 ch;
+    const float4* cf;
+    float4 cv[4];
+    if (SMEM_KB) {
+      if (i < LDG_ENT) {
+        word = ew[i];
+        ch = echi[i];
+      } else {
+        word = __ldg(eword + e0 + i);
+        ch = __ldg((const float4*)(a.kb_chi + 4 * (e0 + i)));
+      }
+      cf = kbc + (word >> 16) * 16 + vp;
+#pragma unroll
+      for (int l = 0; l < 4; l++) cv[l] = cf[4 * l];
+    } else {
+      word = __ldg(a.entry_lslot + e0 + i);
+      ch = __ldg((const float4*)(a.kb_chi + 4 * (e0 + i)));
+      const float* g = a.coef + (int64_t)__ldg(a.kb_atom + e0 + i) * 4 * a.cld + c * 16 + vl;
+#pragma unroll
+      for (int l = 0; l < 4; l++) cv[l] = ld4(g + l * a.cld);
+    }
+    const int ls = word & 0xffff;
+    float4 q = f4_mul(f2(ch.x), cv[0]);
+    q = f4_fma(f2(ch.y), cv[1], q);
+    q = f4_fma(f2(ch.z), cv[2], q);
+    q = f4_fma(f2(ch.w), cv[3], q);
+    float* acc = (float*)&acc4[sl(ls & 7, (ls >> 3) & 7, ls >> 6) * 4 + vp];
+    atomicAdd(acc, q.x);
+    atomicAdd(acc + 1, q.y);
+    atomicAdd(acc + 2, q.z);
+    atomicAdd(acc + 3, q.w);
+  }
+  // ---- z pass: line (x, y); potential, recurrence, store ----
+  {
+    const int x = lz & 7, y = lz >> 3;
+    float4 w[20];
+    if (lz >= 0) {
+#pragma unroll
+      for (int zz = 0; zz < 6; zz++) {
+        const float4 m = ld4(nbp[4] + ((2 + zz) * 64 + y * 8 + x) * 16);
+        const float4 p = ld4(nbp[5] + (zz * 64 + y * 8 + x) * 16);
+        w[zz] = nbv[4] ? m : z4;
+        w[14 + zz] = nbv[5] ? p : z4;
+      }
+#pragma unroll
+      for (int z = 0; z < 8; z++) w[6 + z] = core4[sl(x, y, z) * 4 + vp];
+    }
+    __syncthreads();  // scatter atomics are complete
+    if (lz >= 0) {
+      const float2 alpha = f2(a.alpha), beta = f2(a.beta), negc = f2(-a.c);
+      const float* prevp = a.prev ? a.prev + (int64_t)c * a.cs_prev + vl : nullptr;
+      float* outp = a.out + (int64_t)c * a.cs_out + vl;
+      const int col = c * 16 + vl;
+      bool bad = false;
+#pragma unroll
+      for (int z = 0; z < 8; z++) {
+        const int64_t s = b0 + z * 64 + lz;
+        if (!((mk >> z) & 1u)) continue;
+        const float4 yc = w[6 + z];
+        float4 hy = f4_add(acc4[sl(x, y, z) * 4 + vp], line4<false>(w, 6 + z, c2));
+        hy = f4_fma(f2(vv[z]), yc, hy);
+        float4 r = f4_mul(alpha, f4_fma(negc, yc, hy));
+        if (prevp) {
+          const float4 pv = *(const float4*)(prevp + s * a.ld_prev);   // plain load: prev may be out
+          r = f4_fma(beta, pv, r);
+        }
+        if (a.check)
+          bad |= !finite4(make_float4(col < a.w ? r.x : 0.f, col + 1 < a.w ? r.y : 0.f,
+                                      col + 2 < a.w ? r.z : 0.f, col + 3 < a.w ? r.w : 0.f));
+        float* o = outp + s * a.ld_out;
+        if (a.out_vec) {
+          *(float4*)o = r;
+        } else {
+          if (col < a.w) o[0] = r.x;
+          if (col + 1 < a.w) o[1] = r.y;
+          if (col + 2 < a.w) o[2] = r.z;
+          if (col + 3 < a.w) o[3] = r.w;
+        }
+      }
+      if (bad) atomicOr(&g_nonfinite, 1u);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// coef[(a*4+l)*cld + v] = E_l h^3 sum_{entries e of atom a} chi_l(e) Y(slot_e, v) for
+// v < w, and 0 for w <= v < cld (the padded columns of the last chunk then stay zero
+// through the recurrence).  Y chunk-major with chunk width cw.
+__global__ void __launch_bounds__(256) kb_gather_cm(const float* __restrict__ Y, int64_t n_slots, int cw, int w,
+                                                    int64_t cld, const int64_t* __restrict__ aptr,
+                                                    const int64_t* __restrict__ aslot,
+                                                    const float* __restrict__ achi,
+                                                    const double* __restrict__ energy, float* __restrict__ coef) {
+  const int at = blockIdx.x;
+  const int v = blockIdx.y * 32 + threadIdx.x;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  if (v < w) {
+    const float* base = Y + (int64_t)(v / cw) * n_slots * cw + (v % cw);
+    for (int64_t e = aptr[at] + threadIdx.y; e < aptr[at + 1]; e += 8) {
+      const float y = base[aslot[e] * cw];
+      const float4 ch = __ldg((const float4*)(achi + 4 * e));
+      acc[0] += ch.x * y;
+      acc[1] += ch.y * y;
+      acc[2] += ch.z * y;
+      acc[3] += ch.w * y;
+    }
+  }
+  __shared__ float red[8][4][32];
+#pragma unroll
+  for (int l = 0; l < 4; l++) red[threadIdx.y][l][threadIdx.x] = acc[l];
+  __syncthreads();
+  if (threadIdx.y < 4 && v < cld) {
+    const int l = threadIdx.y;
+    float sum = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; q++) sum += red[q][l][threadIdx.x];
+    coef[((int64_t)at * 4 + l) * cld + v] = v < w ? (float)energy[4 * at + l] * sum : 0.f;
+  }
+}
+
+// chunk-major copy of w columns of a slot-major block (row stride ld), padded columns
+// zero; the padding rows of the second working buffer are zeroed too (the step kernels
+// never write padding rows, and they are read as halos)
+__global__ void to_chunk_major(const float* __restrict__ X, int64_t ld, int w, int cw, int wpad, int64_t n_slots,
+                               const uint8_t* __restrict__ mask, float* __restrict__ buf, float* __restrict__ buf2) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_slots * wpad) return;
+  const int64_t s = t / wpad;
+  const int col = (int)(t - s * wpad);
+  const int c = col / cw, v = col - c * cw;
+  const int64_t o = ((int64_t)c * n_slots + s) * cw + v;
+  buf[o] = col < w ? X[s * ld + col] : 0.f;
+  if (!mask[s]) buf2[o] = 0.f;
+}
+
+namespace {
+bool g_ldg_attr[64] = {false};
+
+unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+}  // namespace
+
+int cm_chunk_width() { return 16; }
+
+cudaError_t launch_to_chunk_major(const Ham& H, const float* X, int64_t ld, int w, int cw, float* buf, float* buf2,
+                                  cudaStream_t st) {
+  const int wpad = (w + cw - 1) / cw * cw;
+  const int64_t n = H.grid.n_slots * wpad;
+  to_chunk_major<<<blocks(n, 256), 256, 0, st>>>(X, ld, w, cw, wpad, H.grid.n_slots, H.d_mask, buf, buf2),
+      count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kb_gather_cm(const Ham& H, const float* Y, int cw, int w, float* coef, int64_t cld,
+                                cudaStream_t st) {
+  if (H.n_kb == 0 || w == 0) return cudaSuccess;
+  dim3 grid(H.n_kb, (unsigned)((cld + 31) / 32)), block(32, 8);
+  kb_gather_cm<<<grid, block, 0, st>>>(Y, H.grid.n_slots, cw, w, cld, H.d_kb_atom_ptr, H.d_kb_atom_slot,
+                                       H.d_kb_atom_chi32, H.d_kb_energy, coef),
+      count_launch();
+  return cudaGetLastError();
+}
+
+// One degree step: in chunk-major (chunk width cm_chunk_width()); prev chunk-major or
+// null; out chunk-major (out_ld < 0) or the caller's slot-major block (row stride out_ld).
+cudaError_t launch_cm_step(const Ham& H, const float* in, const float* prev, float* out, int64_t out_ld, int w,
+                           double alpha, double beta, double cshift, const float* coef, int64_t cld, bool check,
+                           const float* zero, cudaStream_t st) {
+  const int cw = cm_chunk_width();
+  CmArgs a;
+  a.in = in;
+  a.prev = prev;
+  a.cs_prev = H.grid.n_slots * cw;
+  a.ld_prev = cw;
+  a.out = out;
+  if (out_ld < 0) {
+    a.cs_out = H.grid.n_slots * cw;
+    a.ld_out = cw;
+    a.out_vec = 1;
+  } else {
+    a.cs_out = cw;
+    a.ld_out = out_ld;
+    a.out_vec = (out_ld % cw == 0 && ((uintptr_t)out % 16) == 0 && w % cw == 0) ? 1 : 0;
+  }
+  a.w = w;
+  a.nchunk = (w + cw - 1) / cw;
+  a.n_bricks = (int)H.grid.n_bricks;
+  // supertiles: the bricks of one chunk stay L2-resident (three buffers x 512 rows x cw x 4 B each)
+  const int64_t per_brick = 3LL * 512 * cw * 4;
+  a.super = (int)std::max<int64_t>(64, std::min<int64_t>(H.grid.n_bricks, (64LL << 20) / per_brick));
+  a.alpha = (float)alpha;
+  a.beta = (float)beta;
+  a.c = (float)cshift;
+  a.coef = coef;
+  a.cld = cld;
+  a.V = H.d_v32;
+  a.nbr = H.d_nbr;
+  a.mask = H.d_mask;
+  a.kb_ptr = H.d_kb_slot_ptr;
+  a.kb_atom = H.d_kb_slot_atom;
+  a.kb_chi = H.d_kb_slot_chi32;
+  a.entry_lslot = H.d_kb_entry_lslot;
+  for (int k = 0; k < 7; k++) a.st[k] = (float)H.stencil[k];
+  a.n_slots = H.grid.n_slots;
+  a.check = check ? 1 : 0;
+  const int n_super = (int)((H.grid.n_bricks + a.super - 1) / a.super);
+  const unsigned grid = (unsigned)((int64_t)n_super * a.super * a.nchunk);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    if (dev >= 0 && dev < 64 && !g_ldg_attr[dev]) {
+      cudaError_t e = cudaFuncSetAttribute(cm_step_ldg16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, LDG_SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(cm_step_ldg16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, LDG_SMEM);
+      if (e != cudaSuccess) return e;
+      g_ldg_attr[dev] = true;
+    }
+    if (H.brick_atoms_ok)
+      cm_step_ldg16<true><<<grid, 256, LDG_SMEM, st>>>(a, H.d_lines, H.d_nlines, H.d_brick_atoms, H.d_brick_natoms,
+                                                       H.d_kb_entry_word), count_launch();
+    else
+      cm_step_ldg16<false><<<grid, 256, LDG_SMEM, st>>>(a, H.d_lines, H.d_nlines, H.d_brick_atoms,
+                                                        H.d_brick_natoms, H.d_kb_entry_word), count_launch();
+  }
+  return cudaGetLastError();
+}
+
+unsigned int* nonfinite_flag() {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_nonfinite) != cudaSuccess) return nullptr;
+  return (unsigned int*)p;
+}
+
+cudaError_t cm_status(bool reset, unsigned int* timeout, unsigned int* nonfinite) {
+  cudaError_t e = cudaMemcpyFromSymbol(timeout, g_cm_status, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(nonfinite, g_nonfinite, sizeof(unsigned int));
+  if (e == cudaSuccess && reset && (*timeout || *nonfinite)) {
+    unsigned int z = 0;
+    e = cudaMemcpyToSymbol(g_cm_status, &z, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_nonfinite, &z, sizeof(unsigned int));
+  }
+  return e;
+}
+
+}  // namespace kscf

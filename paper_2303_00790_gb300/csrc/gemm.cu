@@ -259,4 +259,17 @@ cudaError_t launch_f64_to_dtype(const double* src, int64_t n, int dtype, void* o
   return cudaGetLastError();
 }
 
+// status = 1 when a diagonal element of the k x k matrix S (column-major) is NaN or Inf
+__global__ void diag_finite_kernel(const double* S, int k, int64_t lds, int* status) {
+  bool bad = false;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) bad |= !(fabs(S[i + i * lds]) <= 1.7976931348623157e308);
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) *status = bad ? 1 : 0;
+}
+
+cudaError_t launch_diag_finite(const double* S, int k, int64_t lds, int* status, cudaStream_t st) {
+  diag_finite_kernel<<<1, 256, 0, st>>>(S, k, lds, status), count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace kscf

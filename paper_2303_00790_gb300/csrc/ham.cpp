@@ -34,7 +34,8 @@ static void free_ham(Ham& H) {
   void* ptrs[] = {H.d_nbr,           H.d_mask,         H.d_lex,          H.d_pad,
                   H.d_vion,          H.d_v64,           H.d_v32,          H.d_kb_atom_ptr,  H.d_kb_atom_slot,
                   H.d_kb_atom_chi64, H.d_kb_atom_chi32, H.d_kb_slot_ptr, H.d_kb_slot_atom,
-                  H.d_kb_slot_chi64, H.d_kb_slot_chi32, H.d_kb_energy, H.d_kb_entry_lslot};
+                  H.d_kb_slot_chi64, H.d_kb_slot_chi32, H.d_kb_energy, H.d_kb_entry_lslot,
+                  H.d_lines,         H.d_nlines,        H.d_brick_atoms, H.d_brick_natoms, H.d_kb_entry_word};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -103,6 +104,31 @@ extern "C" int kscf_build_hamiltonian(const kscf_grid* grid, const kscf_atom* at
     if (e == cudaSuccess) e = upload(&H.d_mask, g.mask.data(), g.mask.size());
     if (e == cudaSuccess) e = upload(&H.d_lex, g.lex_of_slot.data(), g.lex_of_slot.size());
     if (e == cudaSuccess) e = upload(&H.d_pad, pad.data(), pad.size());
+    if (g.B == 8 && e == cudaSuccess) {
+      // live lines per brick and pass: x lines (y, z), y lines (x, z), z lines (x, y)
+      std::vector<uint8_t> lines((size_t)g.n_bricks * 3 * 64, 0), nlines((size_t)g.n_bricks * 3, 0);
+      for (int64_t b = 0; b < g.n_bricks; b++) {
+        const uint8_t* m = g.mask.data() + b * 512;
+        for (int pass = 0; pass < 3; pass++) {
+          int n = 0;
+          for (int bb = 0; bb < 8; bb++)
+            for (int aa = 0; aa < 8; aa++) {
+              bool live = false;
+              for (int t = 0; t < 8; t++) {
+                int x, y, z;
+                if (pass == 0) { x = t; y = aa; z = bb; }
+                else if (pass == 1) { x = aa; y = t; z = bb; }
+                else { x = aa; y = bb; z = t; }
+                live |= m[(z * 8 + y) * 8 + x] != 0;
+              }
+              if (live) lines[(b * 3 + pass) * 64 + n++] = (uint8_t)(aa + 8 * bb);
+            }
+          nlines[b * 3 + pass] = (uint8_t)n;
+        }
+      }
+      e = upload(&H.d_lines, lines.data(), lines.size());
+      if (e == cudaSuccess) e = upload(&H.d_nlines, nlines.data(), nlines.size());
+    }
     if (e == cudaSuccess) e = cudaMalloc((void**)&H.d_v64, sizeof(double) * g.n_slots);
     if (e == cudaSuccess) e = cudaMalloc((void**)&H.d_v32, sizeof(float) * g.n_slots);
     if (e != cudaSuccess) {
@@ -291,6 +317,34 @@ extern "C" int kscf_build_hamiltonian(const kscf_grid* grid, const kscf_atom* at
       for (int64_t s2 = 0; s2 < g.n_slots; s2++)
         for (int64_t q = s_ptr[s2]; q < s_ptr[s2 + 1]; q++) lslot[q] = (uint16_t)(s2 % b3);
       if (e == cudaSuccess) e = upload(&H.d_kb_entry_lslot, lslot.data(), lslot.size());
+      if (g.B == 8 && e == cudaSuccess) {
+        // per-brick atom lists and packed entry words for the chunk-major filter kernels
+        const int64_t nb = g.n_bricks;
+        std::vector<int32_t> batoms((size_t)nb * KSCF_BRICK_ATOMS, -1), bnat(nb, 0);
+        std::vector<uint32_t> word(ne);
+        bool ok = true;
+        for (int64_t b = 0; b < nb; b++) {
+          for (int64_t q = s_ptr[b * 512]; q < s_ptr[(b + 1) * 512]; q++) {
+            const int32_t at = s_atom[q];
+            int li = 0;
+            while (li < bnat[b] && batoms[b * KSCF_BRICK_ATOMS + li] != at) li++;
+            if (li == bnat[b]) {
+              if (bnat[b] == KSCF_BRICK_ATOMS) {
+                ok = false;
+                li = 0;
+              } else {
+                batoms[b * KSCF_BRICK_ATOMS + li] = at;
+                bnat[b]++;
+              }
+            }
+            word[q] = (uint32_t)lslot[q] | ((uint32_t)li << 16);
+          }
+        }
+        H.brick_atoms_ok = ok;
+        if (e == cudaSuccess) e = upload(&H.d_brick_atoms, batoms.data(), batoms.size());
+        if (e == cudaSuccess) e = upload(&H.d_brick_natoms, bnat.data(), bnat.size());
+        if (e == cudaSuccess) e = upload(&H.d_kb_entry_word, word.data(), word.size());
+      }
     }
     if (e != cudaSuccess) {
       set_error("kscf_build_hamiltonian: KB upload failed: %s", cudaGetErrorString(e));

@@ -79,7 +79,19 @@ struct Ham {
   double* d_kb_energy = nullptr;      // n_kb*4: E_l * h^3
   double kb_upper = 0.0, kb_lower = 0.0;  // Gershgorin bounds of V_NL
   int max_slot_entries = 0;
+  // 8^3 bricks only (null otherwise): per brick and line pass (x, y, z) the lines holding
+  // at least one domain point, compacted (line = a + 8 b for the pass's two other axes)
+  uint8_t* d_lines = nullptr;          // n_bricks * 3 * 64
+  uint8_t* d_nlines = nullptr;         // n_bricks * 3
+  // per brick the KB atoms whose projectors reach into it (kb atom ids, at most
+  // KSCF_BRICK_ATOMS; brick_atoms_ok false when a brick has more), and per entry (slot
+  // order) the packed word  slot-in-brick | (index in its brick's atom list << 16)
+  int32_t* d_brick_atoms = nullptr;    // n_bricks * KSCF_BRICK_ATOMS, -1 padded
+  int32_t* d_brick_natoms = nullptr;   // n_bricks
+  uint32_t* d_kb_entry_word = nullptr;  // n_kb_entries
+  bool brick_atoms_ok = false;
 };
+constexpr int KSCF_BRICK_ATOMS = 32;
 
 // ---- launchers (filter.cu) ----
 cudaError_t launch_zero_rows(const Ham& H, void* X, int64_t ld, int k, int dtype, cudaStream_t st);
@@ -97,6 +109,33 @@ cudaError_t launch_cheb_step(const Ham& H, const void* in, int64_t ld_in, const 
                              double alpha, double beta, double c, const void* coef, int64_t cld,
                              cudaStream_t st);
 inline int64_t coef_ld(int w) { return (int64_t)(w + 31) / 32 * 32; }
+
+// ---- chunk-major filter path (filter_cm.cu, FP32, 8^3 bricks) ----
+// Working copies of a column block are chunk-major: element (c, s, v) at
+// buf[(c * n_slots + s) * cw + v], cw = cm_chunk_width().
+int cm_chunk_width();
+// buf = chunk-major copy of the block (padded columns zero); padding rows of buf2 zeroed
+cudaError_t launch_to_chunk_major(const Ham& H, const float* X, int64_t ld, int w, int cw, float* buf, float* buf2,
+                                  cudaStream_t st);
+// coef rows of stride cld; columns w <= v < cld are written as zero
+cudaError_t launch_kb_gather_cm(const Ham& H, const float* Y, int cw, int w, float* coef, int64_t cld,
+                                cudaStream_t st);
+// in: chunk-major; prev: chunk-major or null; out: chunk-major (out_ld < 0) or a slot-major
+// block with row stride out_ld (padding rows untouched).  check: flag NaN/Inf outputs.
+// zero: KSCF_CM_ZERO_BYTES of zeros, 256-aligned (the halo rows of missing neighbour bricks)
+cudaError_t launch_cm_step(const Ham& H, const float* in, const float* prev, float* out, int64_t out_ld, int w,
+                           double alpha, double beta, double c, const float* coef, int64_t cld, bool check,
+                           const float* zero, cudaStream_t st);
+constexpr size_t KSCF_CM_ZERO_BYTES = 512 * 16 * 4;
+// device address of the non-finite flag that kscf_check_status reports
+unsigned int* nonfinite_flag();
+// sets *flag when a domain row of X holds a NaN or Inf in its first k values
+cudaError_t launch_finite_rows(const Ham& H, const void* X, int64_t ld, int k, int dtype, unsigned int* flag,
+                               cudaStream_t st);
+// *status = 1 if a diagonal element of S is NaN or Inf, else 0
+cudaError_t launch_diag_finite(const double* S, int k, int64_t lds, int* status, cudaStream_t st);
+// device status words of the chunk-major path: a timed-out wait, non-finite output
+cudaError_t cm_status(bool reset, unsigned int* timeout, unsigned int* nonfinite);
 cudaError_t launch_copy_cols(const void* src, int64_t ld_src, void* dst, int64_t ld_dst, int64_t rows,
                              int w, int dtype, cudaStream_t st);
 

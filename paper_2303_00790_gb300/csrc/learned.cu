@@ -422,6 +422,76 @@ cudaError_t set_smem_attrs() {
   return e;
 }
 
+
+// ---- standardisation statistics: deterministic FP64 sums over kStdBlocks row ranges ----
+constexpr int kStdBlocks = 256, kStdCols = NIN + 1;   // 32 descriptor columns + the target
+
+// part[b][j] = sum over the rows of block b of (x_j - centre_j)^pw (pw = 1 or 2; column NIN
+// is the target t); centre null means 0.  Thread (j = tid % 32, g = tid / 32) takes rows
+// g, g + 8, ... of the block's range so that one warp reads whole rows.
+__global__ void __launch_bounds__(256) std_partial_kernel(const float* __restrict__ D, const float* __restrict__ t,
+                                                          int64_t n, const double* __restrict__ centre, int pw,
+                                                          double* __restrict__ part) {
+  const int j = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int64_t per = (n + kStdBlocks - 1) / kStdBlocks;
+  const int64_t r0 = (int64_t)blockIdx.x * per, r1 = min(n, r0 + per);
+  const double cj = centre ? centre[j] : 0.0, ct = centre ? centre[NIN] : 0.0;
+  double sx = 0.0, st = 0.0;
+  for (int64_t r = r0 + g; r < r1; r += 8) {
+    const double x = (double)D[r * NIN + j] - cj;
+    sx += pw == 1 ? x : x * x;
+    if (j == 0) {
+      const double y = (double)t[r] - ct;
+      st += pw == 1 ? y : y * y;
+    }
+  }
+  __shared__ double red[8][kStdCols];
+  red[g][j] = sx;
+  if (j == 0) red[g][NIN] = st;
+  __syncthreads();
+  if (threadIdx.x < kStdCols) {
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; q++) acc += red[q][threadIdx.x];
+    part[(int64_t)blockIdx.x * kStdCols + threadIdx.x] = acc;
+  }
+}
+
+// out[j] = (sum_b part[b][j]) / div in block order
+__global__ void std_finish_kernel(const double* __restrict__ part, double div, double* __restrict__ out) {
+  const int j = threadIdx.x;
+  if (j >= kStdCols) return;
+  double acc = 0.0;
+  for (int b = 0; b < kStdBlocks; b++) acc += part[(int64_t)b * kStdCols + j];
+  out[j] = acc / div;
+}
+
+// mu, inv_sd (floor 1e-6), t_shift / t_scale (1 for a constant target) from mean and variance
+__global__ void std_params_kernel(const double* __restrict__ mean, const double* __restrict__ var, float* __restrict__ mu,
+                                  float* __restrict__ inv_sd, double* __restrict__ shift_scale) {
+  const int j = threadIdx.x;
+  if (j < NIN) {
+    const double sd = sqrt(var[j]);
+    mu[j] = (float)mean[j];
+    inv_sd[j] = sd > 1e-6 ? (float)(1.0 / sd) : 0.0f;
+  } else if (j == NIN) {
+    const double sc = sqrt(var[NIN]);
+    shift_scale[0] = mean[NIN];
+    shift_scale[1] = sc > 0.0 ? sc : 1.0;
+  }
+}
+
+__global__ void std_target_kernel(const float* __restrict__ t, int64_t n, const double* __restrict__ shift_scale,
+                                  float* __restrict__ t_norm) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) t_norm[r] = (float)(((double)t[r] - shift_scale[0]) / shift_scale[1]);
+}
+
+__global__ void affine_kernel(const float* __restrict__ y, int64_t n, double scale, double shift,
+                              double* __restrict__ dv) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) dv[r] = (double)y[r] * scale + shift;
+}
 }  // namespace
 }  // namespace kscf
 
@@ -535,6 +605,53 @@ extern "C" int kscf_mlp_adam(float* params, const float* grad, float* m, float* 
   const float c2 = (float)(1.0 - std::pow((double)beta2, step));
   adam_kernel<<<(NPAR + 255) / 256, 256, 0, (cudaStream_t)stream>>>(params, grad, m, v, NPAR, lr, beta1, beta2, eps,
                                                                     c1, c2);
+  count_launch();
+  KSCF_CUDA_TRY(cudaGetLastError());
+  return KSCF_OK;
+}
+
+extern "C" int kscf_mlp_standardize(const float* D, const float* t, int64_t n, float* mu, float* inv_sd, float* t_norm,
+                                    double* t_shift_scale, void* stream) {
+  if (!D || !t || !mu || !inv_sd || !t_norm || !t_shift_scale || n < 2) {
+    set_error("kscf_mlp_standardize: invalid argument (n >= 2 rows needed)");
+    return KSCF_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double* buf = nullptr;   // partials, mean, variance, shift/scale
+  const size_t nbuf = (size_t)kStdBlocks * kStdCols + 3 * kStdCols;
+  KSCF_CUDA_TRY(cudaMalloc((void**)&buf, nbuf * sizeof(double)));
+  double* part = buf;
+  double* mean = part + (size_t)kStdBlocks * kStdCols;
+  double* var = mean + kStdCols;
+  double* ss = var + kStdCols;
+  std_partial_kernel<<<kStdBlocks, 256, 0, st>>>(D, t, n, nullptr, 1, part), count_launch();
+  std_finish_kernel<<<1, 64, 0, st>>>(part, (double)n, mean), count_launch();
+  std_partial_kernel<<<kStdBlocks, 256, 0, st>>>(D, t, n, mean, 2, part), count_launch();
+  std_finish_kernel<<<1, 64, 0, st>>>(part, (double)(n - 1), var), count_launch();
+  std_params_kernel<<<1, 64, 0, st>>>(mean, var, mu, inv_sd, ss), count_launch();
+  std_target_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(t, n, ss, t_norm), count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(t_shift_scale, ss, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (e != cudaSuccess) {
+    set_error("kscf_mlp_standardize: %s", cudaGetErrorString(e));
+    return KSCF_ERR_CUDA;
+  }
+  return KSCF_OK;
+}
+
+extern "C" int kscf_mlp_correction(const float* params, const float* mu, const float* inv_sd, double t_shift,
+                                   double t_scale, const float* D, int64_t n, int precision, float* y_work, double* dv,
+                                   void* stream) {
+  if (!dv || (n > 0 && !y_work) || !std::isfinite(t_shift) || !std::isfinite(t_scale)) {
+    set_error("kscf_mlp_correction: invalid argument");
+    return KSCF_ERR_INVALID;
+  }
+  int rc = kscf_mlp_forward(params, mu, inv_sd, D, n, precision, y_work, stream);
+  if (rc) return rc;
+  if (n == 0) return KSCF_OK;
+  affine_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(y_work, n, t_scale, t_shift, dv);
   count_launch();
   KSCF_CUDA_TRY(cudaGetLastError());
   return KSCF_OK;

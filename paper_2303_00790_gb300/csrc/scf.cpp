@@ -857,3 +857,12 @@ extern "C" int kscf_scf_get(const kscf_scf* scf, int field, double* dst) {
   KSCF_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(double) * scf->n, cudaMemcpyDeviceToDevice, scf->st));
   return KSCF_OK;
 }
+
+extern "C" int kscf_mlp_training_data(const kscf_scf* scf, const float* D_slots, float* D_out, float* t_out) {
+  if (!scf || !D_slots || !D_out || !t_out) {
+    set_error("kscf_mlp_training_data: null argument");
+    return KSCF_ERR_INVALID;
+  }
+  KSCF_CUDA_TRY(launch_training_rows(scf->ham->h, D_slots, scf->v_in, scf->v_start, D_out, t_out, scf->st));
+  return KSCF_OK;
+}

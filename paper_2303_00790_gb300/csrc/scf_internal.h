@@ -78,4 +78,8 @@ cudaError_t launch_anderson_gram(const AndersonCols& cols, const double* df, con
 cudaError_t launch_anderson_update(const Ham& H, const AndersonCols& cols, double alpha, const double* dv,
                                    const double* dpf, const double* pf, double* v, cudaStream_t st);
 
+// training data of the learned start: rows in lexicographic point order
+cudaError_t launch_training_rows(const Ham& H, const float* D, const double* v_in, const double* v_start, float* D_out,
+                                 float* t_out, cudaStream_t st);
+
 }  // namespace kscf

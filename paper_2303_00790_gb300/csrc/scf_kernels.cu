@@ -688,4 +688,28 @@ cudaError_t launch_anderson_update(const Ham& H, const AndersonCols& cols, doubl
   return cudaGetLastError();
 }
 
+// row lex(s) of D_out / t_out for every domain slot s: the slot's descriptors and
+// dV = V_in - V_start (training data of the learned start)
+__global__ void training_rows_kernel(const float* __restrict__ D, const double* __restrict__ v_in,
+                                     const double* __restrict__ v_start, const int64_t* __restrict__ lex,
+                                     int64_t n_slots, float* __restrict__ D_out, float* __restrict__ t_out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t s = t >> 5;
+  const int j = (int)(t & 31);
+  if (s >= n_slots) return;
+  const int64_t p = lex[s];
+  if (p < 0) return;
+  D_out[p * KSCF_MLP_N_IN + j] = D[s * KSCF_MLP_N_IN + j];
+  if (j == 0) t_out[p] = (float)(v_in[s] - v_start[s]);
+}
+
+cudaError_t launch_training_rows(const Ham& H, const float* D, const double* v_in, const double* v_start, float* D_out,
+                                 float* t_out, cudaStream_t st) {
+  const int64_t n = H.grid.n_slots * 32;
+  training_rows_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(D, v_in, v_start, H.d_lex, H.grid.n_slots, D_out,
+                                                                     t_out);
+  count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace kscf

@@ -134,6 +134,9 @@ _sigs = {
                             _i32),
     "kscf_dos": ([_vp, _i32, _i32, _d, _d, _i32, _vp, C.POINTER(_d)], _i32),
     "kscf_mlp_adam": ([_vp, _vp, _vp, _vp, _i32, C.c_float, C.c_float, C.c_float, C.c_float, _vp], _i32),
+    "kscf_mlp_training_data": ([_vp, _vp, _vp, _vp], _i32),
+    "kscf_mlp_standardize": ([_vp, _vp, _i64, _vp, _vp, _vp, C.POINTER(_d), _vp], _i32),
+    "kscf_mlp_correction": ([_vp, _vp, _vp, _d, _d, _vp, _i64, _i32, _vp, _vp, _vp], _i32),
 }
 for _name, (_args, _res) in _sigs.items():
     _f = getattr(lib, _name)
@@ -606,6 +609,41 @@ def kscf_mlp_forward(params, mu, inv_sd, D, precision: int = KSCF_MLP_FP32, y=No
         y = torch.empty(n, dtype=torch.float32, device="cuda")
     _check(lib.kscf_mlp_forward(_p(params), _p(mu), _p(inv_sd), _p(D), n, precision, _p(y), _stream(stream)))
     return y
+
+
+def kscf_mlp_training_data(scf, D_slots, n_points: int):
+    """(D, t): descriptors and dV = V_in - V_start of the domain points (lexicographic
+    rows, float32 device tensors) of a self-consistent SCF handle."""
+    torch = _torch()
+    D = torch.empty((n_points, KSCF_MLP_N_IN), dtype=torch.float32, device="cuda")
+    t = torch.empty(n_points, dtype=torch.float32, device="cuda")
+    _check(lib.kscf_mlp_training_data(scf.handle, _p(D_slots), _p(D), _p(t)))
+    return D, t
+
+
+def kscf_mlp_standardize(D, t, stream=None):
+    """(mu, inv_sd, t_norm, t_shift, t_scale) of a training set (synchronous)."""
+    torch = _torch()
+    n = D.shape[0]
+    mu = torch.empty(KSCF_MLP_N_IN, dtype=torch.float32, device="cuda")
+    inv_sd = torch.empty_like(mu)
+    t_norm = torch.empty(n, dtype=torch.float32, device="cuda")
+    ss = (C.c_double * 2)()
+    _check(lib.kscf_mlp_standardize(_p(D), _p(t), n, _p(mu), _p(inv_sd), _p(t_norm), ss, _stream(stream)))
+    return mu, inv_sd, t_norm, ss[0], ss[1]
+
+
+def kscf_mlp_correction(params, mu, inv_sd, t_shift: float, t_scale: float, D, precision: int = KSCF_MLP_FP32,
+                        dv=None, stream=None):
+    """dV per row of D (float64 device tensor): the network output de-standardised."""
+    torch = _torch()
+    n = D.shape[0]
+    if dv is None:
+        dv = torch.empty(n, dtype=torch.float64, device="cuda")
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    _check(lib.kscf_mlp_correction(_p(params), _p(mu), _p(inv_sd), float(t_shift), float(t_scale), _p(D), n,
+                                   precision, _p(y), _p(dv), _stream(stream)))
+    return dv
 
 
 def kscf_mlp_work_size(n: int) -> int:

@@ -2,8 +2,9 @@
 kernels on the GPU, and the predicted correction of the superposition starting potential.
 
 Host orchestration only (which clusters, which batches, when to stop); the descriptors,
-the network's forward and backward passes, the optimiser and every SCF step run in
-libkscf's kernels through the C ABI.  The target of the network is
+the training targets, the standardisation, the network's forward and backward passes,
+the de-standardised correction, the optimiser and every SCF step run in libkscf's
+kernels through the C ABI.  The target of the network is
     dV = V_in(converged) - V_start(superposition of neutral atoms)
 on the domain points, standardised by its mean and standard deviation; the inputs are
 the 32 radial descriptors standardised per feature over the training set.
@@ -43,8 +44,7 @@ class LearnedStart:
     def correction(self, ham, atom_pos, atom_z, precision: int = kscf.KSCF_MLP_BF16):
         """dV per slot (torch float64, device) for kscf_scf_start."""
         D = kscf.kscf_descriptors(ham, atom_pos, atom_z)
-        y = kscf.kscf_mlp_forward(self.params, self.mu, self.inv_sd, D, precision)
-        return y.double() * self.t_scale + self.t_shift
+        return kscf.kscf_mlp_correction(self.params, self.mu, self.inv_sd, self.t_shift, self.t_scale, D, precision)
 
     def state(self) -> dict:
         return {"params": self.params.cpu().numpy(), "mu": self.mu.cpu().numpy(),
@@ -130,26 +130,17 @@ def sample_cluster(pos, z, species, cfg: dict, seed: int = 1, **scf_kw):
         ex["scf"].free()
         return None, None, {"steps": len(reps), "wall_s": wall, "converged": False}
     g, H, S = ex["grid"], ex["ham"], ex["scf"]
-    lex, _ = g.slots()
-    live = torch.tensor(lex >= 0, device="cuda")
-    v_in = S.get(kscf.KSCF_FIELD_V_IN)
-    v_start = S.get(kscf.KSCF_FIELD_V_START)
-    D = kscf.kscf_descriptors(H, pos, z)
+    D, t = kscf.kscf_mlp_training_data(S, kscf.kscf_descriptors(H, pos, z), g.info["n_points"])
+    torch.cuda.synchronize()
     S.free()
-    return (D[live].contiguous(), (v_in - v_start)[live].float().contiguous(),
-            {"steps": len(reps), "wall_s": wall, "converged": True, "sre_ry": reps[-1]["sre_ry"]})
+    return D, t, {"steps": len(reps), "wall_s": wall, "converged": True, "sre_ry": reps[-1]["sre_ry"]}
 
 
 def train(D, T, steps: int = 3000, batch: int = 16384, lr: float = 2e-3, seed: int = 0, log_every: int = 0):
     """Fits the network to (D, T) (device float32; T raw dV) with Adam on random batches.
     Returns (LearnedStart, losses)."""
     import torch
-    mu = D.mean(0)
-    sd = D.std(0)
-    inv_sd = torch.where(sd > 1e-6, 1.0 / sd, torch.zeros_like(sd)).contiguous()
-    t_shift = float(T.mean().item())
-    t_scale = float(T.std().item()) or 1.0
-    Tn = ((T - t_shift) / t_scale).contiguous()
+    mu, inv_sd, Tn, t_shift, t_scale = kscf.kscf_mlp_standardize(D, T)
     P = torch.tensor(glorot_params(seed), device="cuda")
     m = torch.zeros_like(P)
     v = torch.zeros_like(P)
@@ -173,7 +164,7 @@ def train(D, T, steps: int = 3000, batch: int = 16384, lr: float = 2e-3, seed: i
         kscf.kscf_mlp_adam(P, g, m, v, it, max(lr_t, 1e-6))
         if log_every and (it % log_every == 0 or it == steps):
             losses.append((it, float(loss.item())))
-    return LearnedStart(P, mu.contiguous(), inv_sd, t_shift, t_scale), losses
+    return LearnedStart(P, mu, inv_sd, t_shift, t_scale), losses
 
 
 def steps_to_energy(reports, e_ref: float, n_atoms: int, tol_per_atom: float = 1e-6) -> int:

@@ -106,6 +106,57 @@ def test_adam_matches_oracle(kscf):
     assert np.max(np.abs(P.cpu().numpy() - params["a"])) < 1e-6
 
 
+def test_standardize_matches_oracle(kscf):
+    """FP64 sums of FP32 inputs: mu, inv_sd and the target statistics to ~1e-12 relative
+    before the rounding of the stored FP32 values (half an ulp, 6e-8)."""
+    from oracle import learned as L
+    rng = np.random.default_rng(12)
+    n = 10007
+    D = rng.uniform(0, 3, (n, 32)).astype(np.float32)
+    D[:, 11] = 0.5                       # constant feature: switched off
+    t = (0.2 * rng.standard_normal(n) - 0.05).astype(np.float32)
+    mu, isd, tn, ts, sc = kscf.kscf_mlp_standardize(torch.tensor(D, device="cuda"), torch.tensor(t, device="cuda"))
+    rmu, risd, rts, rsc, rtn = L.standardise(D.astype(np.float64), t.astype(np.float64))
+    assert np.allclose(mu.cpu().numpy(), rmu, rtol=1e-7, atol=0)
+    assert np.allclose(isd.cpu().numpy(), risd, rtol=1e-7, atol=0) and isd[11].item() == 0.0
+    assert abs(ts - rts) < 1e-12 * abs(rsc) and abs(sc - rsc) < 1e-12 * rsc
+    assert np.allclose(tn.cpu().numpy(), rtn, rtol=0, atol=1e-6)
+
+
+def test_correction_and_training_data_match_oracle(kscf, species):
+    """kscf_mlp_correction = the oracle's de-standardised network (FP32 forward tolerance
+    times t_scale); kscf_mlp_training_data = descriptors and V_in - V_start of the domain
+    points, in lexicographic order."""
+    from oracle import learned as L
+    p = random_net(8)
+    rng = np.random.default_rng(2)
+    D = rng.uniform(0, 2, (777, 32))
+    mu, isd = D.mean(0), 1.0 / D.std(0)
+    P = torch.tensor(L.pack(p), dtype=torch.float32, device="cuda")
+    dv = kscf.kscf_mlp_correction(P, torch.tensor(mu, dtype=torch.float32, device="cuda"),
+                                  torch.tensor(isd, dtype=torch.float32, device="cuda"), 0.37, 2.5,
+                                  torch.tensor(D, dtype=torch.float32, device="cuda"))
+    ref = L.correction(p, mu.astype(np.float32).astype(np.float64), isd.astype(np.float32).astype(np.float64),
+                       0.37, 2.5, D.astype(np.float32).astype(np.float64))
+    assert dv.dtype == torch.float64 and np.max(np.abs(dv.cpu().numpy() - ref)) < 5e-5 * 2.5
+    # training data of a (not yet self-consistent) SCF state: the definition on the host
+    pos, z = small_cluster()
+    g, H = kscf.build_cluster(pos, z, species, 9.0, 0.7)
+    S = kscf.Scf(H, pos, z, species, kscf.scf_params(8, 8))
+    S.start(seed=1)
+    S.step()
+    Ds = kscf.kscf_descriptors(H, pos, z)
+    Dp, tp = kscf.kscf_mlp_training_data(S, Ds, g.info["n_points"])
+    torch.cuda.synchronize()
+    lex, _ = g.slots()
+    n = g.info["n_points"]
+    want_t = L.training_target(from_slots(S.get(kscf.KSCF_FIELD_V_IN).cpu().numpy(), lex, n),
+                               from_slots(S.get(kscf.KSCF_FIELD_V_START).cpu().numpy(), lex, n))
+    assert np.array_equal(Dp.cpu().numpy(), from_slots(Ds.cpu().numpy(), lex, n))
+    assert np.array_equal(tp.cpu().numpy(), want_t.astype(np.float32))
+    S.free()
+
+
 def test_training_fits_a_smooth_target(kscf):
     from paper_2303_00790_gb300 import learned
     rng = np.random.default_rng(0)
@@ -114,7 +165,7 @@ def test_training_fits_a_smooth_target(kscf):
     model, losses = learned.train(D, T, steps=600, batch=4096, lr=3e-3, log_every=100)
     # standardised target: the initial loss is ~1; the fit explains > 99 % of the variance
     assert losses[-1][1] < 0.01, losses
-    pred = kscf.kscf_mlp_forward(model.params, model.mu, model.inv_sd, D) * model.t_scale + model.t_shift
+    pred = kscf.kscf_mlp_correction(model.params, model.mu, model.inv_sd, model.t_shift, model.t_scale, D)
     r2 = 1.0 - torch.mean((pred - T) ** 2).item() / torch.var(T).item()
     assert r2 > 0.99, r2
 

@@ -397,3 +397,69 @@ def test_tensor_rayleigh_ritz_is_stable_on_ritz_vectors(kscf, species):
     d = torch.max(torch.abs(X - X1), dim=0).values.cpu().numpy()
     scale = torch.max(torch.abs(X1)).item()
     assert np.max(d[sep]) < 1e-4 * scale, np.max(d[sep]) / scale
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_nonfinite_inputs_are_reported(kscf, system, dtype):
+    """A NaN put into X (or into the potential) on the host: the filter and the apply
+    flag it on the device and kscf_check_status returns KSCF_ERR_NONFINITE, the Cholesky-QR
+    returns it directly, and the context stays usable (a clean filter afterwards)."""
+    from workloads import random_block_lex
+    H, lex = system["H"], system["lex"]
+    if dtype == torch.float64 or system["brick"] != 8:
+        pytest.skip("the device-side flag covers the FP32 brick filter; the other paths are checked below")
+    k = 12
+    X0 = to_slots(random_block_lex(8, system["n"], k), lex)
+    live = np.nonzero(lex >= 0)[0]
+    _, b = kscf.kscf_spectral_bounds(H)
+    assert kscf.lib.kscf_check_status() == kscf.KSCF_OK
+    # NaN in X: filter
+    Xn = X0.copy()
+    Xn[live[len(live) // 2], 3] = np.nan
+    Xd = dev(Xn, dtype)
+    kscf.kscf_chebyshev_filter(H, Xd, 5, -0.5, b, -9.0)
+    torch.cuda.synchronize()
+    assert kscf.lib.kscf_check_status() == kscf.KSCF_ERR_NONFINITE
+    assert kscf.lib.kscf_check_status() == kscf.KSCF_OK          # the flag is cleared once reported
+    with pytest.raises(kscf.KscfError) as e:
+        kscf.kscf_orthonormalize(H, Xd)
+    assert e.value.code == kscf.KSCF_ERR_NONFINITE
+    # NaN in Y: apply
+    Yd = dev(Xn, dtype)
+    kscf.kscf_hamiltonian_apply(H, Yd, torch.empty_like(Yd))
+    torch.cuda.synchronize()
+    assert kscf.lib.kscf_check_status() == kscf.KSCF_ERR_NONFINITE
+    # NaN in the potential: filter of a clean block
+    V = kscf.kscf_get_potential(H)
+    Vn = V.clone()
+    Vn[int(live[7])] = float("inf")
+    kscf.kscf_set_potential(H, Vn)
+    try:
+        Xd = dev(X0, dtype)
+        kscf.kscf_chebyshev_filter(H, Xd, 5, -0.5, b, -9.0)
+        torch.cuda.synchronize()
+        assert kscf.lib.kscf_check_status() == kscf.KSCF_ERR_NONFINITE
+    finally:
+        kscf.kscf_set_potential(H, V)
+    # clean again: no flag, finite result
+    Xd = dev(X0, dtype)
+    kscf.kscf_chebyshev_filter(H, Xd, 5, -0.5, b, -9.0)
+    torch.cuda.synchronize()
+    assert kscf.lib.kscf_check_status() == kscf.KSCF_OK
+    assert torch.isfinite(Xd).all()
+
+
+def test_nonfinite_f64_orthonormalize_and_apply(kscf, system):
+    """FP64: the apply's output check and the Cholesky-QR Gram check report a NaN too."""
+    from workloads import random_block_lex
+    H, lex = system["H"], system["lex"]
+    X = to_slots(random_block_lex(9, system["n"], 6), lex)
+    X[np.nonzero(lex >= 0)[0][3], 2] = np.nan
+    Xd = dev(X)
+    kscf.kscf_hamiltonian_apply(H, Xd, torch.empty_like(Xd))
+    torch.cuda.synchronize()
+    assert kscf.lib.kscf_check_status() == kscf.KSCF_ERR_NONFINITE
+    with pytest.raises(kscf.KscfError) as e:
+        kscf.kscf_orthonormalize(H, Xd)
+    assert e.value.code == kscf.KSCF_ERR_NONFINITE
+    assert kscf.lib.kscf_check_status() == kscf.KSCF_OK

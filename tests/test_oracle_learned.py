@@ -111,3 +111,37 @@ def test_adam_first_step_is_signed_learning_rate():
     p, m, v = L.adam_step(p, g, m, v, 1, lr=0.01)
     # m_hat = g, v_hat = g^2: the step is lr * g / (|g| + eps)
     assert np.allclose(p["a"], [1.0 - 0.01 * 0.5 / (0.5 + 1e-8), -2.0 + 0.01 * 4.0 / (4.0 + 1e-8), 3.0], atol=1e-15)
+
+
+def test_standardise_closed_form_and_invariants():
+    """Two rows (0, 2) give mean 1 and unbiased sd sqrt(2); a constant feature gets
+    inv_sd 0; the standardised set has mean 0 and unbiased variance 1 per live feature; a
+    biased (1/n) variance or a missing floor fails."""
+    D = np.zeros((2, 32))
+    D[:, 0] = [0.0, 2.0]
+    D[:, 1] = 5.0
+    mu, inv_sd, ts, sc, tn = L.standardise(D, np.array([1.0, 3.0]))
+    assert mu[0] == 1.0 and abs(inv_sd[0] - 1.0 / math.sqrt(2.0)) < 1e-15 and inv_sd[1] == 0.0
+    assert ts == 2.0 and abs(sc - math.sqrt(2.0)) < 1e-15
+    assert np.allclose(tn, [-1.0 / math.sqrt(2.0), 1.0 / math.sqrt(2.0)], atol=1e-15)
+    rng = np.random.default_rng(4)
+    D = rng.uniform(0, 3, (500, 32))
+    D[:, 7] = 0.25
+    t = rng.standard_normal(500) * 0.3 + 0.1
+    mu, inv_sd, ts, sc, tn = L.standardise(D, t)
+    X = (D - mu) * inv_sd
+    live = np.arange(32) != 7
+    assert np.allclose(X[:, live].mean(0), 0.0, atol=1e-12) and np.allclose(X[:, live].var(0, ddof=1), 1.0)
+    assert np.all(X[:, 7] == 0) and abs(tn.mean()) < 1e-12 and abs(tn.var(ddof=1) - 1.0) < 1e-12
+    # constant target: scale 1
+    assert L.standardise(D, np.full(500, 0.4))[3] == 1.0
+
+
+def test_correction_is_affine_in_the_network_output():
+    p = L.init_params(2)
+    rng = np.random.default_rng(6)
+    D = rng.uniform(0, 2, (9, 32))
+    mu, inv_sd = D.mean(0), np.full(32, 0.7)
+    y, _ = L.forward(p, (D - mu) * inv_sd)
+    assert np.allclose(L.correction(p, mu, inv_sd, 0.3, 2.5, D), 2.5 * y + 0.3, rtol=0, atol=1e-14)
+    assert np.array_equal(L.training_target([1.0, 2.0], [0.5, 3.0]), [0.5, -1.0])
