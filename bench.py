@@ -50,8 +50,14 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-scf", action="store_true", help="skip the SCF wall-time comparison (mixed vs FP64)")
+    p.add_argument("--scf-only", action="store_true", help="only the SCF comparison (mixed vs FP64, vs the oracle)")
+    p.add_argument("--scf-refine-fp64", action="store_true",
+                   help="also run the converged mode of the FP64 SCF against the oracle (minutes at 2.2 nm)")
     p.add_argument("--scf-workload", default="si353h196")
     p.add_argument("--scf-max-steps", type=int, default=80)
+    p.add_argument("--scf-radius-rule", default="nominal", choices=["nominal", "atoms"],
+                   help="SCF domain radius: nominal diameter / 2 + 6 bohr (default), or the largest "
+                        "distance of an atom from the centre + 6 bohr")
     p.add_argument("--gap-study", action="store_true",
                    help="HOMO-LUMO gap and DOS (0.1 eV bins) vs cluster diameter from converged SCF runs")
     p.add_argument("--learned-full", action="store_true",
@@ -264,8 +270,16 @@ def run_scf_pair(args):
     w = workload(args.scf_workload)
     pos, z = w.atoms()
     species = pseudo_params()
-    grid, H = kscf.build_cluster(pos, z, species, w.radius, w.h, brick=args.brick)
+    radius = w.radius
+    if args.scf_radius_rule == "atoms":
+        radius = float(np.max(np.linalg.norm(pos - pos[0], axis=1))) + w.margin
+    grid, H = kscf.build_cluster(pos, z, species, radius, w.h, brick=args.brick)
     h3 = grid.info["h"] ** 3
+    gpath = os.path.join(ROOT, "tests", "golden", f"{w.name}_scf.json")
+    golden = None
+    if os.path.exists(gpath) and args.scf_radius_rule == "nominal":
+        with open(gpath) as f:
+            golden = json.load(f)
     runs = {}
     rhos = {}
     variants = (("mixed", kscf.KSCF_F32, kscf.KSCF_GEMM_TENSOR, w.block),
@@ -286,6 +300,13 @@ def run_scf_pair(args):
                       "sre_ry": reps[-1]["sre_ry"], "e_total": ev["e_total"], "homo": ev["homo"], "lumo": ev["lumo"],
                       "gap": ev["lumo"] - ev["homo"], "max_resid_occ": float(np.max(ev["resid"][:len(lam)])),
                       "poisson_iters": int(sum(r["poisson_iters"] for r in reps)), "_lam": lam}
+        # converged mode at the final potential, compared with the oracle's (golden file)
+        if golden is not None and (name == "mixed" or args.scf_refine_fp64):
+            t1 = time.perf_counter()
+            rf = S.refine(80, golden["converged"]["resid_tol_ha"])
+            torch.cuda.synchronize()
+            runs[name]["converged_mode"] = compare_golden(golden, rf, S.get(kscf.KSCF_FIELD_RHO), grid, len(z),
+                                                          time.perf_counter() - t1)
         S.free()
         del S
         torch.cuda.empty_cache()
@@ -297,10 +318,53 @@ def run_scf_pair(args):
            "rho_l1_electrons": float(h3 * torch.sum(torch.abs(rhos["mixed"] - rhos["fp64"])).item())}
     for r in runs.values():
         r.pop("_lam")
-    return {"workload": w.name, "n_points": grid.info["n_points"], "n_atoms": len(z), "k": w.k, "degree": w.degree,
+    return {"workload": w.name, "radius_bohr": radius, "radius_rule": args.scf_radius_rule,
+            "n_points": grid.info["n_points"], "n_atoms": len(z), "k": w.k, "degree": w.degree,
             "sre_tol_ry": 1e-4, "mixing": "Anderson alpha 0.3 history 8", "chefsi_schedule": "4 then 1",
             "wall": "host clock around start + steps + final FP64 evaluation, synchronised",
             "mixed": a, "fp64": b, "speedup_fp64_over_mixed": b["wall_s"] / a["wall_s"], "mixed_vs_fp64": err}
+
+
+def compare_golden(golden, rf, rho_slots, grid, n_atoms, seconds):
+    """Errors of a converged-mode GPU result against the oracle's stored one: Ritz values of
+    the occupied states and the LUMO, HOMO-LUMO gap, total energy per atom, and the density
+    through its stored moments (charge, dipole, quadrupole, 1-bohr shell charges, values at
+    the sampled points)."""
+    gc = golden["converged"]
+    nocc = golden["n_occ"]
+    order = np.argsort(rf["lam"])
+    lam = rf["lam"][order]
+    ref = np.asarray(gc["lam"])
+    lex, ijk_s = grid.slots()
+    live = lex >= 0
+    n = grid.info["n_points"]
+    rho = np.zeros(n)
+    ijk = np.zeros((n, 3))
+    rho[lex[live]] = rho_slots.cpu().numpy()[live]
+    ijk[lex[live]] = ijk_s[live]
+    h = grid.info["h"]
+    h3 = h ** 3
+    x = h * ijk
+    r2 = (x * x).sum(1)
+    gr = gc["rho"]
+    quad = h3 * (3.0 * np.einsum("n,ni,nj->ij", rho, x, x) - np.eye(3) * (rho * r2).sum())
+    quad6 = np.array([quad[0, 0], quad[1, 1], quad[2, 2], quad[0, 1], quad[0, 2], quad[1, 2]])
+    shells = np.bincount(np.floor(np.sqrt(r2)).astype(np.int64), weights=rho,
+                         minlength=len(gr["shell_charge_1bohr"])) * h3
+    idx = np.asarray(gr["sample_index_lex"])
+    sample = np.asarray(gr["sample_rho"])
+    return {"iters": rf["iters"], "seconds": seconds,
+            "max_resid_wanted_ha": float(np.max(rf["resid"][order[:nocc + 1]])),
+            "eig_occ_lumo_max_err_ha": float(np.max(np.abs(lam[:nocc + 1] - ref[:nocc + 1]))),
+            "gap": float(lam[nocc] - lam[nocc - 1]),
+            "gap_err_ha": abs(float(lam[nocc] - lam[nocc - 1]) - gc["gap"]),
+            "e_total": rf["e_total"], "e_total_err_per_atom_ha": abs(rf["e_total"] - gc["e_total"]) / n_atoms,
+            "rho_charge_err": abs(h3 * rho.sum() - gr["charge"]),
+            "rho_dipole_err": float(np.max(np.abs(h3 * (rho[:, None] * x).sum(0) - np.asarray(gr["dipole"])))),
+            "rho_quadrupole_err": float(np.max(np.abs(quad6 - np.asarray(gr["quadrupole"])))),
+            "rho_shell_max_err": float(np.max(np.abs(shells[:len(gr["shell_charge_1bohr"])]
+                                                     - np.asarray(gr["shell_charge_1bohr"])))),
+            "rho_sample_max_rel_err": float(np.max(np.abs(rho[idx] - sample)) / np.max(np.abs(sample)))}
 
 
 # ------------------------------------------------------------------ learned start
@@ -650,6 +714,9 @@ def main():
     args = parse()
     if args.filter_sweep:
         run_filter_sweep(args)
+        return
+    if args.scf_only:
+        print(json.dumps({"scf": run_scf_pair(args)}), flush=True)
         return
     if args.gap_study:
         run_gap_study(args)

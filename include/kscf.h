@@ -453,6 +453,19 @@ int kscf_scf_step(kscf_scf* scf, kscf_scf_report* report, double* eigvals_host);
  * and leaves the Hamiltonian at that V_in.  Synchronous. */
 int kscf_scf_evaluate(kscf_scf* scf, kscf_scf_report* report, double* eigvals_host, double* resid_host);
 
+/* Converged mode at the current input potential V_in (normally after the SCF has met
+ * its SRE criterion, when V_in is the last step's potential): CheFSI iterations (filter,
+ * Cholesky-QR, Rayleigh-Ritz, in the SCF's precision) at fixed potential until every
+ * wanted state -- the occupied ones and the first empty one -- has FP64 residual norm
+ * |H x - lambda x| below resid_tol (Ha), or the residuals stop falling for three
+ * iterations (the working precision's floor), or max_iters iterations.  Then the density
+ * of the refined vectors, its Hartree and exchange-correlation terms and the energy at
+ * the same V_in are recomputed, and the result is reported as kscf_scf_evaluate does
+ * (FP64 Rayleigh quotients, residuals, e_total).  iters_done (or NULL): iterations run.
+ * V_in is not changed.  Synchronous; allocates like kscf_scf_evaluate. */
+int kscf_scf_refine(kscf_scf* scf, int max_iters, double resid_tol, kscf_scf_report* report, double* eigvals_host,
+                    double* resid_host, int* iters_done);
+
 /* Fields for kscf_scf_get (device, n_slots doubles each, slot order, 0 in padding). */
 #define KSCF_FIELD_RHO     0   /* density of the last step (start: rho_0) */
 #define KSCF_FIELD_V_IN    1   /* current input potential (after mixing) */

@@ -264,6 +264,35 @@ def group_degrees(lam, r, a, b, tol, m_min, m_max, group):
     return [int(m[g:g + group].max()) for g in range(0, len(lam), group)]
 
 
+def total_energy(h3, e_band, rho, v_in, v_ion, vh, eps, minus_ts=0.0):
+    """E = sum_i f_i lambda_i - h^3 sum rho (V_in - V_ion) + 1/2 h^3 sum rho V_H + h^3 sum rho eps_xc
+    (- T S): the band energy with the double-counted Hartree and exchange-correlation
+    terms removed (no ion-ion term)."""
+    return (e_band - h3 * float(np.dot(rho, v_in - v_ion)) + 0.5 * h3 * float(np.dot(rho, vh))
+            + h3 * float(np.dot(rho, eps)) + minus_ts)
+
+
+def converged_mode(res, atom_pos, atom_z, species, degree, tol=1e-7, max_iter=400):
+    """Fixed-potential CheFSI at the SCF's last input potential until the occupied states and
+    the first empty one have residual norm < tol, then the energy of the converged orbitals:
+    (lam, X, rho, e_total, iters).  kT = 0 occupations."""
+    from .potential import kb_projectors, local_potential
+    from workloads.cluster import n_electrons
+    g = res["grid"]
+    ne = n_electrons(atom_z)
+    nocc = ne // 2
+    v_ion = local_potential(g.points(), atom_pos, atom_z, species)
+    P, E, _ = kb_projectors(g, atom_pos, atom_z, species)
+    H = Hamiltonian(g, res["v_in"], P, E)
+    conv = cf.chefsi_converged(H, res["X"], degree, nocc + 1, tol=tol, max_iter=max_iter)
+    occ, _, minus_ts = occupations(conv["lam"], ne, 0.0)
+    rho = cf.density(conv["X"], occ)
+    vh = Poisson(g).solve(rho)
+    eps, _ = lda_xc(rho)
+    e = total_energy(H.h3, float(np.dot(occ, conv["lam"])), rho, res["v_in"], v_ion, vh, eps, minus_ts)
+    return {"lam": conv["lam"], "X": conv["X"], "rho": rho, "e_total": e, "iters": conv["iters"], "res": conv["res"]}
+
+
 def scf(atom_pos, atom_z, species, radius, h, k, degree, X0, max_steps=40, sre_tol_ry=1e-4,
         first_iters=4, alpha=0.3, history=8, center=None, kT=0.0, kerker_q0=0.0, degree_min=0,
         degree_max=0, reduction=0.1, tol_floor=1e-6, group=64):
@@ -320,8 +349,7 @@ def scf(atom_pos, atom_z, species, radius, h, k, degree, X0, max_steps=40, sre_t
         f = v_out - v_in
         sre = 2.0 * math.sqrt(H.h3 * float(np.sum(rho * f * f)))
         e_band = float(np.dot(occ, lam))
-        e_tot = (e_band - H.h3 * float(np.dot(rho, v_in - v_ion)) + 0.5 * H.h3 * float(np.dot(rho, vh))
-                 + H.h3 * float(np.dot(rho, eps)) + minus_ts)
+        e_tot = total_energy(H.h3, e_band, rho, v_in, v_ion, vh, eps, minus_ts)
         reports.append({"step": step, "sre_ry": sre, "e_band": e_band, "e_total": e_tot, "mu": mu,
                         "filter_work": work,
                         "minus_ts": minus_ts,

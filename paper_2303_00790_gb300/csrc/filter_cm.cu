@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
                                                         const uint8_t* __restrict__ nlines,
                                                         const int32_t* __restrict__ batoms,
                                                         const int32_t* __restrict__ bnat,
-                                                        const uint32_t* __restrict__ eword) {
+                                                        const uint32_t* __restrict__ eword,
+                                                        const float* __restrict__ zero) {
   extern __shared__ __align__(16) uint8_t smw[];
   float4* core4 = (float4*)(smw + LDG_CORE);   // [512][4]
   float4* acc4 = (float4*)(smw + LDG_ACC);     // [512][4]
@@ -155,13 +156,11 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
   const int64_t b0 = (int64_t)brick * 512;
   const float* inc = a.in + (int64_t)c * a.n_slots * 16 + vl;   // row stride 16 floats
   const float* own = inc + b0 * 16;
-  const float* nbp[6];
-  bool nbv[6];
+  const float* nbp[6];   // a missing neighbour reads the zero brick
 #pragma unroll
   for (int f = 0; f < 6; f++) {
     const int q = __ldg(a.nbr + (int64_t)brick * 6 + f);
-    nbv[f] = q >= 0;
-    nbp[f] = q >= 0 ? inc + (int64_t)q * 512 * 16 : own;
+    nbp[f] = q >= 0 ? inc + (int64_t)q * 512 * 16 : zero + vl;
   }
   const uint8_t* bl = lines + (int64_t)brick * 192;
   const int nlx = __ldg(nlines + brick * 3), nly = __ldg(nlines + brick * 3 + 1), nlz = __ldg(nlines + brick * 3 + 2);
@@ -219,10 +218,8 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
     if (lx >= 0) {
 #pragma unroll
       for (int xx = 0; xx < 6; xx++) {
-        const float4 m = ld4(nbp[0] + rb + (2 + xx) * 16);
-        const float4 p = ld4(nbp[1] + rb + xx * 16);
-        w[xx] = nbv[0] ? m : z4;
-        w[14 + xx] = nbv[1] ? p : z4;
+        w[xx] = ld4(nbp[0] + rb + (2 + xx) * 16);
+        w[14 + xx] = ld4(nbp[1] + rb + xx * 16);
       }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -241,10 +238,8 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
     if (ly >= 0) {
 #pragma unroll
       for (int yy = 0; yy < 6; yy++) {
-        const float4 m = ld4(nbp[2] + ((z * 8 + 2 + yy) * 8 + x) * 16);
-        const float4 p = ld4(nbp[3] + ((z * 8 + yy) * 8 + x) * 16);
-        w[yy] = nbv[2] ? m : z4;
-        w[14 + yy] = nbv[3] ? p : z4;
+        w[yy] = ld4(nbp[2] + ((z * 8 + 2 + yy) * 8 + x) * 16);
+        w[14 + yy] = ld4(nbp[3] + ((z * 8 + yy) * 8 + x) * 16);
       }
 #pragma unroll
       for (int y = 0; y < 8; y++) w[6 + y] = core4[sl(x, y, z) * 4 + vp];
@@ -301,10 +296,8 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
     if (lz >= 0) {
 #pragma unroll
       for (int zz = 0; zz < 6; zz++) {
-        const float4 m = ld4(nbp[4] + ((2 + zz) * 64 + y * 8 + x) * 16);
-        const float4 p = ld4(nbp[5] + (zz * 64 + y * 8 + x) * 16);
-        w[zz] = nbv[4] ? m : z4;
-        w[14 + zz] = nbv[5] ? p : z4;
+        w[zz] = ld4(nbp[4] + ((2 + zz) * 64 + y * 8 + x) * 16);
+        w[14 + zz] = ld4(nbp[5] + (zz * 64 + y * 8 + x) * 16);
       }
 #pragma unroll
       for (int z = 0; z < 8; z++) w[6 + z] = core4[sl(x, y, z) * 4 + vp];
@@ -480,10 +473,10 @@ cudaError_t launch_cm_step(const Ham& H, const float* in, const float* prev, flo
     }
     if (H.brick_atoms_ok)
       cm_step_ldg16<true><<<grid, 256, LDG_SMEM, st>>>(a, H.d_lines, H.d_nlines, H.d_brick_atoms, H.d_brick_natoms,
-                                                       H.d_kb_entry_word), count_launch();
+                                                       H.d_kb_entry_word, zero), count_launch();
     else
       cm_step_ldg16<false><<<grid, 256, LDG_SMEM, st>>>(a, H.d_lines, H.d_nlines, H.d_brick_atoms,
-                                                        H.d_brick_natoms, H.d_kb_entry_word), count_launch();
+                                                        H.d_brick_natoms, H.d_kb_entry_word, zero), count_launch();
   }
   return cudaGetLastError();
 }

@@ -596,6 +596,9 @@ extern "C" int kscf_scf_start(kscf_scf* scf, const double* dv_start, int init_x,
   return KSCF_OK;
 }
 
+int density_energy(kscf_scf* S, kscf_scf_report* report);
+int mix(kscf_scf* S, kscf_scf_report* report);
+
 extern "C" int kscf_scf_step(kscf_scf* scf, kscf_scf_report* report, double* eigvals_host) {
   if (!scf || !report) {
     set_error("kscf_scf_step: null argument");
@@ -637,7 +640,26 @@ extern "C" int kscf_scf_step(kscf_scf* scf, kscf_scf_report* report, double* eig
   if (rc) return rc;
   report->chefsi_iters = iters;
 
-  // occupations and the output density of the normalised Ritz vectors
+  rc = density_energy(S, report);
+  if (rc) return rc;
+  if (eigvals_host) std::memcpy(eigvals_host, S->lam.data(), sizeof(double) * p.k);
+  report->converged = report->sre_ry < p.sre_tol_ry ? 1 : 0;
+  S->sre_prev = report->sre_ry;
+  S->last = *report;
+  S->stepped = true;
+  if (report->converged) return KSCF_OK;
+  return mix(S, report);
+}
+
+// occupations of the current Ritz values, the output density of the normalised Ritz
+// vectors, its Hartree and exchange-correlation potentials, the residual V_out - V_in and
+// the energy integrals (S->sums); fills the density and energy figures of report
+int density_energy(kscf_scf* S, kscf_scf_report* report) {
+  const Ham& H = S->ham->h;
+  const kscf_scf_params& p = S->p;
+  cudaStream_t st = S->st;
+  const double h3 = H.grid.h * H.grid.h * H.grid.h;
+  int rc = KSCF_OK;
   std::vector<double> occ;
   double mu = 0.0, minus_ts = 0.0;
   occupations(S->lam, S->n_e, p.kT, occ, &mu, &minus_ts);
@@ -675,18 +697,19 @@ extern "C" int kscf_scf_step(kscf_scf* scf, kscf_scf_report* report, double* eig
   report->electrons = h3 * sums[4];
   report->homo = S->lam[S->n_occ - 1];
   report->lumo = S->lam[S->n_occ];
-  if (eigvals_host) std::memcpy(eigvals_host, S->lam.data(), sizeof(double) * p.k);
   if (!std::isfinite(report->sre_ry) || !std::isfinite(report->e_total)) {
     set_error("kscf_scf_step: non-finite residual or energy");
     return KSCF_ERR_NONFINITE;
   }
-  report->converged = report->sre_ry < p.sre_tol_ry ? 1 : 0;
-  S->sre_prev = report->sre_ry;
-  S->last = *report;
-  S->stepped = true;
-  if (report->converged) return KSCF_OK;
+  return KSCF_OK;
+}
 
-  // Anderson mixing of V_in (with the Kerker-preconditioned residual when q0 > 0)
+// Anderson mixing of V_in (with the Kerker-preconditioned residual when q0 > 0)
+int mix(kscf_scf* S, kscf_scf_report* report) {
+  const Ham& H = S->ham->h;
+  const kscf_scf_params& p = S->p;
+  cudaStream_t st = S->st;
+  int rc = KSCF_OK;
   const int m = p.history;
   const int slot = S->ring_next;
   const bool kerk = p.kerker_q0 > 0.0;
@@ -834,6 +857,73 @@ extern "C" int kscf_scf_evaluate(kscf_scf* scf, kscf_scf_report* report, double*
   if (eigvals_host) std::memcpy(eigvals_host, lam.data(), sizeof(double) * k);
   if (resid_host) std::memcpy(resid_host, res.data(), sizeof(double) * k);
   return KSCF_OK;
+}
+
+extern "C" int kscf_scf_refine(kscf_scf* scf, int max_iters, double resid_tol, kscf_scf_report* report,
+                               double* eigvals_host, double* resid_host, int* iters_done) {
+  if (!scf || !report || max_iters < 0 || !(resid_tol > 0.0)) {
+    set_error("kscf_scf_refine: invalid argument");
+    return KSCF_ERR_INVALID;
+  }
+  kscf_scf* S = scf;
+  if (!S->stepped) {
+    set_error("kscf_scf_refine: call kscf_scf_step first");
+    return KSCF_ERR_INVALID;
+  }
+  const kscf_scf_params& p = S->p;
+  const int k = p.k;
+  cudaStream_t st = S->st;
+  // wanted states: the occupied ones (occupation above 1e-12) and the first empty one
+  std::vector<double> occ;
+  double mu = 0.0, minus_ts = 0.0;
+  int rc = kscf_set_potential(S->ham, S->v_in, st);
+  if (rc) return rc;
+  KSCF_CUDA_TRY(cudaStreamSynchronize(st));
+  double lower = 0.0, upper = 0.0;
+  rc = kscf_spectral_bounds(S->ham, &lower, &upper);
+  if (rc) return rc;
+  std::vector<double> lam(k), res(k);
+  kscf_scf_report tmp;
+  double best = 0.0;
+  int stall = 0, it = 0;
+  for (; it < max_iters; it++) {
+    rc = eig_step(S, true, upper);
+    if (rc) return rc;
+    rc = kscf_scf_evaluate(S, &tmp, lam.data(), res.data());   // FP64 residuals of the current vectors
+    if (rc) return rc;
+    occupations(S->lam, S->n_e, p.kT, occ, &mu, &minus_ts);
+    int n_want = 0;
+    while (n_want < k && occ[n_want] > 1e-12) n_want++;
+    n_want = std::min(k, n_want + 1);
+    double worst = 0.0;
+    for (int i = 0; i < n_want; i++) worst = std::max(worst, res[i]);
+    if (worst < resid_tol) {
+      it++;
+      break;
+    }
+    // stop once the residuals no longer fall (the working precision's floor)
+    if (it == 0 || worst < 0.9 * best) {
+      best = worst;
+      stall = 0;
+    } else if (++stall >= 3) {
+      it++;
+      break;
+    }
+  }
+  if (iters_done) *iters_done = it;
+  rc = kscf_check_status();
+  if (rc) return rc;
+  // density, potentials and energy integrals of the refined vectors at the same V_in
+  kscf_scf_report r;
+  std::memset(&r, 0, sizeof(r));
+  r.step = S->step;
+  rc = density_energy(S, &r);
+  if (rc) return rc;
+  r.converged = S->last.converged;
+  r.chefsi_iters = it;
+  r.upper_bound = upper;
+  S->last = r;
+  return kscf_scf_evaluate(S, report, eigvals_host, resid_host);
 }
 
 extern "C" int kscf_scf_get(const kscf_scf* scf, int field, double* dst) {

@@ -123,6 +123,8 @@ _sigs = {
     "kscf_scf_step": ([_vp, C.POINTER(kscf_scf_report), C.POINTER(_d)], _i32),
     "kscf_scf_get": ([_vp, _i32, _vp], _i32),
     "kscf_scf_evaluate": ([_vp, C.POINTER(kscf_scf_report), C.POINTER(_d), C.POINTER(_d)], _i32),
+    "kscf_scf_refine": ([_vp, _i32, _d, C.POINTER(kscf_scf_report), C.POINTER(_d), C.POINTER(_d),
+                         C.POINTER(_i32)], _i32),
     "kscf_scf_hartree": ([_vp, _vp, _vp, C.POINTER(_i32)], _i32),
     "kscf_scf_free": ([_vp], _i32),
     "kscf_lda_xc": ([_vp, _vp, _vp, _vp, _vp], _i32),
@@ -533,6 +535,21 @@ class Scf:
         d = {f: getattr(rep, f) for f, _ in kscf_scf_report._fields_}
         d["lam"] = lam
         d["resid"] = res
+        return d
+
+    def refine(self, max_iters: int = 40, resid_tol: float = 1e-7):
+        """Converged mode at the current V_in (see kscf_scf_refine)."""
+        rep = kscf_scf_report()
+        lam = np.empty(self.k, dtype=np.float64)
+        res = np.empty(self.k, dtype=np.float64)
+        it = C.c_int()
+        _check(lib.kscf_scf_refine(self.handle, int(max_iters), float(resid_tol), C.byref(rep),
+                                   lam.ctypes.data_as(C.POINTER(C.c_double)), res.ctypes.data_as(C.POINTER(C.c_double)),
+                                   C.byref(it)))
+        d = {f: getattr(rep, f) for f, _ in kscf_scf_report._fields_}
+        d["lam"] = lam
+        d["resid"] = res
+        d["iters"] = it.value
         return d
 
     def run(self, max_steps: int = 40):

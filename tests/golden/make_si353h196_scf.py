@@ -1,6 +1,7 @@
-"""Writes tests/golden/si353h196_scf.json from the FP64 CPU oracle alone.
+"""Writes tests/golden/<workload>_scf.json from the FP64 CPU oracle alone.
 
-The 2.2 nm cluster (Si353H196, 234,489 grid points, k = 850, degree 12): the oracle's
+Default: the 2.2 nm cluster (Si353H196, 234,489 grid points, k = 850, degree 12); with
+--workload si35h36 the 1 nm cluster (Si35H36, 45,025 points, k = 100, degree 10).  The oracle's
 self-consistent field (Computational details: LDA, Anderson mixing of the input
 potential, the 4-then-1 CheFSI schedule, stop at SRE < 1e-4 Ry) from the seeded X0
 (seed 1), followed by the converged mode at the final input potential: CheFSI at
@@ -11,8 +12,9 @@ evaluated with the converged orbitals, and moments of the converged density (cha
 dipole, quadrupole about the domain centre, charge in 1-bohr radial shells, and the
 density at 4096 seeded sample points of the lexicographic grid).
 
-Only oracle/ and workloads/ are called.  About two hours on eight cores:
-    python tests/golden/make_si353h196_scf.py [--checkpoint DIR]
+Only oracle/ and workloads/ are called.  About two hours on eight cores for the 2.2 nm
+cluster, a few minutes for the 1 nm one:
+    python tests/golden/make_si353h196_scf.py [--workload NAME] [--checkpoint DIR]
 """
 from __future__ import annotations
 
@@ -35,7 +37,7 @@ from oracle.potential import kb_projectors, local_potential  # noqa: E402
 from oracle.scf import Poisson, lda_xc, occupations, scf    # noqa: E402
 from workloads import n_electrons, pseudo_params, random_block_lex, workload  # noqa: E402
 
-OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "si353h196_scf.json")
+HERE = os.path.dirname(os.path.abspath(__file__))
 N_SAMPLE = 4096
 N_UNOCC = 10
 RESID_TOL = 1e-7
@@ -60,14 +62,16 @@ def density_moments(grid, rho):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--checkpoint", default=None, help="directory for the post-SCF state (resumable)")
+    ap.add_argument("--workload", default="si353h196")
     args = ap.parse_args()
-    wl = workload("si353h196")
+    wl = workload(args.workload)
+    out_path = os.path.join(HERE, f"{wl.name}_scf.json")
     pos, z = wl.atoms()
     species = pseudo_params()
     ne = n_electrons(z)
     nocc = ne // 2
     t0 = time.time()
-    ck = os.path.join(args.checkpoint, "si353h196_scf_state.npz") if args.checkpoint else None
+    ck = os.path.join(args.checkpoint, f"{wl.name}_scf_state.npz") if args.checkpoint else None
     if ck and os.path.exists(ck):
         st = np.load(ck, allow_pickle=False)
         X, v_in, lam = st["X"], st["v_in"], st["lam"]
@@ -104,7 +108,7 @@ def main():
     e_tot = (e_band - h3 * float(np.dot(rho, v_in - v_ion)) + 0.5 * h3 * float(np.dot(rho, vh))
              + h3 * float(np.dot(rho, eps)) + minus_ts)
     out = {
-        "what": "FP64 CPU oracle: SCF of the 2.2 nm cluster to SRE < 1e-4 Ry, then fixed-potential CheFSI "
+        "what": f"FP64 CPU oracle: SCF of {wl.name} to SRE < 1e-4 Ry, then fixed-potential CheFSI "
                 "to residual < 1e-7 Ha (occupied states and the LUMO)",
         "written_by": "tests/golden/make_si353h196_scf.py (oracle/ and workloads/ only)",
         "workload": wl.name, "n_points": int(g.n), "n_atoms": int(len(z)), "k": wl.k, "degree": wl.degree,
@@ -119,9 +123,9 @@ def main():
                       "rho": density_moments(g, rho)},
         "seconds": time.time() - t0,
     }
-    with open(OUT, "w") as f:
+    with open(out_path, "w") as f:
         json.dump(out, f, indent=1)
-    print(f"wrote {OUT} ({time.time() - t0:.0f} s)", flush=True)
+    print(f"wrote {out_path} ({time.time() - t0:.0f} s)", flush=True)
 
 
 if __name__ == "__main__":

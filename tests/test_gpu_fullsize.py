@@ -91,3 +91,48 @@ def test_step_fullsize_largest(kscf, species):
     ref = (e / (a0 - c)) / e * (HY - c * Y[rows])
     scale = np.max(np.abs(ref), axis=0)
     assert np.all(np.max(np.abs(got - ref), axis=0) <= 2e-5 * scale)
+
+
+def test_tensor_orthonormalize_and_rayleigh_ritz_fullsize(kscf, species):
+    """Tensor-mode CholeskyQR2 and Rayleigh-Ritz at the benchmark size (336,384 slots x 850
+    FP32, rotated in place in 5 row panels of 78,848 rows).  Checks: orthonormality of the
+    split-bf16 result (< 2e-6); every panel rotated by the same k x k matrix (rows at each
+    panel boundary equal X_before[rows] M, M recovered in FP64 from the whole block, to
+    2e-5 of the rows' maximum); Ritz values within 1e-5 of the FP64 native path started
+    from the same X; and the spans of the two Ritz bases within a principal angle of 1e-4."""
+    from workloads import workload
+    w = workload("si353h196")
+    pos, z = w.atoms()
+    g, H = kscf.build_cluster(pos, z, species, w.radius, w.h)
+    n_slots, k = g.info["n_slots"], w.k
+    h3 = g.info["h"] ** 3
+    full, X = device_block(kscf, H, n_slots, k, seed=7)
+    Xb = X.double().clone()
+    kscf.kscf_orthonormalize(H, X, mode=kscf.KSCF_GEMM_TENSOR)
+    Xa = X.double()
+    eye = torch.eye(k, dtype=torch.float64, device="cuda")
+    assert (h3 * (Xa.T @ Xa) - eye).abs().max().item() < 2e-6
+    prows = (256 << 20) // (k * 4) // 512 * 512
+    assert prows == 78848 and n_slots > 4 * prows
+    bnd = np.unique(np.concatenate([[p * prows - 2, p * prows - 1, p * prows, p * prows + 1]
+                                    for p in range(1, (n_slots - 1) // prows + 1)] + [[0, n_slots - 1]]))
+    rows = torch.tensor(bnd, device="cuda")
+
+    def same_matrix(before, after):
+        M = torch.linalg.solve(before.T @ before, before.T @ after)
+        err = (after[rows] - before[rows] @ M).abs().amax(1)
+        return bool(torch.all(err <= 2e-5 * after[rows].abs().amax(1).clamp_min(1e-30)).item())
+
+    assert same_matrix(Xb, Xa)
+    X64 = Xb.clone()
+    kscf.kscf_orthonormalize(H, X64, mode=kscf.KSCF_GEMM_NATIVE)
+    before = X.double().clone()
+    lam32 = kscf.kscf_rayleigh_ritz(H, X, mode=kscf.KSCF_GEMM_TENSOR)
+    lam64 = kscf.kscf_rayleigh_ritz(H, X64, mode=kscf.KSCF_GEMM_NATIVE)
+    assert np.max(np.abs(lam32 - lam64)) <= 1e-5 * np.max(np.abs(lam64))
+    after = X.double()
+    assert same_matrix(before, after)
+    q1, _ = torch.linalg.qr(after)
+    q2, _ = torch.linalg.qr(X64)
+    s = torch.linalg.svdvals(q1.T @ q2)
+    assert float(torch.sqrt(torch.clamp(1.0 - s.min() ** 2, min=0.0))) < 1e-4
