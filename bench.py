@@ -654,7 +654,7 @@ def run_kscf(args):
                 "step_breakdown_ms": breakdown,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
-                             "kernel": "cheb_step (fused stencil+V+KB+recurrence), per degree-step launch",
+                             "kernel": "cm_step_ldg16 (fused stencil + V + KB scatter + recurrence) with its kb_gather_cm, per degree step",
                              "alg_bytes_per_launch": alg_bytes, "launch_ms": step_ms},
                 "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks, "scf": scf,
                 "learned_start": learned_start}
@@ -667,7 +667,7 @@ def run_kscf(args):
 def run_filter_sweep(args):
     """Filter-only sweep: Gpoint*vec/s and the algorithmic-bytes roofline fraction (12 B per
     point*vector*degree step, as in the main line) for brick sizes 8 and 16 and column block
-    widths 32, 64 and 128, on a 1024-column sample of the workload's block (the column
+    widths 32, 64, 128 and 1024, on a 1024-column sample of the workload's block (the column
     blocks are independent, so the rate of a sample is the rate of the whole block)."""
     import torch
     from paper_2303_00790_gb300 import kscf
@@ -686,7 +686,7 @@ def run_filter_sweep(args):
         kscf.kscf_random_subspace(H, X, seed=1)
         lo, hi = kscf.kscf_spectral_bounds(H)
         a0, a = lo, lo + 0.25 * (hi - lo)     # any a0 < a < b: the work does not depend on them
-        for block in (32, 64, 128):
+        for block in (32, 64, 128, 1024):
             wf = torch.empty(kscf.kscf_workspace_size(H, kscf.KSCF_OP_FILTER, cols, kscf.KSCF_F32, 0, block),
                              dtype=torch.uint8, device="cuda")
             kscf.kscf_chebyshev_filter(H, X, m, a, hi, a0, block=block, work=wf)

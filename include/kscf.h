@@ -310,11 +310,17 @@ int kscf_rotate(const void* A, int64_t lda, const double* Q, int64_t ldq, int64_
                 void* stream);
 int kscf_gemm_workspace_size(int op, int64_t rows, int m, int n, int dtype, int mode, size_t* bytes);
 
-/* Reads and clears the device status words of the kernels that wait on mbarriers (the
- * tensor-core GEMMs and the TMA filter step): KSCF_ERR_TIMEOUT if a bounded wait gave
- * up since the last check (the kernel then skipped its remaining work and, for the
- * GEMMs, freed its tensor memory), else KSCF_OK.  Synchronising.  orthonormalize and
- * rayleigh_ritz check the GEMM word themselves; filter callers check after the filter. */
+/* Reads and clears the device status words (synchronising):
+ *   KSCF_ERR_TIMEOUT   a bounded wait of a kernel that waits on mbarriers (the tensor-core
+ *                      GEMMs, the TMA filter step) gave up since the last check; the kernel
+ *                      then skipped its remaining work and, for the GEMMs, freed its tensor
+ *                      memory;
+ *   KSCF_ERR_NONFINITE the last degree step of an FP32 filter on 8^3 bricks, or
+ *                      kscf_hamiltonian_apply, stored a NaN or Inf in a domain row (a
+ *                      non-finite X, Y or potential), since the last check;
+ *   else KSCF_OK.  orthonormalize and rayleigh_ritz check the GEMM word themselves, and
+ *   orthonormalize returns KSCF_ERR_NONFINITE when the Gram matrix of X has a non-finite
+ *   diagonal; filter and apply callers check after those calls. */
 int kscf_check_status(void);
 
 /* Self-test of the bounded grid barriers of the FP64 Cholesky kernel (orthonormalize):

@@ -125,9 +125,9 @@ __device__ __forceinline__ bool finite4(float4 v) {
 // Shared memory of cm_step_ldg16 (bytes): core and accumulator (512 point slots x 16
 // floats each), the coefficients of the brick's KB atoms (KSCF_BRICK_ATOMS x 4 x 16
 // floats) and the first LDG_ENT entries of the brick (packed word + chi).
-constexpr int LDG_ENT = 512;
+constexpr int LDG_ENT = 256;
 constexpr int LDG_CORE = 0, LDG_ACC = 32768, LDG_KBC = 65536, LDG_EW = LDG_KBC + KSCF_BRICK_ATOMS * 4 * 64,
-              LDG_ECHI = LDG_EW + LDG_ENT * 4, LDG_SMEM = LDG_ECHI + LDG_ENT * 16;
+              LDG_ECHI = LDG_EW + LDG_ENT * 4, LDG_PREV = LDG_ECHI + LDG_ENT * 16, LDG_SMEM = LDG_PREV + 32768;
 
 // Lines of a pass that hold no domain point are skipped: each pass takes its lines from
 // the brick's compacted list of live lines, and the threads past the list's end idle
@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
   float4* kbc = (float4*)(smw + LDG_KBC);      // [atom][l][4]
   uint32_t* ew = (uint32_t*)(smw + LDG_EW);
   float4* echi = (float4*)(smw + LDG_ECHI);
+  const float4* prev4 = (const float4*)(smw + LDG_PREV);   // [512][4]: Y_{j-2} rows of this brick
   auto sl = [](int x, int y, int z) { return (z * 8 + y) * 8 + (x ^ (y & 1)); };
   int c, brick;
   if (!cta_item(a, &c, &brick)) return;
@@ -167,7 +168,10 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
   const int lx = L < nlx ? __ldg(bl + L) : -1;
   const int ly = L < nly ? __ldg(bl + 64 + L) : -1;
   const int lz = L < nlz ? __ldg(bl + 128 + L) : -1;
-  // core: 512 rows x 64 B, padding rows zero-filled without a read
+  // core: 512 rows x 64 B, padding rows zero-filled without a read; with it the brick's
+  // Y_{j-2} rows (chunk-major, contiguous), so that the z pass finds them in shared memory
+  const bool prev_smem = a.prev != nullptr && a.ld_prev == 16;
+  const float* psrc = prev_smem ? a.prev + (int64_t)c * a.cs_prev + b0 * 16 + vl : nullptr;
 #pragma unroll
   for (int i = 0; i < 8; i++) {
     const int r = L + 64 * i;
@@ -175,6 +179,11 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(&core4[sl(r & 7, (r >> 3) & 7, r >> 6) * 4 + vp]);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(own + r * 16), "r"(live ? 16 : 0)
                  : "memory");
+    if (prev_smem) {
+      const uint32_t dp = (uint32_t)__cvta_generic_to_shared(smw + LDG_PREV + (r * 4 + vp) * 16);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dp), "l"(psrc + r * 16), "r"(live ? 16 : 0)
+                   : "memory");
+    }
   }
   const int64_t e0 = __ldg(a.kb_ptr + b0), e1 = __ldg(a.kb_ptr + b0 + 512);
   const int ne = (int)(e1 - e0);
@@ -318,7 +327,8 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
         hy = f4_fma(f2(vv[z]), yc, hy);
         float4 r = f4_mul(alpha, f4_fma(negc, yc, hy));
         if (prevp) {
-          const float4 pv = *(const float4*)(prevp + s * a.ld_prev);   // plain load: prev may be out
+          // plain load otherwise: prev may be the output buffer
+          const float4 pv = prev_smem ? prev4[(z * 64 + lz) * 4 + vp] : *(const float4*)(prevp + s * a.ld_prev);
           r = f4_fma(beta, pv, r);
         }
         if (a.check)
