@@ -43,7 +43,7 @@ extern "C" {
 /* ---- status codes ---- */
 #define KSCF_OK               0
 #define KSCF_ERR_INVALID     -1   /* bad argument (null pointer, size, bounds, dtype) */
-#define KSCF_ERR_CUDA        -2   /* a CUDA / cuSOLVER call failed */
+#define KSCF_ERR_CUDA        -2   /* a CUDA runtime call failed */
 #define KSCF_ERR_WORKSPACE   -3   /* work buffer smaller than kscf_workspace_size */
 #define KSCF_ERR_NOT_SPD     -4   /* Gram matrix not positive definite (rank-deficient X) */
 #define KSCF_ERR_NONFINITE   -5   /* NaN/Inf found in an input or result */
@@ -309,6 +309,23 @@ int kscf_rotate(const void* A, int64_t lda, const double* Q, int64_t ldq, int64_
                 int dtype, int mode, int minus_identity, void* out, int64_t ldo, void* work, size_t work_bytes,
                 void* stream);
 int kscf_gemm_workspace_size(int op, int64_t rows, int m, int n, int dtype, int mode, size_t* bytes);
+
+/* Dense FP64 symmetric eigensolver of the Rayleigh-Ritz step (CheFSI paragraph:
+ * Hs = Q Lambda Q^T, the eigenvalue problem projected onto the filtered subspace), the
+ * one kscf_rayleigh_ritz calls.  A: device, n x n, column-major with leading dimension
+ * lda >= n; the symmetric part (A + A^T) / 2 is diagonalised and A is overwritten by the
+ * orthonormal eigenvectors (column j belongs to w[j]).  w: device, n doubles, ascending.
+ * Householder tridiagonalisation, tridiagonal divide and conquer with deflation and
+ * Gu-Eisenstat eigenvectors, back-transformation; everything on the device in FP64
+ * (backward error O(n u max|A_ij|), u = 2^-53).  1 <= n <= 8192.
+ * work: device buffer of kscf_sym_eig_work_bytes(n) bytes (about 4 n^2 doubles),
+ * caller-owned, 256-byte aligned.  Synchronous on `stream`.  Errors: KSCF_ERR_NONFINITE
+ * (A holds a NaN or Inf; the outputs are then those of the zero matrix),
+ * KSCF_ERR_TIMEOUT (a bounded grid barrier of the tridiagonalisation gave up),
+ * KSCF_ERR_NO_CONVERGE (a secular-equation root did not converge), KSCF_ERR_WORKSPACE,
+ * KSCF_ERR_INVALID. */
+int kscf_sym_eig_work_bytes(int n, size_t* bytes);
+int kscf_sym_eig(double* A, int64_t lda, int n, double* w, void* work, size_t work_bytes, void* stream);
 
 /* Reads and clears the device status words (synchronising):
  *   KSCF_ERR_TIMEOUT   a bounded wait of a kernel that waits on mbarriers (the tensor-core

@@ -14,7 +14,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkscf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["grid.cpp", "ham.cpp", "capi.cpp", "setup.cu", "filter.cu", "filter_cm.cu", "gemm.cu", "gemm_tc.cu", "apply_noalloc.cu",
-           "scf_kernels.cu", "scf.cpp", "learned.cu", "dos.cpp", "lanczos.cpp", "chol.cu"]
+           "scf_kernels.cu", "scf.cpp", "learned.cu", "dos.cpp", "lanczos.cpp", "chol.cu", "eig.cu"]
 
 
 def _nvcc() -> str:
@@ -68,7 +68,7 @@ def build(verbose: bool = False, ptxas_verbose: bool = False, force: bool = Fals
     if jobs or not os.path.exists(LIB):
         lib64 = os.path.join(_cuda_home(nvcc), "lib64")
         cmd = [nvcc, "-shared", "-o", LIB + ".tmp"] + objs + ARCH + [
-            "-L", lib64, "-lcusolver", "-lcublas", "-Xlinker", f"-rpath,{lib64}"]
+            "-L", lib64, "-Xlinker", f"-rpath,{lib64}"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)

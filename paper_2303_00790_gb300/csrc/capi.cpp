@@ -1,12 +1,9 @@
 // C ABI drivers of the CheFSI hot path: Hamiltonian apply, Chebyshev filter,
 // Cholesky-QR, Rayleigh-Ritz, density and the initial subspace (arXiv 2303.00790,
-// CheFSI paragraph).  The FP64 Cholesky factor and its inverse come from chol.cu; the
-// k x k FP64 symmetric eigensolver is cuSOLVER's.
-#include <cusolverDn.h>
-
+// CheFSI paragraph).  The FP64 Cholesky factor and its inverse come from chol.cu, the
+// k x k FP64 symmetric eigensolver from eig.cu.
 #include <algorithm>
 #include <cmath>
-#include <mutex>
 #include <vector>
 
 #include "kscf_internal.h"
@@ -29,39 +26,24 @@ cudaError_t filter_status(bool reset, unsigned int* status);
 
 namespace {
 
-// ---- per-device cuSOLVER handles ----
-std::mutex g_mu;
-std::vector<cusolverDnHandle_t> g_handles;
+size_t esize(int dtype) { return dtype == KSCF_F64 ? 8 : 4; }
 
-int solver_handle(cusolverDnHandle_t* out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
-    set_error("cudaGetDevice failed");
-    return KSCF_ERR_CUDA;
+// status words of launch_sym_eig, read back after a synchronisation
+int eig_info_code(const int* info, const char* who) {
+  if (info[2]) {
+    set_error("%s: the matrix to diagonalise holds a NaN or Inf", who);
+    return KSCF_ERR_NONFINITE;
   }
-  std::lock_guard<std::mutex> lk(g_mu);
-  if ((int)g_handles.size() <= dev) g_handles.resize(dev + 1, nullptr);
-  if (!g_handles[dev]) {
-    if (cusolverDnCreate(&g_handles[dev]) != CUSOLVER_STATUS_SUCCESS) {
-      set_error("cusolverDnCreate failed");
-      return KSCF_ERR_CUDA;
-    }
+  if (info[0]) {
+    set_error("%s: a bounded grid barrier of the tridiagonalisation gave up", who);
+    return KSCF_ERR_TIMEOUT;
   }
-  *out = g_handles[dev];
+  if (info[1]) {
+    set_error("%s: %d secular-equation roots did not converge", who, info[1]);
+    return KSCF_ERR_NO_CONVERGE;
+  }
   return KSCF_OK;
 }
-
-#define SOLVER_TRY(expr)                                                              \
-  do {                                                                                \
-    cusolverStatus_t _s = (expr);                                                     \
-    if (_s != CUSOLVER_STATUS_SUCCESS) {                                              \
-      set_error("%s failed with cuSOLVER status %d (%s:%d)", #expr, (int)_s, __FILE__, \
-                __LINE__);                                                            \
-      return KSCF_ERR_CUDA;                                                           \
-    }                                                                                 \
-  } while (0)
-
-size_t esize(int dtype) { return dtype == KSCF_F64 ? 8 : 4; }
 
 // after a synchronisation: did a tensor-core pipeline wait time out?
 int check_tc(int mode, const char* who) {
@@ -148,12 +130,10 @@ struct RRPlan {
 };
 
 int rr_plan(const Ham& H, int k, int dtype, int mode, int block, RRPlan* p) {
-  cusolverDnHandle_t hs;
-  int rc = solver_handle(&hs);
-  if (rc) return rc;
-  int lw = 0;
-  SOLVER_TRY(cusolverDnDsyevd_bufferSize(hs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, k, nullptr, k,
-                                         nullptr, &lw));
+  if (k > KSCF_EIG_MAX_N) {
+    set_error("kscf_rayleigh_ritz: k = %d above the eigensolver's limit %d", k, KSCF_EIG_MAX_N);
+    return KSCF_ERR_INVALID;
+  }
   p->w = block_width(k, block);
   p->hxb = (size_t)H.grid.n_slots * coef_ld(p->w) * esize(dtype);
   p->coef = (size_t)std::max(H.n_kb, 1) * 4 * coef_ld(p->w) * esize(dtype);
@@ -161,7 +141,7 @@ int rr_plan(const Ham& H, int k, int dtype, int mode, int block, RRPlan* p) {
   p->W = (size_t)k * 8;
   p->Q = (size_t)k * k * esize(dtype);
   p->info = 256;
-  p->lwork_bytes = (size_t)lw * 8 + 256;
+  p->lwork_bytes = sym_eig_work_bytes(k);
   p->prows = panel_rows(H.grid.n_slots, k, dtype);
   p->panel = mode == KSCF_GEMM_TENSOR ? 0 : (size_t)p->prows * k * esize(dtype);
   p->tc = 0;
@@ -523,11 +503,7 @@ extern "C" int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int 
   if (rc) return rc;
   rc = check_work(work, work_bytes, rr_bytes(p), "kscf_rayleigh_ritz");
   if (rc) return rc;
-  cusolverDnHandle_t hs;
-  rc = solver_handle(&hs);
-  if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  SOLVER_TRY(cusolverDnSetStream(hs, st));
   Carver cv(work);
   void* hxb = cv.take(p.hxb);
   void* coef = cv.take(p.coef);
@@ -535,7 +511,7 @@ extern "C" int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int 
   double* W = (double*)cv.take(p.W);
   void* Qm = cv.take(p.Q);
   int* info = (int*)cv.take(p.info);
-  double* lwork = (double*)cv.take(p.lwork_bytes);
+  void* lwork = cv.take(p.lwork_bytes);
   void* panel = cv.take(p.panel);
   void* tcw = cv.take(p.tc);
   const size_t es = esize(dtype);
@@ -554,24 +530,20 @@ extern "C" int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int 
     rc = gram(X, ld, hxb, wpad, rows, k, wb, dtype, mode, h3, Hs + (size_t)c0 * k, k, tcw, p.tc, st, wb == k);
     if (rc) return rc;
   }
-  KSCF_CUDA_TRY(launch_symmetrize(Hs, k, k, st));
-  SOLVER_TRY(cusolverDnDsyevd(hs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_UPPER, k, Hs, k, W, lwork,
-                              (int)(p.lwork_bytes / 8 - 32), info));
+  KSCF_CUDA_TRY(launch_sym_eig(Hs, k, k, W, lwork, p.lwork_bytes, info, st));
   // eigenvector signs chosen so that diag(Q) >= 0: for an input block already close to
   // Ritz vectors Q is then close to the identity, and the tensor-core rotation is applied
   // as X + X (Q - I), whose rounding error scales with |Q - I| instead of |Q|
   if (mode == KSCF_GEMM_TENSOR) KSCF_CUDA_TRY(launch_sign_fix(Hs, k, st));
   if (mode != KSCF_GEMM_TENSOR) KSCF_CUDA_TRY(launch_f64_to_dtype(Hs, (int64_t)k * k, dtype, Qm, st));
-  int hinfo = 0;
-  KSCF_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+  int hinfo[4] = {0, 0, 0, 0};
+  KSCF_CUDA_TRY(cudaMemcpyAsync(hinfo, info, sizeof(hinfo), cudaMemcpyDeviceToHost, st));
   KSCF_CUDA_TRY(cudaMemcpyAsync(eigvals_host, W, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
   KSCF_CUDA_TRY(cudaStreamSynchronize(st));
   rc = check_tc(mode, "kscf_rayleigh_ritz");
   if (rc) return rc;
-  if (hinfo != 0) {
-    set_error("kscf_rayleigh_ritz: symmetric eigensolver failed (info %d)", hinfo);
-    return hinfo > 0 ? KSCF_ERR_NO_CONVERGE : KSCF_ERR_INVALID;
-  }
+  rc = eig_info_code(hinfo, "kscf_rayleigh_ritz");
+  if (rc) return rc;
   for (int i = 0; i < k; i++)
     if (!std::isfinite(eigvals_host[i])) {
       set_error("kscf_rayleigh_ritz: non-finite Ritz value");
@@ -579,6 +551,34 @@ extern "C" int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int 
     }
   return rotate_inplace(X, ld, rows, k, dtype, mode, Qm, Hs, mode == KSCF_GEMM_TENSOR, panel, p.prows, tcw, p.tc,
                         st);
+}
+
+extern "C" int kscf_sym_eig_work_bytes(int n, size_t* bytes) {
+  if (n < 1 || n > KSCF_EIG_MAX_N || !bytes) {
+    set_error("kscf_sym_eig_work_bytes: n = %d outside [1, %d] or null output", n, KSCF_EIG_MAX_N);
+    return KSCF_ERR_INVALID;
+  }
+  *bytes = sym_eig_work_bytes(n) + 256;
+  return KSCF_OK;
+}
+
+extern "C" int kscf_sym_eig(double* A, int64_t lda, int n, double* w, void* work, size_t work_bytes, void* stream) {
+  if (!A || !w || n < 1 || n > KSCF_EIG_MAX_N || lda < n) {
+    set_error("kscf_sym_eig: invalid argument (n = %d, lda = %lld)", n, (long long)lda);
+    return KSCF_ERR_INVALID;
+  }
+  const size_t need = sym_eig_work_bytes(n) + 256;
+  if (!work || work_bytes < need) {
+    set_error("kscf_sym_eig: work buffer of %zu bytes, need %zu", work_bytes, need);
+    return KSCF_ERR_WORKSPACE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int* info = (int*)work;   // first 256 bytes: status words
+  KSCF_CUDA_TRY(launch_sym_eig(A, lda, n, w, (char*)work + 256, work_bytes - 256, info, st));
+  int hinfo[4] = {0, 0, 0, 0};
+  KSCF_CUDA_TRY(cudaMemcpyAsync(hinfo, info, sizeof(hinfo), cudaMemcpyDeviceToHost, st));
+  KSCF_CUDA_TRY(cudaStreamSynchronize(st));
+  return eig_info_code(hinfo, "kscf_sym_eig");
 }
 
 extern "C" int kscf_density(const kscf_ham* ham, const void* X, int64_t ld, int n_occ, int dtype, const double* occ,

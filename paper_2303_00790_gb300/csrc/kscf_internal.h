@@ -178,6 +178,15 @@ size_t chol_inv_work_bytes(int k);
 cudaError_t launch_chol_inv(const double* S, int64_t lds, int k, double floor_rel, double* out, int64_t ldo,
                             void* work, int* status, cudaStream_t st, long long spin_limit = 2000000000LL,
                             int leave_cta = -1);
+// FP64 symmetric eigensolver (eig.cu): A (n x n column-major, lda; the symmetric part
+// (A + A^T) / 2 is diagonalised) is overwritten by the orthonormal eigenvectors, column j
+// for w[j] (device, ascending).  info (4 device ints, zeroed here): [0] = 1 if a bounded
+// grid barrier gave up, [1] = secular roots that did not converge, [2] = 1 if A held a
+// NaN or Inf.  work: sym_eig_work_bytes(n), 256-aligned.  n <= KSCF_EIG_MAX_N.
+constexpr int KSCF_EIG_MAX_N = 8192;
+size_t sym_eig_work_bytes(int n);
+cudaError_t launch_sym_eig(double* A, int64_t lda, int n, double* w, void* work, size_t work_bytes, int* info,
+                           cudaStream_t st, long long spin_limit = 2000000000LL);
 cudaError_t launch_f64_to_dtype(const double* src, int64_t n, int dtype, void* out, cudaStream_t st);
 
 }  // namespace kscf

@@ -115,6 +115,8 @@ _sigs = {
     "kscf_gram": ([_vp, _i64, _vp, _i64, _i64, _i32, _i32, _i32, _i32, _d, _vp, _i64, _vp, _sz, _vp], _i32),
     "kscf_rotate": ([_vp, _i64, _vp, _i64, _i64, _i32, _i32, _i32, _i32, _i32, _vp, _i64, _vp, _sz, _vp], _i32),
     "kscf_gemm_workspace_size": ([_i32, _i64, _i32, _i32, _i32, _i32, C.POINTER(_sz)], _i32),
+    "kscf_sym_eig_work_bytes": ([_i32, C.POINTER(_sz)], _i32),
+    "kscf_sym_eig": ([_vp, _i64, _i32, _vp, _vp, _sz, _vp], _i32),
     "kscf_check_status": ([], _i32),
     "kscf_selftest_barrier_timeout": ([_vp], _i32),
     "kscf_scf_create": ([_vp, C.POINTER(kscf_atom), _i32, C.POINTER(kscf_species), _i32, C.POINTER(_d),
@@ -444,6 +446,24 @@ def kscf_rotate(A, Q, mode: int = KSCF_GEMM_NATIVE, minus_identity: bool = False
                            dt, mode, 1 if minus_identity else 0, C.c_void_p(out.data_ptr()), _rows(out, kout),
                            C.c_void_p(work.data_ptr()), work.numel(), _stream(stream)))
     return out
+
+
+def kscf_sym_eig(A, w=None, work=None, stream=None):
+    """In place: A (n x n FP64 device tensor, symmetric) <- eigenvectors; returns w
+    (device, ascending).  A row-major torch tensor is the transpose of the column-major
+    matrix the library sees; for a symmetric A both are the same, and the eigenvector of
+    w[j] is row j of the result (column j of its column-major reading)."""
+    torch = _torch()
+    n = A.shape[0]
+    if w is None:
+        w = torch.empty(n, dtype=torch.float64, device=A.device)
+    if work is None:
+        b = C.c_size_t()
+        _check(lib.kscf_sym_eig_work_bytes(n, C.byref(b)))
+        work = torch.empty(b.value, dtype=torch.uint8, device=A.device)
+    _check(lib.kscf_sym_eig(C.c_void_p(A.data_ptr()), A.stride(0), n, C.c_void_p(w.data_ptr()),
+                            C.c_void_p(work.data_ptr()), work.numel(), _stream(stream)))
+    return w
 
 
 def kscf_check_status():
