@@ -93,17 +93,6 @@ __device__ __forceinline__ double rsqrt_pos(double x) {
   return r;
 }
 
-// sum over the CTA (NT threads); every thread gets the result.  red: NW doubles.
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  v = warp_sum(v);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  double t = 0.0;
-#pragma unroll
-  for (int w = 0; w < NW; w++) t += red[w];
-  return t;
-}
 __device__ __forceinline__ double block_max(double v, double* red) {
   v = warp_max(v);
   __syncthreads();
@@ -220,49 +209,42 @@ __device__ bool tri_barrier(const TriArgs& a, unsigned target, int* s_ok) {
   return *s_ok != 0;
 }
 
-// Householder vector of x = r[s .. n-1]: (I - tau v v^T) x = beta e_1 with v[s] = 1
-// (Golub & Van Loan, Algorithm 5.1.1).  beta = -sign(x_0) |x|, tau = 1 + |x_0| / |x|,
-// v = x / (x_0 - beta).  A vector whose tail norm is negligible against max|A| = 1
-// (|x_1..|^2 <= eps^2) gets tau = 0, beta = x_0.  Writes v into vout[s .. n-1]; returns
-// (tau, beta) through sc[0], sc[1].  All threads of the CTA call it.
-__device__ void householder(const double* r, int s, int n, double* vout, double* red, double* sc) {
-  double sg = 0.0;
-  for (int l = s + 1 + threadIdx.x; l < n; l += NT) sg = fma(r[l], r[l], sg);
-  sg = block_sum(sg, red);
-  const double alpha = r[s];
-  double t, beta, scal;
-  if (sg <= EPS * EPS) {
-    t = 0.0;
-    beta = alpha;
-    scal = 0.0;
-  } else {
-    const double x2 = fma(alpha, alpha, sg);
-    const double y = rsqrt_pos(x2);   // 1 / |x|
-    const double nrm = x2 * y;
-    beta = alpha >= 0.0 ? -nrm : nrm;
-    t = fma(fabs(alpha), y, 1.0);
-    scal = recip(alpha - beta);
+// Scalars of the Householder reflector of x = r[s .. n-1] (Golub & Van Loan, Sec. 5.1.2,
+// without the normalisation v_0 = 1): with |x|^2 = alpha^2 + sigma, beta = -sign(alpha)|x|,
+// v = x - beta e_1 (so v_0 = alpha - beta = sign(alpha)(|alpha| + |x|), v_l = x_l after it)
+// and tau = 2 / v^T v = 1 / (|x|^2 + |alpha| |x|), (I - tau v v^T) x = beta e_1.  A tail
+// negligible against max|A| = 1 (sigma <= eps^2) gives tau = 0, beta = alpha.
+// Returns tau, beta, v_0 in sc[0..2].  One thread.
+__device__ __forceinline__ void reflector_scalars(double alpha, double sigma, double* sc) {
+  if (sigma <= EPS * EPS) {
+    sc[0] = 0.0;
+    sc[1] = alpha;
+    sc[2] = 1.0;
+    return;
   }
-  for (int l = s + threadIdx.x; l < n; l += NT) vout[l] = l == s ? 1.0 : r[l] * scal;
-  if (threadIdx.x == 0) {
-    sc[0] = t;
-    sc[1] = beta;
-  }
-  __syncthreads();
+  const double x2 = fma(alpha, alpha, sigma);
+  const double y = rsqrt_pos(x2);
+  const double nrm = x2 * y;
+  const double aa = fabs(alpha);
+  sc[0] = recip(fma(aa, nrm, x2));
+  sc[1] = alpha >= 0.0 ? -nrm : nrm;
+  sc[2] = alpha >= 0.0 ? aa + nrm : -(aa + nrm);
 }
 
 template <bool SMEM>
-__global__ void __launch_bounds__(NT) tridiag_kernel(TriArgs a) {
+__global__ void __launch_bounds__(NT, 1) tridiag_kernel(TriArgs a) {
   extern __shared__ __align__(16) double smd[];
   __shared__ double red[NW];
   __shared__ double sc[4];
   __shared__ int s_ok;
   const int n = a.n, P = a.P, cta = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* vc = smd;          // v_j
-  double* vp = smd + n;      // v_{j-1}, then v_{j+1}
-  double* wp = smd + 2 * n;  // w_{j-1}, then w_j
-  double* rw = a.rwg ? a.rwg + (int64_t)cta * n : smd + 3 * n;   // row work
+  // three rotating vectors: v_j (current), v_{j-1} (previous), the row work vector that
+  // becomes v_{j+1}; and w (w_{j-1} during the pass, then w_j)
+  double* vc = smd;
+  double* vp = smd + n;
+  double* wp = smd + 2 * n;
+  double* rw = a.rwg ? a.rwg + (int64_t)cta * n : smd + 3 * n;
   double* rows = smd + (a.rwg ? 3 : 4) * n;
   const int nown = cta < n ? (n - cta + P - 1) / P : 0;
   if (n == 1) {
@@ -279,14 +261,33 @@ __global__ void __launch_bounds__(NT) tridiag_kernel(TriArgs a) {
       for (int l = threadIdx.x; l < n; l += NT) rows[(int64_t)r * n + l] = src[l];
     }
   }
-  for (int l = threadIdx.x; l < n; l += NT) rw[l] = a.A[l];   // row 0
+  // reflector 0 from row 0 of A
+  double sg = 0.0;
+  for (int l = threadIdx.x; l < n; l += NT) {
+    const double x = a.A[l];
+    vc[l] = x;
+    if (l >= 2) sg = fma(x, x, sg);
+  }
+  sg = warp_sum(sg);
+  if (lane == 0) red[warp] = sg;
   __syncthreads();
-  householder(rw, 1, n, vc, red, sc);
+  if (warp == 0) {
+    double t = lane < NW ? red[lane] : 0.0;
+    t += __shfl_xor_sync(0xffffffffu, t, 4);
+    t += __shfl_xor_sync(0xffffffffu, t, 2);
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    if (lane == 0) reflector_scalars(vc[1], t, sc);
+  }
+  __syncthreads();
   double tj = sc[0];
+  const double d0 = vc[0];
+  __syncthreads();
+  if (threadIdx.x == 0) vc[1] = sc[2];
+  __syncthreads();
   if (cta == 0) {
     for (int l = 1 + threadIdx.x; l < n; l += NT) a.V[l] = vc[l];
     if (threadIdx.x == 0) {
-      a.d[0] = rw[0];
+      a.d[0] = d0;
       a.e[0] = sc[1];
       a.tau[0] = tj;
     }
@@ -298,26 +299,28 @@ __global__ void __launch_bounds__(NT) tridiag_kernel(TriArgs a) {
     // pass over the owned rows i > j: A^(j) = A^(j-1) - v w^T - w v^T, p_i = tau_j A^(j)_i. v_j
     double dotp = 0.0;
     const int r0 = j + 1 > cta ? (j + 1 - cta + P - 1) / P : 0;
+    const bool upd = j >= 1;
     for (int r = r0 + warp; r < nown; r += NW) {
       const int i = cta + r * P;
       double* row = SMEM ? rows + (int64_t)r * n : a.A + (int64_t)i * a.lda;
-      const bool upd = j >= 1;
       const double vpi = upd ? vp[i] : 0.0, wpi = upd ? wp[i] : 0.0;
       const bool pub = i == j + 1;
       double acc0 = 0.0, acc1 = 0.0;
-      for (int l = j + 1 + lane; l < n; l += 64) {
-        double x = row[l];
-        if (upd) x = fma(-vpi, wp[l], fma(-wpi, vp[l], x));
-        row[l] = x;
-        if (pub) rb[l] = x;
-        acc0 = fma(x, vc[l], acc0);
-        const int l2 = l + 32;
-        if (l2 < n) {
-          double y = row[l2];
-          if (upd) y = fma(-vpi, wp[l2], fma(-wpi, vp[l2], y));
-          row[l2] = y;
-          if (pub) rb[l2] = y;
-          acc1 = fma(y, vc[l2], acc1);
+      for (int l = j + 1 + lane; l < n; l += 8 * 32) {
+        double x[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) x[q] = l + 32 * q < n ? row[l + 32 * q] : 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+          const int ll = l + 32 * q;
+          if (ll < n) {
+            double y = x[q];
+            if (upd) y = fma(-vpi, wp[ll], fma(-wpi, vp[ll], y));
+            row[ll] = y;
+            if (pub) rb[ll] = y;
+            if (q & 1) acc1 = fma(y, vc[ll], acc1);
+            else acc0 = fma(y, vc[ll], acc0);
+          }
         }
       }
       const double pi = warp_sum(acc0 + acc1) * tj;
@@ -334,36 +337,82 @@ __global__ void __launch_bounds__(NT) tridiag_kernel(TriArgs a) {
       a.dotbuf[par * P + cta] = s;
     }
     if (!tri_barrier(a, (unsigned)P * (unsigned)(j + 1), &s_ok)) return;
-    // every CTA: K = tau/2 p.v, w_j = p - K v_j, row j+1 of A^(j+1), next reflector
+    // every CTA: K = tau/2 p.v, w_j = p - K v_j, row j+1 of A^(j+1), next reflector.
+    // The first 4 NT elements of p and of the published row are loaded before the
+    // reduction of K so that the two L2 round trips overlap.
+    const int l0 = j + 1 + threadIdx.x;
+    double pv[4], rv[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int ll = l0 + q * NT;
+      pv[q] = ll < n ? __ldcg(pb + ll) : 0.0;
+      rv[q] = ll < n ? __ldcg(rb + ll) : 0.0;
+    }
+    const double p1 = __ldcg(pb + j + 1);
     if (warp == 0) {
       double s = 0.0;
       for (int c = lane; c < P; c += 32) s += __ldcg(a.dotbuf + par * P + c);
       s = warp_sum(s);
-      if (lane == 0) sc[2] = 0.5 * tj * s;
+      if (lane == 0) sc[3] = 0.5 * tj * s;
     }
     __syncthreads();
-    const double K = sc[2];
-    const double w1 = __ldcg(pb + j + 1) - K;   // w_{j+1} (v_j[j+1] = 1)
-    for (int l = j + 1 + threadIdx.x; l < n; l += NT) {
-      const double wl = fma(-K, vc[l], __ldcg(pb + l));
-      wp[l] = wl;
-      rw[l] = __ldcg(rb + l) - wl - w1 * vc[l];
+    const double K = sc[3];
+    const double v1 = vc[j + 1];
+    const double w1 = fma(-K, v1, p1);   // w_j[j+1]
+    double sig = 0.0;
+    for (int l = l0; l < n; l += 4 * NT) {
+      if (l > l0) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int ll = l + q * NT;
+          pv[q] = ll < n ? __ldcg(pb + ll) : 0.0;
+          rv[q] = ll < n ? __ldcg(rb + ll) : 0.0;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int ll = l + q * NT;
+        if (ll < n) {
+          const double vl = vc[ll];
+          const double wl = fma(-K, vl, pv[q]);
+          const double x = fma(-w1, vl, fma(-v1, wl, rv[q]));
+          wp[ll] = wl;
+          rw[ll] = x;
+          if (ll >= j + 3) sig = fma(x, x, sig);
+        }
+      }
     }
+    sig = warp_sum(sig);
+    if (lane == 0) red[warp] = sig;
     __syncthreads();
     if (j <= n - 3) {
-      householder(rw, j + 2, n, vp, red, sc);
+      if (warp == 0) {
+        double t = lane < NW ? red[lane] : 0.0;
+        t += __shfl_xor_sync(0xffffffffu, t, 4);
+        t += __shfl_xor_sync(0xffffffffu, t, 2);
+        t += __shfl_xor_sync(0xffffffffu, t, 1);
+        if (lane == 0) {
+          const double dj = rw[j + 1];
+          reflector_scalars(rw[j + 2], t, sc);
+          rw[j + 2] = sc[2];        // v_{j+1} = rw with its first element replaced
+          sc[3] = dj;
+        }
+      }
+      __syncthreads();
       tj = sc[0];
-      if (cta == 0) {
-        for (int l = j + 2 + threadIdx.x; l < n; l += NT) a.V[l + (int64_t)(j + 1) * n] = vp[l];
+      const int wcta = (j + 1) % P;
+      if (cta == wcta) {
+        for (int l = j + 2 + threadIdx.x; l < n; l += NT) a.V[l + (int64_t)(j + 1) * n] = rw[l];
         if (threadIdx.x == 0) {
-          a.d[j + 1] = rw[j + 1];
+          a.d[j + 1] = sc[3];
           a.e[j + 1] = sc[1];
           a.tau[j + 1] = tj;
         }
       }
-      double* t = vc;   // v_{j+1} becomes current, v_j previous
-      vc = vp;
-      vp = t;
+      double* t = vp;   // v_{j-1} is free: it becomes the next work vector
+      vp = vc;
+      vc = rw;
+      rw = t;
     } else if (cta == 0 && threadIdx.x == 0) {
       a.d[n - 1] = rw[n - 1];
       a.e[n - 1] = 0.0;
@@ -372,7 +421,6 @@ __global__ void __launch_bounds__(NT) tridiag_kernel(TriArgs a) {
     __syncthreads();
   }
 }
-
 
 // ------------------------------------------------------- divide and conquer ----
 //
@@ -843,13 +891,15 @@ __global__ void __launch_bounds__(NT) dc_rotperm_kernel(DcArgs a, int depth) {
 }
 
 // Batched FP64 GEMM of the merge: Zt[a:b, a:c] = Z[a:b, a:b] M[a:b, a:c] and
-// Zt[b:c, a:c] = Z[b:c, b:c] M[b:c, a:c] (Z, Zt column-major, M row-major).  64 x 64
-// output tile per CTA, 4 x 4 per thread, k-steps of 16 through shared memory.
-// blockIdx.x: column tile; blockIdx.y: row tile (first the tiles of block 1, rt1 of
-// them, then those of block 2); blockIdx.z: node.
+// Zt[b:c, a:c] = Z[b:c, b:c] M[b:c, a:c] (Z, Zt column-major, M row-major).  32 x 64
+// output tile per CTA (small tiles: the top merges have only a few hundred tiles for 152
+// SMs), 2 x 4 per thread, k-steps of 16 through shared memory.  blockIdx.x: column tile;
+// blockIdx.y: row tile (first the rt1 tiles of block 1, then those of block 2);
+// blockIdx.z: node.
+constexpr int GTM = 32, GTN = 64, GTK = 16;
 __global__ void __launch_bounds__(NT) dc_gemm_kernel(DcArgs a, int depth, int rt1) {
-  __shared__ __align__(16) double As[16][64];
-  __shared__ __align__(16) double Bs[16][64];
+  __shared__ __align__(16) double As[GTK][GTM];
+  __shared__ __align__(16) double Bs[GTK][GTN];
   int A0, B0, C0;
   node_range(a.n, depth, blockIdx.z, &A0, &B0, &C0);
   const int N = C0 - A0;
@@ -863,47 +913,48 @@ __global__ void __launch_bounds__(NT) dc_gemm_kernel(DcArgs a, int depth, int rt
     kd = C0 - B0;
   }
   const int rt = (int)blockIdx.y < rt1 ? blockIdx.y : blockIdx.y - rt1;
-  const int row0 = rt * 64, col0 = blockIdx.x * 64;
+  const int row0 = rt * GTM, col0 = blockIdx.x * GTN;
   if (row0 >= kd || col0 >= N) return;
   const int64_t ld = a.ldz;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4];
+  double acc[2][4];
 #pragma unroll
-  for (int i = 0; i < 4; i++)
+  for (int i = 0; i < 2; i++)
 #pragma unroll
     for (int jj = 0; jj < 4; jj++) acc[i][jj] = 0.0;
-  for (int k0 = 0; k0 < kd; k0 += 16) {
-    // A tile: rows r0+row0 .. +63, k columns r0+k0 .. +15
-    for (int q = threadIdx.x; q < 16 * 64; q += NT) {
-      const int kk = q >> 6, rr = q & 63;
+  for (int k0 = 0; k0 < kd; k0 += GTK) {
+    for (int q = threadIdx.x; q < GTK * GTM; q += NT) {
+      const int kk = q / GTM, rr = q % GTM;
       const int gr = row0 + rr, gk = k0 + kk;
       As[kk][rr] = gr < kd && gk < kd ? a.Z[(int64_t)(r0 + gr) + (int64_t)(r0 + gk) * ld] : 0.0;
-      const int cc = rr;
-      const int gc = col0 + cc;
+    }
+    for (int q = threadIdx.x; q < GTK * GTN; q += NT) {
+      const int kk = q / GTN, cc = q % GTN;
+      const int gk = k0 + kk, gc = col0 + cc;
       Bs[kk][cc] = gk < kd && gc < N ? a.M[(int64_t)(r0 + gk) * ld + A0 + gc] : 0.0;
     }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < 16; kk++) {
-      double av[4], bv[4];
+    for (int kk = 0; kk < GTK; kk++) {
+      const double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
+      double bv[4];
 #pragma unroll
-      for (int i = 0; i < 4; i++) av[i] = As[kk][ty * 4 + i];
+      for (int jj = 0; jj < 4; jj++) bv[jj] = Bs[kk][tx + 16 * jj];
 #pragma unroll
-      for (int jj = 0; jj < 4; jj++) bv[jj] = Bs[kk][tx * 4 + jj];
-#pragma unroll
-      for (int i = 0; i < 4; i++)
-#pragma unroll
-        for (int jj = 0; jj < 4; jj++) acc[i][jj] = fma(av[i], bv[jj], acc[i][jj]);
+      for (int jj = 0; jj < 4; jj++) {
+        acc[0][jj] = fma(a0, bv[jj], acc[0][jj]);
+        acc[1][jj] = fma(a1, bv[jj], acc[1][jj]);
+      }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; i++) {
-    const int gr = row0 + ty * 4 + i;
+  for (int i = 0; i < 2; i++) {
+    const int gr = row0 + ty * 2 + i;
     if (gr >= kd) continue;
 #pragma unroll
     for (int jj = 0; jj < 4; jj++) {
-      const int gc = col0 + tx * 4 + jj;
+      const int gc = col0 + tx + 16 * jj;
       if (gc < N) a.Zt[(int64_t)(r0 + gr) + (int64_t)(A0 + gc) * ld] = acc[i][jj];
     }
   }
@@ -1181,8 +1232,8 @@ cudaError_t launch_sym_eig(double* A, int64_t lda, int n, double* w, void* work,
     dc_order_kernel<<<nodes, NT, (size_t)p2 * 12, st>>>(a, d, p2), count_launch();
     dc_build_m_kernel<<<dim3((Nmax + 31) / 32, (Nmax + 63) / 64, nodes), NT, 0, st>>>(a, d), count_launch();
     dc_rotperm_kernel<<<dim3((Nmax + NT - 1) / NT, nodes), NT, 0, st>>>(a, d), count_launch();
-    const int rt = (Nmax / 2 + 1 + 63) / 64;
-    dc_gemm_kernel<<<dim3((Nmax + 63) / 64, 2 * rt, nodes), NT, 0, st>>>(a, d, rt), count_launch();
+    const int rt = (Nmax / 2 + 1 + GTM - 1) / GTM;
+    dc_gemm_kernel<<<dim3((Nmax + GTN - 1) / GTN, 2 * rt, nodes), NT, 0, st>>>(a, d, rt), count_launch();
     const int cb = (int)std::min<int64_t>(256, ((int64_t)Nmax * Nmax + NT - 1) / NT);
     dc_copy_kernel<<<dim3(cb, nodes), NT, 0, st>>>(a, d), count_launch();
   }
