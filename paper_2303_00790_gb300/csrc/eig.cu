@@ -186,23 +186,28 @@ struct TriArgs {
   long long spin_limit;
 };
 
+// Grid-wide barrier of the tridiagonalisation: arrival by a release reduction on a
+// monotonic counter, then acquire loads until all P arrivals of this step are seen (the
+// bar.sync before and after orders the other threads of the CTA).  Bounded: after
+// spin_limit clock cycles, or when another CTA gave up, the status word is set and
+// false returned.
 __device__ bool tri_barrier(const TriArgs& a, unsigned target, int* s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(a.bar, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.bar) : "memory");
     int ok = 1;
-    volatile unsigned* cnt = a.bar;
     volatile int* to = a.status;
     const long long t0 = clock64();
-    while (*cnt < target) {
+    for (;;) {
+      unsigned c;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(c) : "l"(a.bar) : "memory");
+      if (c >= target) break;
       if (*to != 0 || clock64() - t0 > a.spin_limit) {
         atomicExch(a.status, 1);
         ok = 0;
         break;
       }
     }
-    __threadfence();
     *s_ok = ok;
   }
   __syncthreads();
@@ -299,7 +304,7 @@ __global__ void __launch_bounds__(NT, 1) tridiag_kernel(TriArgs a) {
     // pass over the owned rows i > j: A^(j) = A^(j-1) - v w^T - w v^T, p_i = tau_j A^(j)_i. v_j
     double dotp = 0.0;
     const int r0 = j + 1 > cta ? (j + 1 - cta + P - 1) / P : 0;
-    const bool upd = j >= 1;
+    const bool upd = !SMEM && j >= 1;   // shared-memory rows were updated in the last step
     for (int r = r0 + warp; r < nown; r += NW) {
       const int i = cta + r * P;
       double* row = SMEM ? rows + (int64_t)r * n : a.A + (int64_t)i * a.lda;
@@ -315,8 +320,10 @@ __global__ void __launch_bounds__(NT, 1) tridiag_kernel(TriArgs a) {
           const int ll = l + 32 * q;
           if (ll < n) {
             double y = x[q];
-            if (upd) y = fma(-vpi, wp[ll], fma(-wpi, vp[ll], y));
-            row[ll] = y;
+            if (upd) {
+              y = fma(-vpi, wp[ll], fma(-wpi, vp[ll], y));
+              row[ll] = y;
+            }
             if (pub) rb[ll] = y;
             if (q & 1) acc1 = fma(y, vc[ll], acc1);
             else acc0 = fma(y, vc[ll], acc0);
@@ -396,6 +403,29 @@ __global__ void __launch_bounds__(NT, 1) tridiag_kernel(TriArgs a) {
           reflector_scalars(rw[j + 2], t, sc);
           rw[j + 2] = sc[2];        // v_{j+1} = rw with its first element replaced
           sc[3] = dj;
+        }
+      } else if (SMEM && (warp & 3) != 0) {
+        // meanwhile the warps of the other three SM sub-partitions (whose FP64 pipes the
+        // scalar chain does not use) update the owned rows i >= j+2 to A^(j+1) over the
+        // columns l >= j+2, in items of one row x 256 columns
+        const int u = (warp >> 2) * 3 + (warp & 3) - 1;
+        const int rs = j + 2 > cta ? (j + 2 - cta + P - 1) / P : 0;
+        const int nch = (n - (j + 2) + 255) / 256;
+        const int items = (nown - rs) * nch;
+        for (int it = u; it < items; it += NW - NW / 4) {
+          const int r = rs + it / nch;
+          const int i = cta + r * P;
+          double* row = rows + (int64_t)r * n;
+          const double vi = vc[i], wi = wp[i];
+          const int lb = j + 2 + (it % nch) * 256 + lane;
+          double x[8];
+#pragma unroll
+          for (int q = 0; q < 8; q++) x[q] = lb + 32 * q < n ? row[lb + 32 * q] : 0.0;
+#pragma unroll
+          for (int q = 0; q < 8; q++) {
+            const int ll = lb + 32 * q;
+            if (ll < n) row[ll] = fma(-vi, wp[ll], fma(-wi, vc[ll], x[q]));
+          }
         }
       }
       __syncthreads();
