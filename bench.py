@@ -66,6 +66,12 @@ def parse():
     p.add_argument("--filter-sweep", action="store_true",
                    help="filter throughput and roofline fraction over brick size (8, 16) and column block width "
                         "(32, 64, 128) on the first 1024 columns of --workload (default si3325h876)")
+    p.add_argument("--eig-bench", action="store_true",
+                   help="the FP64 k x k eigensolver of Rayleigh-Ritz (kscf_sym_eig) against cuSOLVER syevd "
+                        "(torch.linalg.eigh) on the same matrices, CUDA events")
+    p.add_argument("--eig-sizes", default="850,1654,4600", help="matrix orders for --eig-bench")
+    p.add_argument("--eig-no-ref", action="store_true",
+                   help="--eig-bench without the cuSOLVER comparison (for profiling the library's kernels)")
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-start comparison (train on 30 clusters, SCF on a held-out one)")
     return p.parse_args()
@@ -710,8 +716,81 @@ def run_filter_sweep(args):
                                        "peak_gbs": peak, "peak_source": peak_src, "results": results}}), flush=True)
 
 
+def run_eig_bench(args):
+    """kscf_sym_eig vs cuSOLVER's syevd (through torch.linalg.eigh) on seeded symmetric
+    matrices: a Ritz-like one (sorted diagonal in [-0.8, 0.1] Ha plus a symmetric coupling
+    of 1e-4, the shape Rayleigh-Ritz sees once CheFSI has settled) and a Gaussian one.
+    Best and median of 5 calls (2 at n > 3000) after 2 warm-up calls, CUDA events on the
+    current stream; accuracy against cuSOLVER's eigenvalues and the residual and
+    orthogonality of the returned vectors."""
+    import ctypes as C
+    import torch
+    from paper_2303_00790_gb300 import kscf
+    torch.cuda.init()
+    st = torch.cuda.current_stream()
+    out = []
+    for n in [int(x) for x in args.eig_sizes.split(",") if x]:
+        for kind in (("ritz", "gaussian") if n <= 1000 else ("gaussian",)):
+            rng = np.random.default_rng(n + (1 if kind == "ritz" else 2))
+            if kind == "ritz":
+                E = rng.standard_normal((n, n)) * 1e-4
+                A = np.diag(np.sort(rng.uniform(-0.8, 0.1, n))) + (E + E.T) / 2
+            else:
+                B = rng.standard_normal((n, n))
+                A = (B + B.T) / 2
+            Ad = torch.tensor(A, dtype=torch.float64, device="cuda")
+            w = torch.empty(n, dtype=torch.float64, device="cuda")
+            b = C.c_size_t()
+            kscf._check(kscf.lib.kscf_sym_eig_work_bytes(n, C.byref(b)))
+            work = torch.empty(b.value, dtype=torch.uint8, device="cuda")
+            X = torch.empty_like(Ad)
+
+            def ours():
+                X.copy_(Ad)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                kscf._check(kscf.lib.kscf_sym_eig(C.c_void_p(X.data_ptr()), n, n, C.c_void_p(w.data_ptr()),
+                                                  C.c_void_p(work.data_ptr()), work.numel(),
+                                                  C.c_void_p(st.cuda_stream)))
+                e1.record(st)
+                torch.cuda.synchronize()
+                return e0.elapsed_time(e1)
+
+            def lib():
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                L, _ = torch.linalg.eigh(Ad)
+                e1.record(st)
+                torch.cuda.synchronize()
+                return e0.elapsed_time(e1), L
+
+            reps = 5 if n <= 3000 else 2
+            for _ in range(2):
+                ours()
+                if not args.eig_no_ref:
+                    lib()
+            t_o = sorted(ours() for _ in range(reps))
+            Z = X.t()   # column-major eigenvectors
+            eye = torch.eye(n, dtype=torch.float64, device="cuda")
+            r = {"n": n, "matrix": kind, "kscf_ms": t_o[0], "kscf_ms_median": t_o[len(t_o) // 2],
+                 "residual_rel": float((Ad @ Z - Z * w).abs().max() / Ad.abs().max()),
+                 "orthogonality": float((Z.t() @ Z - eye).abs().max())}
+            if not args.eig_no_ref:
+                t_l = sorted(lib()[0] for _ in range(reps))
+                L = lib()[1]
+                r.update({"cusolver_ms": t_l[0], "cusolver_ms_median": t_l[len(t_l) // 2],
+                          "speedup": t_l[0] / t_o[0], "eig_err_rel": float((w - L).abs().max() / L.abs().max())})
+            out.append(r)
+            del Ad, X, work
+            torch.cuda.empty_cache()
+    print(json.dumps({"eig_bench": out}), flush=True)
+
+
 def main():
     args = parse()
+    if args.eig_bench:
+        run_eig_bench(args)
+        return
     if args.filter_sweep:
         run_filter_sweep(args)
         return

@@ -110,7 +110,7 @@ typedef struct kscf_grid_info {
 const char* kscf_last_error(void);
 
 /* Number of CUDA kernels this library has launched since it was loaded (all threads;
- * kernels launched inside cuSOLVER are not counted).  For launch accounting. */
+ * every kernel of the path is the library's own).  For launch accounting. */
 uint64_t kscf_launch_counter(void);
 
 /* ---------------------------------------------------------------------------------
