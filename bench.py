@@ -165,21 +165,20 @@ def max_over_ranks(x: float, world: int) -> float:
 
 
 # ------------------------------------------------------------------ oracle (CPU) legs
-ORACLE_SAMPLE_COLS = 64
 
 
 class OracleSample:
     """The FP64 CPU oracle on a bounded sample of one CheFSI step of the workload, the
     same sample in the cpu_baseline leg and in the reference arm.
 
-    The filter's degree steps and the Rayleigh-Ritz H*X are applied column by column
-    (each column of p_m(H)X and of HX depends on that column alone), so they are timed on
-    the first ORACLE_SAMPLE_COLS columns and scaled by k / ORACLE_SAMPLE_COLS.  Everything
-    that couples the columns -- the Gram matrices, the Cholesky factor, the triangular
-    solve, the k x k eigensolve, the rotations and the density -- runs at the full k
-    columns.  step seconds = scaled column-separable time + full-width time."""
+    Every part runs at the full k columns.  The filter's m degree steps each apply the same
+    operator (H, a shift and a scaling) to a block of the same size, so one degree step
+    (a degree-1 filter: H*X plus the shifted scaling) is timed and multiplied by m; the
+    Rayleigh-Ritz H*X, the Cholesky-QR of the block, the Gram matrices, the k x k
+    eigensolve, the rotations and the density are timed as they are.
+    step seconds = m * (one degree step) + everything else."""
 
-    def __init__(self, w, cols: int = ORACLE_SAMPLE_COLS):
+    def __init__(self, w):
         from oracle.system import cluster_hamiltonian
         from oracle import chefsi as orc
         from workloads import pseudo_params, random_block_lex
@@ -188,7 +187,6 @@ class OracleSample:
         self.orc = orc
         self.OH = cluster_hamiltonian(pos, z, pseudo_params(), w.radius, w.h)
         self.b = orc.spectral_upper_bound(self.OH)
-        self.cols = min(cols, w.k)
         X, _ = orc.cholesky_qr(random_block_lex(1, self.OH.n, w.k), self.OH.h3)
         self.X = X
         self.n_occ = min(w.k, 4)
@@ -197,36 +195,49 @@ class OracleSample:
         orc, OH, X, h3, k = self.orc, self.OH, self.X, self.OH.h3, self.w.k
         lam_hi, lam_lo = self.b - 10.0, self.b - 20.0
         t0 = time.perf_counter()
-        orc.chebyshev_filter(OH, X[:, :self.cols], self.w.degree, lam_hi, self.b, lam_lo)
-        t_filter = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        HXc = OH.apply(X[:, :self.cols])
-        t_apply = time.perf_counter() - t0
-        # full width: Cholesky-QR of the block, then the Rayleigh-Ritz steps after H*X
-        # (a stand-in with HX's shape: the timing does not depend on the values)
+        Y = orc.chebyshev_filter(OH, X, 1, lam_hi, self.b, lam_lo)
+        t_step = time.perf_counter() - t0
+        del Y
         t0 = time.perf_counter()
         Xq, _ = orc.cholesky_qr(X, h3)
-        HX = X
+        HX = OH.apply(Xq)
         Hs = h3 * (Xq.T @ HX)
         Hs = 0.5 * (Hs + Hs.T)
         lam, Q = np.linalg.eigh(Hs)
-        Xr, HXr = Xq @ Q, HX @ Q
+        Xr = Xq @ Q
         orc.density(Xr, np.full(self.n_occ, 2.0))
-        t_full = time.perf_counter() - t0
-        del HXc, Xr, HXr
-        scale = k / self.cols
-        seconds = (t_filter + t_apply) * scale + t_full
-        cpu = t_filter + t_apply + t_full
-        units = OH.n * k * self.w.degree
+        t_rest = time.perf_counter() - t0
+        del HX, Xr, Xq
+        m = self.w.degree
+        seconds = m * t_step + t_rest
+        cpu = t_step + t_rest
+        units = OH.n * k * m
         return units / seconds / 1e9, {"n_points": OH.n, "seconds": seconds, "cpu_seconds": cpu,
-                                       "filter_s": t_filter * scale, "apply_s": t_apply * scale, "full_s": t_full}
+                                       "filter_s": m * t_step, "rest_s": t_rest}
 
     def describe(self, info):
-        return (f"one CheFSI step of the FP64 CPU oracle ({info['n_points']} points, k={self.w.k}, degree "
-                f"{self.w.degree}): the filter and the Rayleigh-Ritz H*X timed on {self.cols} of {self.w.k} columns "
-                f"and scaled by {self.w.k}/{self.cols} (columns are independent there); Cholesky-QR, the "
-                f"Rayleigh-Ritz Gram, eigensolve and rotations and the density at all {self.w.k} columns; "
-                f"{info['cpu_seconds']:.1f} s of CPU work for a {info['seconds']:.1f} s step")
+        return (f"one CheFSI step of the FP64 CPU oracle ({info['n_points']} points, all k={self.w.k} columns, "
+                f"degree {self.w.degree}): one filter degree step timed and multiplied by {self.w.degree} (every "
+                f"degree step applies the same operator to the same block), Cholesky-QR, the Rayleigh-Ritz H*X, "
+                f"Gram, eigensolve and rotation and the density timed as they are; {info['cpu_seconds']:.1f} s of "
+                f"CPU work for a {info['seconds']:.1f} s step")
+
+
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name, or the Arm implementer/part codes)."""
+    try:
+        txt = open("/proc/cpuinfo").read()
+    except OSError:
+        return "unknown"
+    for line in txt.splitlines():
+        if line.lower().startswith("model name"):
+            return line.split(":", 1)[1].strip()
+    imp = [l.split(":", 1)[1].strip() for l in txt.splitlines() if l.startswith("CPU implementer")]
+    part = [l.split(":", 1)[1].strip() for l in txt.splitlines() if l.startswith("CPU part")]
+    if imp and part:
+        names = {("0x41", "0xd4f"): "Arm Neoverse V2"}
+        return f"{names.get((imp[0], part[0]), 'Arm')} (implementer {imp[0]}, part {part[0]})"
+    return "unknown"
 
 
 def cpu_threads() -> int:
@@ -259,8 +270,8 @@ def run_reference(args):
             "data": "synthetic",
             "config": {"workload": w.name, "n_points": info["n_points"], "k": w.k, "degree": w.degree,
                        "parallelism": "single"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                             "sample": sampler.describe(info)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "cpu": cpu_model(),
+                             "kind": "oracle", "sample": sampler.describe(info)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -628,8 +639,8 @@ def run_kscf(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sampler = OracleSample(w)
         v, info = sampler.step_seconds()
-        cpu = {"value": v, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sampler.describe(info),
-               "parts_s": {"filter": info["filter_s"], "rr_apply": info["apply_s"], "full_width": info["full_s"]}}
+        cpu = {"value": v, "unit": UNIT, "cores": cpu_threads(), "cpu": cpu_model(), "kind": "oracle",
+               "sample": sampler.describe(info), "parts_s": {"filter": info["filter_s"], "rest": info["rest_s"]}}
 
     scf = None
     x_mib = X.numel() * 4 / 2**20
