@@ -534,13 +534,10 @@ __device__ __forceinline__ int lower_count(const double* x, int len, double v, b
 }
 
 // One CTA per merge: z, the sorted merge of the two pole lists, deflation.
-__global__ void __launch_bounds__(NT) dc_deflate_kernel(DcArgs a, int depth) {
+__device__ void dc_deflate_node(const DcArgs& a, int A0, int B0, int C0) {
   __shared__ double red[NW];
   __shared__ int ired[NW];
-  int A0, B0, C0;
-  node_range(a.n, depth, blockIdx.x, &A0, &B0, &C0);
   const int N = C0 - A0, n1 = B0 - A0;
-  if (N < 2) return;
   const int64_t ld = a.ldz;
   const double beta = a.es[B0 - 1];
   const double sgn = beta >= 0.0 ? 1.0 : -1.0;
@@ -634,6 +631,12 @@ __global__ void __launch_bounds__(NT) dc_deflate_kernel(DcArgs a, int depth) {
   if (threadIdx.x == 0) a.Kof[A0] = tot;
 }
 
+__global__ void __launch_bounds__(NT) dc_deflate_kernel(DcArgs a, int depth) {
+  int A0, B0, C0;
+  node_range(a.n, depth, blockIdx.x, &A0, &B0, &C0);
+  if (C0 - A0 >= 2) dc_deflate_node(a, A0, B0, C0);
+}
+
 // Secular equation 1 + rho sum_i z_i^2 / (d_i - lambda) = 0, one warp per root j of the K
 // kept poles d_0 < ... < d_{K-1}.  Root j lies in (d_j, d_{j+1}) (j < K-1) or in
 // (d_{K-1}, d_{K-1} + rho |z|^2].  The origin is the nearer pole (sign of the secular
@@ -643,14 +646,8 @@ __global__ void __launch_bounds__(NT) dc_deflate_kernel(DcArgs a, int depth) {
 // d_{j+1} for phi; one pole for the last root) and takes the root of that model inside
 // the bracket, else bisects.  Stops when |g| is below its rounding bound or the bracket
 // has collapsed.
-__global__ void __launch_bounds__(NT) dc_secular_kernel(DcArgs a, int depth) {
-  int A0, B0, C0;
-  node_range(a.n, depth, blockIdx.y, &A0, &B0, &C0);
-  if (C0 - A0 < 2) return;
-  const int K = a.Kof[A0];
-  const int j = blockIdx.x * NW + (threadIdx.x >> 5);
+__device__ void dc_secular_root(const DcArgs& a, int A0, int B0, int K, int j) {
   const int lane = threadIdx.x & 31;
-  if (j >= K) return;
   const double rho = 2.0 * fabs(a.es[B0 - 1]);
   const double* dk = a.dk + A0;
   const double* zz = a.zz + A0;
@@ -745,16 +742,19 @@ __global__ void __launch_bounds__(NT) dc_secular_kernel(DcArgs a, int depth) {
   }
 }
 
-// Gu-Eisenstat: zh_i^2 = prod_j (lambda_j - d_i) / (rho prod_{j != i} (d_j - d_i)), the
-// sign of z_i; lambda_j - d_i = (d_{o_j} - d_i) + tau_j.  One warp per kept pole.
-__global__ void __launch_bounds__(NT) dc_zhat_kernel(DcArgs a, int depth) {
+__global__ void __launch_bounds__(NT) dc_secular_kernel(DcArgs a, int depth) {
   int A0, B0, C0;
   node_range(a.n, depth, blockIdx.y, &A0, &B0, &C0);
   if (C0 - A0 < 2) return;
   const int K = a.Kof[A0];
-  const int i = blockIdx.x * NW + (threadIdx.x >> 5);
+  const int j = blockIdx.x * NW + (threadIdx.x >> 5);
+  if (j < K) dc_secular_root(a, A0, B0, K, j);
+}
+
+// Gu-Eisenstat: zh_i^2 = prod_j (lambda_j - d_i) / (rho prod_{j != i} (d_j - d_i)), the
+// sign of z_i; lambda_j - d_i = (d_{o_j} - d_i) + tau_j.  One warp per kept pole.
+__device__ void dc_zhat_one(const DcArgs& a, int A0, int B0, int K, int i) {
   const int lane = threadIdx.x & 31;
-  if (i >= K) return;
   const double rho = 2.0 * fabs(a.es[B0 - 1]);
   const double* dk = a.dk + A0;
   const double di = dk[i];
@@ -767,15 +767,18 @@ __global__ void __launch_bounds__(NT) dc_zhat_kernel(DcArgs a, int depth) {
   if (lane == 0) a.zh[A0 + i] = copysign(sqrt(fabs(p) * recip(rho)), a.zk[A0 + i]);
 }
 
-// 1 / |u_j|, u_j[i] = zh_i / (d_i - lambda_j).  One warp per root.
-__global__ void __launch_bounds__(NT) dc_colnorm_kernel(DcArgs a, int depth) {
+__global__ void __launch_bounds__(NT) dc_zhat_kernel(DcArgs a, int depth) {
   int A0, B0, C0;
   node_range(a.n, depth, blockIdx.y, &A0, &B0, &C0);
   if (C0 - A0 < 2) return;
   const int K = a.Kof[A0];
-  const int j = blockIdx.x * NW + (threadIdx.x >> 5);
+  const int i = blockIdx.x * NW + (threadIdx.x >> 5);
+  if (i < K) dc_zhat_one(a, A0, B0, K, i);
+}
+
+// 1 / |u_j|, u_j[i] = zh_i / (d_i - lambda_j).  One warp per root.
+__device__ void dc_colnorm_one(const DcArgs& a, int A0, int K, int j) {
   const int lane = threadIdx.x & 31;
-  if (j >= K) return;
   const double* dk = a.dk + A0;
   const double dorg = dk[min(max(a.orig[A0 + j], 0), K - 1)], tau = a.tauk[A0 + j];
   double s = 0.0;
@@ -787,6 +790,15 @@ __global__ void __launch_bounds__(NT) dc_colnorm_kernel(DcArgs a, int depth) {
   if (lane == 0) a.invn[A0 + j] = rsqrt_pos(s);
 }
 
+__global__ void __launch_bounds__(NT) dc_colnorm_kernel(DcArgs a, int depth) {
+  int A0, B0, C0;
+  node_range(a.n, depth, blockIdx.y, &A0, &B0, &C0);
+  if (C0 - A0 < 2) return;
+  const int K = a.Kof[A0];
+  const int j = blockIdx.x * NW + (threadIdx.x >> 5);
+  if (j < K) dc_colnorm_one(a, A0, K, j);
+}
+
 // order-preserving integer key of a double
 __device__ __forceinline__ unsigned long long dkey(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
@@ -795,14 +807,7 @@ __device__ __forceinline__ unsigned long long dkey(double v) {
 
 // Final ascending order of the merge's N eigenvalues (kept roots and deflated poles):
 // bitonic sort of (key, reference) pairs in shared memory; lam[a + col] and colref.
-__global__ void __launch_bounds__(NT) dc_order_kernel(DcArgs a, int depth, int npow) {
-  extern __shared__ __align__(16) unsigned char smb[];
-  unsigned long long* key = (unsigned long long*)smb;
-  int* ref = (int*)(key + npow);
-  int A0, B0, C0;
-  node_range(a.n, depth, blockIdx.x, &A0, &B0, &C0);
-  const int N = C0 - A0;
-  if (N < 2) return;
+__device__ void dc_order_node(const DcArgs& a, int A0, int N, unsigned long long* key, int* ref) {
   const int K = a.Kof[A0];
   int p2 = 1;
   while (p2 < N) p2 <<= 1;
@@ -857,12 +862,64 @@ __global__ void __launch_bounds__(NT) dc_order_kernel(DcArgs a, int depth, int n
   }
 }
 
+__global__ void __launch_bounds__(NT) dc_order_kernel(DcArgs a, int depth, int npow) {
+  extern __shared__ __align__(16) unsigned char smb[];
+  int A0, B0, C0;
+  node_range(a.n, depth, blockIdx.x, &A0, &B0, &C0);
+  if (C0 - A0 < 2) return;
+  dc_order_node(a, A0, C0 - A0, (unsigned long long*)smb, (int*)((unsigned long long*)smb + npow));
+}
+
 // Merge matrix M (row-major, rows = input columns of diag(Q1, Q2) in block order, columns =
 // merged eigenvectors in ascending order).  Column of kept root j: u_j[i] = zh_i /
 // (d_i - lambda_j) / |u_j| at the sorted position of kept pole i; column of deflated
 // position t: e_t.  With deflation rotations the columns go to W (rows = sorted
 // positions) for dc_rotperm_kernel, else straight to M through the sort permutation.
 // Tile: 32 columns x 64 rows per CTA.
+// value of the merge matrix at sorted position t, final column with reference r (kept
+// root j >= 0, or ~deflated position), with the root's origin pole, offset and 1/|u_j|
+__device__ __forceinline__ double dc_m_value(const DcArgs& a, int A0, int K, int t, int r, double dorg, double tau,
+                                             double inv) {
+  if (r >= 0) {
+    const int ki = a.kidx[A0 + t];
+    return ki >= 0 && ki < K ? a.zh[A0 + ki] * recip((a.dk[A0 + ki] - dorg) - tau) * inv : 0.0;
+  }
+  return t == ~r ? 1.0 : 0.0;
+}
+
+// column reference of a final column, guarded (only a failed sort gives a bad one), and
+// its root's origin pole, offset and 1/|u_j|
+__device__ __forceinline__ int dc_col_ref(const DcArgs& a, int A0, int N, int K, int col, double* dorg, double* tau,
+                                          double* inv) {
+  int r = a.colref[A0 + col];
+  if (r >= K || (r < 0 && ~r >= N)) r = ~0;
+  *dorg = 0.0;
+  *tau = 0.0;
+  *inv = 0.0;
+  if (r >= 0) {
+    *dorg = a.dk[A0 + min(max(a.orig[A0 + r], 0), K - 1)];
+    *tau = a.tauk[A0 + r];
+    *inv = a.invn[A0 + r];
+  }
+  return r;
+}
+
+// rotations (last to first) and the sort permutation for one column of W -> M
+__device__ void dc_rotperm_col(const DcArgs& a, int A0, int N, int col) {
+  const int64_t ld = a.ldz;
+  const int nr = a.nrot[A0];
+  double* Wc = a.Zt + A0 + col;
+  for (int q = min(nr, N) - 1; q >= 0; q--) {
+    const int p = min(max(a.rp[A0 + q], 0), N - 1), t = min(max(a.rt[A0 + q], 0), N - 1);
+    const double c = a.rc[A0 + q], s = a.rsn[A0 + q];
+    const double wp = Wc[(int64_t)(A0 + p) * ld], wt = Wc[(int64_t)(A0 + t) * ld];
+    Wc[(int64_t)(A0 + p) * ld] = fma(c, wp, s * wt);
+    Wc[(int64_t)(A0 + t) * ld] = fma(c, wt, -s * wp);
+  }
+  for (int t = 0; t < N; t++)
+    a.M[(int64_t)(A0 + min(max(a.idx[A0 + t], 0), N - 1)) * ld + A0 + col] = Wc[(int64_t)(A0 + t) * ld];
+}
+
 __global__ void __launch_bounds__(NT) dc_build_m_kernel(DcArgs a, int depth) {
   int A0, B0, C0;
   node_range(a.n, depth, blockIdx.z, &A0, &B0, &C0);
@@ -874,22 +931,10 @@ __global__ void __launch_bounds__(NT) dc_build_m_kernel(DcArgs a, int depth) {
   const int64_t ld = a.ldz;
   const bool rot = a.nrot[A0] > 0;
   const int K = a.Kof[A0];
-  int r = a.colref[A0 + col];
-  if (r >= K || (r < 0 && ~r >= N)) r = ~0;   // guard: only a failed sort gets here
-  double dorg = 0.0, tau = 0.0, inv = 0.0;
-  if (r >= 0) {
-    dorg = a.dk[A0 + min(max(a.orig[A0 + r], 0), K - 1)];
-    tau = a.tauk[A0 + r];
-    inv = a.invn[A0 + r];
-  }
+  double dorg, tau, inv;
+  const int r = dc_col_ref(a, A0, N, K, col, &dorg, &tau, &inv);
   for (int t = t0; t < min(N, blockIdx.y * 64 + 64); t += NW) {
-    double v;
-    if (r >= 0) {
-      const int ki = a.kidx[A0 + t];
-      v = ki >= 0 && ki < K ? a.zh[A0 + ki] * recip((a.dk[A0 + ki] - dorg) - tau) * inv : 0.0;
-    } else {
-      v = t == ~r ? 1.0 : 0.0;
-    }
+    const double v = dc_m_value(a, A0, K, t, r, dorg, tau, inv);
     if (rot) a.Zt[(int64_t)(A0 + t) * ld + A0 + col] = v;
     else a.M[(int64_t)(A0 + min(max(a.idx[A0 + t], 0), N - 1)) * ld + A0 + col] = v;
   }
@@ -902,22 +947,62 @@ __global__ void __launch_bounds__(NT) dc_rotperm_kernel(DcArgs a, int depth) {
   int A0, B0, C0;
   node_range(a.n, depth, blockIdx.y, &A0, &B0, &C0);
   const int N = C0 - A0;
-  if (N < 2) return;
-  const int nr = a.nrot[A0];
-  if (nr == 0) return;
+  if (N < 2 || a.nrot[A0] == 0) return;
   const int col = blockIdx.x * NT + threadIdx.x;
-  if (col >= N) return;
+  if (col < N) dc_rotperm_col(a, A0, N, col);
+}
+
+// Merges of at most 32 rows (the lowest depths, many small merges): one CTA per merge runs
+// every phase above in one launch, the phases separated by __syncthreads (the per-merge
+// arrays live in global memory and stay in L1/L2), the two block products element-wise.
+constexpr int DC_SMALL = 32;
+__global__ void __launch_bounds__(NT) dc_small_kernel(DcArgs a, int depth) {
+  __shared__ unsigned long long key[DC_SMALL];
+  __shared__ int ref[DC_SMALL];
+  int A0, B0, C0;
+  node_range(a.n, depth, blockIdx.x, &A0, &B0, &C0);
+  const int N = C0 - A0, n1 = B0 - A0;
+  if (N < 2) return;
+  const int warp = threadIdx.x >> 5;
   const int64_t ld = a.ldz;
-  double* Wc = a.Zt + A0 + col;
-  for (int q = min(nr, N) - 1; q >= 0; q--) {
-    const int p = min(max(a.rp[A0 + q], 0), N - 1), t = min(max(a.rt[A0 + q], 0), N - 1);
-    const double c = a.rc[A0 + q], s = a.rsn[A0 + q];
-    const double wp = Wc[(int64_t)(A0 + p) * ld], wt = Wc[(int64_t)(A0 + t) * ld];
-    Wc[(int64_t)(A0 + p) * ld] = fma(c, wp, s * wt);
-    Wc[(int64_t)(A0 + t) * ld] = fma(c, wt, -s * wp);
+  dc_deflate_node(a, A0, B0, C0);
+  __syncthreads();
+  const int K = a.Kof[A0];
+  for (int j = warp; j < K; j += NW) dc_secular_root(a, A0, B0, K, j);
+  __syncthreads();
+  for (int i = warp; i < K; i += NW) dc_zhat_one(a, A0, B0, K, i);
+  __syncthreads();
+  for (int j = warp; j < K; j += NW) dc_colnorm_one(a, A0, K, j);
+  __syncthreads();
+  dc_order_node(a, A0, N, key, ref);
+  __syncthreads();
+  const bool rot = a.nrot[A0] > 0;
+  for (int q = threadIdx.x; q < N * N; q += NT) {
+    const int t = q / N, col = q - t * N;
+    double dorg, tau, inv;
+    const int r = dc_col_ref(a, A0, N, K, col, &dorg, &tau, &inv);
+    const double v = dc_m_value(a, A0, K, t, r, dorg, tau, inv);
+    if (rot) a.Zt[(int64_t)(A0 + t) * ld + A0 + col] = v;
+    else a.M[(int64_t)(A0 + min(max(a.idx[A0 + t], 0), N - 1)) * ld + A0 + col] = v;
   }
-  for (int t = 0; t < N; t++)
-    a.M[(int64_t)(A0 + min(max(a.idx[A0 + t], 0), N - 1)) * ld + A0 + col] = Wc[(int64_t)(A0 + t) * ld];
+  __syncthreads();
+  if (rot)
+    for (int col = threadIdx.x; col < N; col += NT) dc_rotperm_col(a, A0, N, col);
+  __syncthreads();
+  // Zt[r, col] = sum_k Z[r, k] M[k, col] over the block of row r
+  for (int q = threadIdx.x; q < N * N; q += NT) {
+    const int col = q / N, r = q - col * N;
+    const int k0 = r < n1 ? 0 : n1, k1 = r < n1 ? n1 : N;
+    double acc = 0.0;
+    for (int k = k0; k < k1; k++)
+      acc = fma(a.Z[(int64_t)(A0 + r) + (int64_t)(A0 + k) * ld], a.M[(int64_t)(A0 + k) * ld + A0 + col], acc);
+    a.Zt[(int64_t)(A0 + r) + (int64_t)(A0 + col) * ld] = acc;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < N * N; q += NT) {
+    const int col = q / N, r = q - col * N;
+    a.Z[(int64_t)(A0 + r) + (int64_t)(A0 + col) * ld] = a.Zt[(int64_t)(A0 + r) + (int64_t)(A0 + col) * ld];
+  }
 }
 
 // Batched FP64 GEMM of the merge: Zt[a:b, a:c] = Z[a:b, a:b] M[a:b, a:c] and
@@ -1013,28 +1098,30 @@ __global__ void dc_unscale_kernel(const double* lam, int n, const double* tscale
 
 // ------------------------------------------------------- back-transformation ----
 //
-// Z <- H_0 H_1 ... H_{n-2} Z: each CTA owns cw columns (g = 8 / cw warps per column),
-// held in shared memory; reflectors from the last to the first, each staged in shared
-// memory (double-buffered, the next one loaded while the current one is applied):
-// s = tau_j v_j^T z, z <- z - s v_j.  Output into O (column-major, ldo).
-__global__ void __launch_bounds__(NT) backtransform_kernel(const double* Z, int64_t ldz, const double* V,
-                                                           int64_t ldv, const double* tau, int n, int cw,
-                                                           double* O, int64_t ldo) {
+// Z <- H_0 H_1 ... H_{n-2} Z: each CTA owns cw columns, g = (warps of the CTA) / cw warps
+// per column, the columns held in shared memory; reflectors from the last to the first,
+// each staged in shared memory (double-buffered, the next one loaded while the current one
+// is applied): s = tau_j v_j^T z, z <- z - s v_j.  Output into O (column-major, ldo).
+constexpr int BT_THREADS = 384;   // largest CTA the kernel is compiled for
+__global__ void __launch_bounds__(BT_THREADS, 1) backtransform_kernel(const double* Z, int64_t ldz, const double* V,
+                                                                      int64_t ldv, const double* tau, int n, int cw,
+                                                                      double* O, int64_t ldo) {
   extern __shared__ __align__(16) double smz[];
   double* zc = smz;                       // cw x n
   double* vb = smz + (int64_t)cw * n;     // 2 x n
-  __shared__ double part[NW];
-  const int g = NW / cw;                  // warps per column
+  __shared__ double part[BT_THREADS / 32];
+  const int nthr = blockDim.x, nwarp = nthr >> 5;
+  const int g = nwarp / cw;               // warps per column
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int cl = warp / g, gw = warp % g;     // column within the CTA, warp within its group
   const int col0 = blockIdx.x * cw;
   const int ncol = min(cw, n - col0);
   for (int c = 0; c < ncol; c++)
-    for (int l = threadIdx.x; l < n; l += NT) zc[(int64_t)c * n + l] = Z[l + (int64_t)(col0 + c) * ldz];
+    for (int l = threadIdx.x; l < n; l += nthr) zc[(int64_t)c * n + l] = Z[l + (int64_t)(col0 + c) * ldz];
   auto stage = [&](int j, int buf) {
     double* dst = vb + (int64_t)buf * n;
     const double* src = V + (int64_t)j * ldv;
-    for (int l = j + 1 + threadIdx.x; l < n; l += NT) {
+    for (int l = j + 1 + threadIdx.x; l < n; l += nthr) {
       const uint32_t da = (uint32_t)__cvta_generic_to_shared(dst + l);
       asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(da), "l"(src + l) : "memory");
     }
@@ -1084,7 +1171,7 @@ __global__ void __launch_bounds__(NT) backtransform_kernel(const double* Z, int6
     j = jnext;
   }
   for (int c = 0; c < ncol; c++)
-    for (int l = threadIdx.x; l < n; l += NT) O[l + (int64_t)(col0 + c) * ldo] = zc[(int64_t)c * n + l];
+    for (int l = threadIdx.x; l < n; l += nthr) O[l + (int64_t)(col0 + c) * ldo] = zc[(int64_t)c * n + l];
 }
 
 }  // namespace
@@ -1252,6 +1339,10 @@ cudaError_t launch_sym_eig(double* A, int64_t lda, int n, double* w, void* work,
     const int nodes = 1 << d;
     const int Nmax = (int)(((int64_t)n + nodes - 1) / nodes);
     if (Nmax < 2) continue;
+    if (Nmax <= DC_SMALL) {
+      dc_small_kernel<<<nodes, NT, 0, st>>>(a, d), count_launch();
+      continue;
+    }
     int p2 = 1;
     while (p2 < Nmax) p2 <<= 1;
     const int rw = (Nmax + NW - 1) / NW;
@@ -1269,13 +1360,18 @@ cudaError_t launch_sym_eig(double* A, int64_t lda, int n, double* w, void* work,
   }
   dc_unscale_kernel<<<(n + NT - 1) / NT, NT, 0, st>>>(a.lam, n, tscale, amax, w), count_launch();
   // ---- back-transformation into A ----
+  // 8 warps per CTA: 8 columns of one warp each while they fit in shared memory, else 4,
+  // 2, 1 columns of 2, 4, 8 warps (a 12-warp CTA with 6 two-warp columns spreads k = 850
+  // more evenly over the FP64 pipes but was slower: the per-reflector cross-warp sum costs
+  // a CTA-wide barrier)
   int cw = 8;
-  while (cw > 1 && (size_t)(cw + 2) * n * 8 > SMEM_CAP) cw >>= 1;
+  while (cw > 1 && (size_t)(cw + 2) * n * 8 > SMEM_CAP) cw /= 2;
   const size_t bt_smem = (size_t)(cw + 2) * n * 8;
   if ((e = cudaFuncSetAttribute(backtransform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem)) !=
       cudaSuccess)
     return e;
-  backtransform_kernel<<<(n + cw - 1) / cw, NT, bt_smem, st>>>(a.Z, n, t.V, n, t.tau, n, cw, A, lda), count_launch();
+  backtransform_kernel<<<(n + cw - 1) / cw, NT, bt_smem, st>>>(a.Z, n, t.V, n, t.tau, n, cw, A, lda),
+      count_launch();
   // non-finite input: report through info[2]
   info_nonfinite_kernel<<<1, 32, 0, st>>>(amax, info), count_launch();
   return cudaGetLastError();
