@@ -349,6 +349,13 @@ int kscf_check_status(void);
  * synchronising. */
 int kscf_selftest_barrier_timeout(void* stream);
 
+/* The same for the grid barrier of the eigensolver's tridiagonalisation (kscf_sym_eig):
+ * a 64 x 64 identity, CTA 1 of its 8 returns at the first barrier, the others' waits are
+ * limited to 2e6 clock cycles.  Returns KSCF_ERR_TIMEOUT when they gave up (expected; the
+ * context stays usable and the rest of the solve runs on the zeroed workspace), KSCF_OK if
+ * not, or another code.  Allocates and frees ~0.3 MB of device memory; synchronising. */
+int kscf_selftest_eig_barrier_timeout(void* stream);
+
 /* ---------------------------------------------------------------------------------
  * Self-consistent field (Computational details: Kohn-Sham DFT with the LDA,
  * Ceperley-Alder correlation as parametrised by Perdew & Zunger; SCF stopped when the

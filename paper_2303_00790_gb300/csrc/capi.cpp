@@ -720,6 +720,37 @@ extern "C" int kscf_selftest_barrier_timeout(void* stream) {
   return KSCF_OK;
 }
 
+extern "C" int kscf_selftest_eig_barrier_timeout(void* stream) {
+  const int n = 64;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t abytes = kscf_align256((size_t)n * n * 8), vbytes = kscf_align256((size_t)n * 8);
+  const size_t wbytes = sym_eig_work_bytes(n);
+  char* buf = nullptr;
+  KSCF_CUDA_TRY(cudaMalloc(&buf, abytes + vbytes + 256 + wbytes));
+  double* A = (double*)buf;
+  double* w = (double*)(buf + abytes);
+  int* info = (int*)(buf + abytes + vbytes);
+  void* work = buf + abytes + vbytes + 256;
+  std::vector<double> eye((size_t)n * n, 0.0);
+  for (int i = 0; i < n; i++) eye[(size_t)i * n + i] = 1.0;
+  int hi[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaMemsetAsync(work, 0, wbytes, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(A, eye.data(), (size_t)n * n * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_sym_eig(A, n, n, w, work, wbytes, info, st, 2000000LL, 1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hi, info, sizeof(hi), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(buf);
+  if (e != cudaSuccess) {
+    set_error("kscf_selftest_eig_barrier_timeout: %s", cudaGetErrorString(e));
+    return KSCF_ERR_CUDA;
+  }
+  if (hi[0] != 0) {
+    set_error("kscf_selftest_eig_barrier_timeout: the bounded grid barrier gave up as expected");
+    return KSCF_ERR_TIMEOUT;
+  }
+  return KSCF_OK;
+}
+
 extern "C" int kscf_check_status(void) {
   unsigned int st = 0, fs = 0, cs = 0, nf = 0;
   cudaError_t e = tc_status(true, &st);

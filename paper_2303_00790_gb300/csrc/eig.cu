@@ -184,6 +184,7 @@ struct TriArgs {
   unsigned* bar;      // arrival counter, zero at launch
   int* status;        // [0] = 1: a barrier wait gave up
   long long spin_limit;
+  int leave_cta;      // self-test only: this CTA returns at its first barrier (-1: none)
 };
 
 // Grid-wide barrier of the tridiagonalisation: arrival by a release reduction on a
@@ -192,6 +193,7 @@ struct TriArgs {
 // spin_limit clock cycles, or when another CTA gave up, the status word is set and
 // false returned.
 __device__ bool tri_barrier(const TriArgs& a, unsigned target, int* s_ok) {
+  if ((int)blockIdx.x == a.leave_cta) return false;
   __syncthreads();
   if (threadIdx.x == 0) {
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.bar) : "memory");
@@ -1235,7 +1237,7 @@ size_t sym_eig_work_bytes(int n) {
 }
 
 cudaError_t launch_sym_eig(double* A, int64_t lda, int n, double* w, void* work, size_t work_bytes, int* info,
-                           cudaStream_t st, long long spin_limit) {
+                           cudaStream_t st, long long spin_limit, int leave_cta) {
   if (n < 1 || n > KSCF_EIG_MAX_N || lda < n || !A || !w || !work || !info) return cudaErrorInvalidValue;
   const EigLayout L = eig_layout(n);
   if (work_bytes < L.total) return cudaErrorInvalidValue;
@@ -1270,6 +1272,7 @@ cudaError_t launch_sym_eig(double* A, int64_t lda, int n, double* w, void* work,
   t.bar = (unsigned*)P_(L_BAR);
   t.status = info;
   t.spin_limit = spin_limit;
+  t.leave_cta = leave_cta;
   const int R = (n + t.P - 1) / t.P;
   size_t vec_bytes = (size_t)4 * n * 8;
   if (vec_bytes > SMEM_CAP) {

@@ -185,8 +185,10 @@ cudaError_t launch_chol_inv(const double* S, int64_t lds, int k, double floor_re
 // NaN or Inf.  work: sym_eig_work_bytes(n), 256-aligned.  n <= KSCF_EIG_MAX_N.
 constexpr int KSCF_EIG_MAX_N = 8192;
 size_t sym_eig_work_bytes(int n);
+// leave_cta >= 0 (self-test only): that CTA of the tridiagonalisation returns at its first
+// grid barrier, so that the others' bounded waits run out.
 cudaError_t launch_sym_eig(double* A, int64_t lda, int n, double* w, void* work, size_t work_bytes, int* info,
-                           cudaStream_t st, long long spin_limit = 2000000000LL);
+                           cudaStream_t st, long long spin_limit = 2000000000LL, int leave_cta = -1);
 cudaError_t launch_f64_to_dtype(const double* src, int64_t n, int dtype, void* out, cudaStream_t st);
 
 }  // namespace kscf

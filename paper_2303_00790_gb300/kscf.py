@@ -119,6 +119,7 @@ _sigs = {
     "kscf_sym_eig": ([_vp, _i64, _i32, _vp, _vp, _sz, _vp], _i32),
     "kscf_check_status": ([], _i32),
     "kscf_selftest_barrier_timeout": ([_vp], _i32),
+    "kscf_selftest_eig_barrier_timeout": ([_vp], _i32),
     "kscf_scf_create": ([_vp, C.POINTER(kscf_atom), _i32, C.POINTER(kscf_species), _i32, C.POINTER(_d),
                          C.POINTER(kscf_scf_params), _vp, _i64, _vp, C.POINTER(_vp)], _i32),
     "kscf_scf_start": ([_vp, _vp, _i32, C.c_uint64, C.POINTER(_d)], _i32),
@@ -473,6 +474,11 @@ def kscf_check_status():
 def kscf_selftest_barrier_timeout(stream=None):
     """Raises KscfError(KSCF_ERR_TIMEOUT) when the bounded grid barrier works (see kscf.h)."""
     _check(lib.kscf_selftest_barrier_timeout(_stream(stream)))
+
+
+def kscf_selftest_eig_barrier_timeout(stream=None):
+    """Raises KscfError(KSCF_ERR_TIMEOUT) when the eigensolver's bounded grid barrier works."""
+    _check(lib.kscf_selftest_eig_barrier_timeout(_stream(stream)))
 
 
 def kscf_launch_counter() -> int:

@@ -182,3 +182,17 @@ def test_large_matrix_global_rows(kscf):
     A = (B + B.T) / 2
     lam, Z = solve(kscf, A)
     check(A, lam, Z)
+
+
+def test_bounded_barrier_times_out_and_context_survives(kscf):
+    """One CTA of the tridiagonalisation leaves at its first grid barrier: the others'
+    waits (limit ~1 ms) give up, the call reports KSCF_ERR_TIMEOUT and a following solve
+    is exact."""
+    with pytest.raises(kscf.KscfError) as e:
+        kscf.kscf_selftest_eig_barrier_timeout()
+    assert e.value.code == kscf.KSCF_ERR_TIMEOUT
+    rng = np.random.default_rng(6)
+    B = rng.standard_normal((120, 120))
+    A = (B + B.T) / 2
+    lam, Z = solve(kscf, A)
+    check(A, lam, Z)
