@@ -16,8 +16,9 @@
 // the nonlocal projections <chi_i, in> coming from kb_gather_cm launched just before.
 // cm_step_ldg16 does it for one brick and 16 vectors per CTA: the brick core is copied
 // into shared memory, the halo rows of each line come from the neighbour bricks in L2
-// into registers, lines that hold no domain point are skipped, and the nonlocal scatter
-// reads the brick's KB coefficients and entries from shared memory.
+// into registers, lines that hold no domain point are skipped, and the nonlocal term of a
+// point is gathered over its own KB entries (slot order) from the brick's coefficients
+// and entries staged in shared memory, in the pass that writes the point.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -262,42 +263,6 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
       }
     }
   }
-  __syncthreads();
-  // ---- nonlocal scatter over the brick's entries ----
-  for (int i = L; i < ne; i += 64) {
-    uint32_t word;
-    float4 ch;
-    const float4* cf;
-    float4 cv[4];
-    if (SMEM_KB) {
-      if (i < LDG_ENT) {
-        word = ew[i];
-        ch = echi[i];
-      } else {
-        word = __ldg(eword + e0 + i);
-        ch = __ldg((const float4*)(a.kb_chi + 4 * (e0 + i)));
-      }
-      cf = kbc + (word >> 16) * 16 + vp;
-#pragma unroll
-      for (int l = 0; l < 4; l++) cv[l] = cf[4 * l];
-    } else {
-      word = __ldg(a.entry_lslot + e0 + i);
-      ch = __ldg((const float4*)(a.kb_chi + 4 * (e0 + i)));
-      const float* g = a.coef + (int64_t)__ldg(a.kb_atom + e0 + i) * 4 * a.cld + c * 16 + vl;
-#pragma unroll
-      for (int l = 0; l < 4; l++) cv[l] = ld4(g + l * a.cld);
-    }
-    const int ls = word & 0xffff;
-    float4 q = f4_mul(f2(ch.x), cv[0]);
-    q = f4_fma(f2(ch.y), cv[1], q);
-    q = f4_fma(f2(ch.z), cv[2], q);
-    q = f4_fma(f2(ch.w), cv[3], q);
-    float* acc = (float*)&acc4[sl(ls & 7, (ls >> 3) & 7, ls >> 6) * 4 + vp];
-    atomicAdd(acc, q.x);
-    atomicAdd(acc + 1, q.y);
-    atomicAdd(acc + 2, q.z);
-    atomicAdd(acc + 3, q.w);
-  }
   // ---- z pass: line (x, y); potential, recurrence, store ----
   {
     const int x = lz & 7, y = lz >> 3;
@@ -311,7 +276,7 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
 #pragma unroll
       for (int z = 0; z < 8; z++) w[6 + z] = core4[sl(x, y, z) * 4 + vp];
     }
-    __syncthreads();  // scatter atomics are complete
+    __syncthreads();  // y-pass accumulator writes are visible
     if (lz >= 0) {
       const float2 alpha = f2(a.alpha), beta = f2(a.beta), negc = f2(-a.c);
       const float* prevp = a.prev ? a.prev + (int64_t)c * a.cs_prev + vl : nullptr;
@@ -325,6 +290,35 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
         const float4 yc = w[6 + z];
         float4 hy = f4_add(acc4[sl(x, y, z) * 4 + vp], line4<false>(w, 6 + z, c2));
         hy = f4_fma(f2(vv[z]), yc, hy);
+        // nonlocal term of this point: sum over its KB entries (slot order) of
+        // chi_l(e) * coef(atom(e), l), accumulated in registers
+        for (int64_t qe = __ldg(a.kb_ptr + s), qe1 = __ldg(a.kb_ptr + s + 1); qe < qe1; qe++) {
+          const int i = (int)(qe - e0);
+          float4 ch;
+          float4 cv[4];
+          if (SMEM_KB) {
+            uint32_t word;
+            if (i < LDG_ENT) {
+              word = ew[i];
+              ch = echi[i];
+            } else {
+              word = __ldg(eword + qe);
+              ch = __ldg((const float4*)(a.kb_chi + 4 * qe));
+            }
+            const float4* cf = kbc + (word >> 16) * 16 + vp;
+#pragma unroll
+            for (int l = 0; l < 4; l++) cv[l] = cf[4 * l];
+          } else {
+            ch = __ldg((const float4*)(a.kb_chi + 4 * qe));
+            const float* g = a.coef + (int64_t)__ldg(a.kb_atom + qe) * 4 * a.cld + c * 16 + vl;
+#pragma unroll
+            for (int l = 0; l < 4; l++) cv[l] = ld4(g + l * a.cld);
+          }
+          hy = f4_fma(f2(ch.x), cv[0], hy);
+          hy = f4_fma(f2(ch.y), cv[1], hy);
+          hy = f4_fma(f2(ch.z), cv[2], hy);
+          hy = f4_fma(f2(ch.w), cv[3], hy);
+        }
         float4 r = f4_mul(alpha, f4_fma(negc, yc, hy));
         if (prevp) {
           // plain load otherwise: prev may be the output buffer
