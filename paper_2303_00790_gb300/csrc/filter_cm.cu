@@ -132,8 +132,8 @@ constexpr int LDG_CORE = 0, LDG_ACC = 32768, LDG_KBC = 65536, LDG_EW = LDG_KBC +
 
 // Lines of a pass that hold no domain point are skipped: each pass takes its lines from
 // the brick's compacted list of live lines, and the threads past the list's end idle
-// (their points are padding and never stored).  The nonlocal scatter reads the
-// projection coefficients of the brick's KB atoms and the brick's entries from shared
+// (their points are padding and never stored).  The nonlocal gather of the z pass reads
+// the projection coefficients of the brick's KB atoms and the brick's entries from shared
 // memory, staged at the start together with the core (SMEM_KB; otherwise from global
 // memory).
 template <bool SMEM_KB>
