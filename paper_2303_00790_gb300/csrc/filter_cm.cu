@@ -128,7 +128,8 @@ __device__ __forceinline__ bool finite4(float4 v) {
 // floats) and the first LDG_ENT entries of the brick (packed word + chi).
 constexpr int LDG_ENT = 256;
 constexpr int LDG_CORE = 0, LDG_ACC = 32768, LDG_KBC = 65536, LDG_EW = LDG_KBC + KSCF_BRICK_ATOMS * 4 * 64,
-              LDG_ECHI = LDG_EW + LDG_ENT * 4, LDG_PREV = LDG_ECHI + LDG_ENT * 16, LDG_SMEM = LDG_PREV + 32768;
+              LDG_ECHI = LDG_EW + LDG_ENT * 4, LDG_PREV = LDG_ECHI + LDG_ENT * 16, LDG_KBP = LDG_PREV + 32768,
+              LDG_SMEM = LDG_KBP + 1040;   // + the brick's 513 entry offsets (uint16, from its first entry)
 
 // Lines of a pass that hold no domain point are skipped: each pass takes its lines from
 // the brick's compacted list of live lines, and the threads past the list's end idle
@@ -150,6 +151,7 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
   uint32_t* ew = (uint32_t*)(smw + LDG_EW);
   float4* echi = (float4*)(smw + LDG_ECHI);
   const float4* prev4 = (const float4*)(smw + LDG_PREV);   // [512][4]: Y_{j-2} rows of this brick
+  uint16_t* kbp = (uint16_t*)(smw + LDG_KBP);              // [513]: first entry of each slot, from e0
   auto sl = [](int x, int y, int z) { return (z * 8 + y) * 8 + (x ^ (y & 1)); };
   int c, brick;
   if (!cta_item(a, &c, &brick)) return;
@@ -188,6 +190,7 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
   }
   const int64_t e0 = __ldg(a.kb_ptr + b0), e1 = __ldg(a.kb_ptr + b0 + 512);
   const int ne = (int)(e1 - e0);
+  for (int t = tid; t <= 512; t += 256) kbp[t] = (uint16_t)(__ldg(a.kb_ptr + b0 + t) - e0);
   if (SMEM_KB) {
     const int nat = __ldg(bnat + brick);
     for (int t = tid; t < nat * 16; t += 256) {
@@ -292,8 +295,9 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
         hy = f4_fma(f2(vv[z]), yc, hy);
         // nonlocal term of this point: sum over its KB entries (slot order) of
         // chi_l(e) * coef(atom(e), l), accumulated in registers
-        for (int64_t qe = __ldg(a.kb_ptr + s), qe1 = __ldg(a.kb_ptr + s + 1); qe < qe1; qe++) {
-          const int i = (int)(qe - e0);
+        const int sloc = z * 64 + lz;
+        for (int i = kbp[sloc], i1 = kbp[sloc + 1]; i < i1; i++) {
+          const int64_t qe = e0 + i;
           float4 ch;
           float4 cv[4];
           if (SMEM_KB) {
