@@ -283,23 +283,25 @@ def test_refine_matches_oracle_converged_mode(kscf, species, oracle_scf, dtype_n
     assert abs(out["electrons"] - 8.0) < 1e-9
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_scf_si35h36_against_oracle_golden(kscf, species, precision):
-    """The 1 nm cluster (Si35H36, 45,025 points, k = 100, degree 10): SCF to SRE < 1e-4 Ry
-    and the converged mode (residuals < 1e-7 Ha, kscf_scf_refine) against the oracle's
-    stored run (tests/golden/si35h36_scf.json, written by make_si353h196_scf.py).  FP64
-    runs the oracle's algorithm from the same X0: the same step count and Ritz values and
-    energy to rounding amplified by the SCF (1e-7 Ha, 1e-8 Ha per atom).  Mixed precision:
-    the method's accuracy targets (eigenvalues and gap 1e-5 Ha, energy 1e-6 Ha per atom)."""
+@pytest.mark.parametrize("name,precision", [("si35h36", "fp64"), ("si35h36", "mixed"), ("si353h196", "mixed")])
+def test_scf_against_oracle_golden(kscf, species, name, precision):
+    """SCF to SRE < 1e-4 Ry and the converged mode (residuals < 1e-7 Ha, kscf_scf_refine)
+    against the oracle's stored run (tests/golden/<workload>_scf.json, written by
+    make_si353h196_scf.py from oracle/ alone): the 1 nm cluster (Si35H36, 45,025 points,
+    k = 100, degree 10) and the 2.2 nm benchmark cluster (Si353H196, 234,489 points,
+    k = 850, degree 12).  FP64 runs the oracle's algorithm from the same X0: the same step
+    count and Ritz values and energy to rounding amplified by the SCF (1e-7 Ha, 1e-8 Ha per
+    atom).  Mixed precision: the method's accuracy targets (eigenvalues and gap 1e-5 Ha,
+    energy 1e-6 Ha per atom)."""
     import json
     import os
     from workloads import workload
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "si35h36_scf.json")
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", f"{name}_scf.json")
     with open(path) as f:
         gold = json.load(f)
     gc = gold["converged"]
     nocc = gold["n_occ"]
-    w = workload("si35h36")
+    w = workload(name)
     pos, z = w.atoms()
     g, H = kscf.build_cluster(pos, z, species, w.radius, w.h)
     assert g.info["n_points"] == gold["n_points"]
@@ -322,7 +324,7 @@ def test_scf_si35h36_against_oracle_golden(kscf, species, precision):
     e_tot = abs(rf["e_total"] - gc["e_total"]) / len(z)
     idx = np.asarray(gc["rho"]["sample_index_lex"])
     e_rho = np.max(np.abs(rho[idx] - np.asarray(gc["rho"]["sample_rho"]))) / np.max(gc["rho"]["sample_rho"])
-    print(f"{precision}: steps {len(reps)} (oracle {gold['scf']['steps']}), refine {rf['iters']} iterations, "
+    print(f"{name} {precision}: steps {len(reps)} (oracle {gold['scf']['steps']}), refine {rf['iters']} iterations, "
           f"eig {e_eig:.2e} gap {e_gap:.2e} E/atom {e_tot:.2e} rho {e_rho:.2e}")
     if mixed:
         assert e_eig < 1e-5 and e_gap < 1e-5 and e_tot < 1e-6
