@@ -14,40 +14,22 @@
 // that device current, on the first call made on that device.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "kscf_internal.h"
 
 static __device__ __align__(256) unsigned char g_apply_scratch[KSCF_NOALLOC_SCRATCH_BYTES];
 
 namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
-
-// Device address of g_apply_scratch on the current device (looked up once per device).
+// Device address of g_apply_scratch in the current context, looked up on every call
+// (the lookup allocates nothing, and a cached address would dangle after the context is
+// reset by cudaDeviceReset or by a host framework).
 int scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) {
-    kscf::set_error("kscf_hamiltonian_apply_noalloc: cudaGetDevice failed: %s", cudaGetErrorString(e));
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_apply_scratch);
+  if (e != cudaSuccess || !p) {
+    kscf::set_error("kscf_hamiltonian_apply_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
     return KSCF_ERR_CUDA;
   }
-  if (dev < 0 || dev >= kMaxDevices) {
-    kscf::set_error("kscf_hamiltonian_apply_noalloc: device %d out of range", dev);
-    return KSCF_ERR_INVALID;
-  }
-  std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_apply_scratch);
-    if (e != cudaSuccess || !p) {
-      kscf::set_error("kscf_hamiltonian_apply_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-      return KSCF_ERR_CUDA;
-    }
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
+  *out = p;
   return KSCF_OK;
 }
 }  // namespace
