@@ -1363,17 +1363,23 @@ cudaError_t launch_sym_eig(double* A, int64_t lda, int n, double* w, void* work,
   }
   dc_unscale_kernel<<<(n + NT - 1) / NT, NT, 0, st>>>(a.lam, n, tscale, amax, w), count_launch();
   // ---- back-transformation into A ----
-  // 8 warps per CTA: 8 columns of one warp each while they fit in shared memory, else 4,
-  // 2, 1 columns of 2, 4, 8 warps (a 12-warp CTA with 6 two-warp columns spreads k = 850
-  // more evenly over the FP64 pipes but was slower: the per-reflector cross-warp sum costs
-  // a CTA-wide barrier)
-  int cw = 8;
-  while (cw > 1 && (size_t)(cw + 2) * n * 8 > SMEM_CAP) cw /= 2;
+  // One warp per column, ceil(n / SMs) columns per CTA (at most 8), so that every SM's FP64
+  // pipes get a share; when 8 columns do not fit in shared memory, 8-warp CTAs of 4, 2, 1
+  // columns of 2, 4, 8 warps (a 12-warp CTA with 6 two-warp columns was slower than one
+  // warp per column: the per-reflector cross-warp sum costs a CTA-wide barrier)
+  const int sms = sm_count();
+  int cw = (int)std::min<int64_t>(8, ((int64_t)n + sms - 1) / sms);
+  int bt_threads = 32 * cw;
+  if ((size_t)(cw + 2) * n * 8 > SMEM_CAP) {
+    cw = 8;
+    while (cw > 1 && (size_t)(cw + 2) * n * 8 > SMEM_CAP) cw /= 2;
+    bt_threads = NT;
+  }
   const size_t bt_smem = (size_t)(cw + 2) * n * 8;
   if ((e = cudaFuncSetAttribute(backtransform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem)) !=
       cudaSuccess)
     return e;
-  backtransform_kernel<<<(n + cw - 1) / cw, NT, bt_smem, st>>>(a.Z, n, t.V, n, t.tau, n, cw, A, lda),
+  backtransform_kernel<<<(n + cw - 1) / cw, bt_threads, bt_smem, st>>>(a.Z, n, t.V, n, t.tau, n, cw, A, lda),
       count_launch();
   // non-finite input: report through info[2]
   info_nonfinite_kernel<<<1, 32, 0, st>>>(amax, info), count_launch();
