@@ -157,7 +157,7 @@ size_t rr_bytes(const RRPlan& p) {
 }
 
 // FP32 on 8^3 bricks: the filter runs on two chunk-major working copies of the block
-bool filter_chunk_major(const Ham& H, int dtype) { return dtype == KSCF_F32 && H.grid.B == 8; }
+bool filter_chunk_major(const Ham& H, int dtype) { return dtype == KSCF_F32 && H.n_cells > 0; }
 
 size_t filter_bytes(const Ham& H, int k, int dtype, int block) {
   const int w = block_width(k, block);

@@ -1,23 +1,25 @@
-// Chebyshev filter steps on chunk-major working buffers (FP32, 8^3 bricks).
+// Chebyshev filter steps on chunk-major working buffers (FP32, bricks of 8^3 or 16^3).
 //
 // The filter (CheFSI paragraph of arXiv 2303.00790; three-term recurrence of Zhou,
 // Saad, Tiago & Chelikowsky 2006) runs m degree steps over one column block.  Its
 // working copies of the block are stored chunk-major: the block's columns are cut
 // into chunks of CW vectors, and chunk c holds every slot's CW values contiguously,
 //     element (c, s, v) at buf[(c * n_slots + s) * CW + v],
-// so that one brick of one chunk is one contiguous 512 * CW * 4-byte range.  The
-// degree-step launches walk the bricks chunk by chunk (within supertiles of
-// consecutive bricks), so the neighbour bricks whose faces a brick needs were read
-// from DRAM moments before and still sit in L2, and DRAM sees long sequential runs.
+// so that one brick of one chunk is one contiguous range.  A CTA works on one cell of 8^3
+// points: the brick itself for 8^3 bricks, one octant of a 16^3 brick (whose points stay
+// x-fastest over the whole brick, so that a cell's rows are 64 runs of 8).  The
+// degree-step launches walk the cells chunk by chunk (within supertiles of consecutive
+// cells), so the neighbour cells whose faces a cell needs were read from DRAM moments
+// before and still sit in L2, and DRAM sees long sequential runs.
 //
 // One step computes, for every slot s and vector v,
 //   out = alpha (H in - c in) + beta prev,
 //   H in = -1/2 Lap_h in + V in + sum_i chi_i (E_i h^3 <chi_i, in>),
 // the nonlocal projections <chi_i, in> coming from kb_gather_cm launched just before.
-// cm_step_ldg16 does it for one brick and 16 vectors per CTA: the brick core is copied
-// into shared memory, the halo rows of each line come from the neighbour bricks in L2
+// cm_step_ldg16 does it for one cell and 16 vectors per CTA: the cell core is copied
+// into shared memory, the halo rows of each line come from the neighbour cells in L2
 // into registers, lines that hold no domain point are skipped, and the nonlocal term of a
-// point is gathered over its own KB entries (slot order) from the brick's coefficients
+// point is gathered over its own KB entries (cell order) from the cell's coefficients
 // and entries staged in shared memory, in the pass that writes the point.
 #include <cuda_runtime.h>
 
@@ -43,33 +45,46 @@ struct CmArgs {
   int64_t cs_out, ld_out;
   int out_vec;            // out rows allow aligned vector stores
   int w;                  // valid columns of the block
-  int nchunk, n_bricks, super;  // CTA order: supertiles of `super` bricks, chunk-major inside
+  int nchunk, n_cells, super;   // CTA order: supertiles of `super` cells, chunk-major inside
   float alpha, beta, c;
   const float* coef;      // (n_kb*4) rows of cld, global column index
   int64_t cld;
   const float* V;
-  const int32_t* nbr;
+  const int32_t* nbr;      // face neighbour cells
   const uint8_t* mask;
-  const int64_t* kb_ptr;
+  const int64_t* kb_ptr;   // KB entries in cell order: CSR over the cell-local points
   const int32_t* kb_atom;
   const float* kb_chi;
-  const uint16_t* entry_lslot;
   float st[7];
   int64_t n_slots;
   int check;              // flag non-finite stored values
 };
 
-// CTA -> (chunk, brick): supertiles of `super` consecutive bricks (Hilbert order); inside
-// a supertile all bricks of chunk 0, then of chunk 1, ...  Returns false for the idle
-// CTAs of a partial last supertile.
-__device__ __forceinline__ bool cta_item(const CmArgs& a, int* chunk, int* brick) {
+// CTA -> (chunk, cell): supertiles of `super` consecutive cells (Hilbert order of the
+// bricks); inside a supertile all cells of chunk 0, then of chunk 1, ...  Returns false for
+// the idle CTAs of a partial last supertile.
+__device__ __forceinline__ bool cta_item(const CmArgs& a, int* chunk, int* cell) {
   const int per = a.nchunk * a.super;
   const int t = blockIdx.x / per, rem = blockIdx.x - t * per;
   const int c = rem / a.super, i = rem - c * a.super;
   const int b = t * a.super + i;
   *chunk = c;
-  *brick = b;
-  return b < a.n_bricks;
+  *cell = b;
+  return b < a.n_cells;
+}
+
+// Cells of 8^3 points: a brick of 8^3, or an octant of a 16^3 brick (cell = brick * 8 +
+// ox + 2 oy + 4 oz).  Slot of the cell's first point; slots of the cell-local point
+// (x, y, z) are that plus z * SZ + y * SY + x with SZ = B^2, SY = B.
+template <int B>
+__device__ __forceinline__ int64_t cell_base(int cell) {
+  if (B == 8) return (int64_t)cell * 512;
+  const int o = cell & 7;
+  return (int64_t)(cell >> 3) * 4096 + (o >> 2) * 2048 + ((o >> 1) & 1) * 128 + (o & 1) * 8;
+}
+template <int B>
+__device__ __forceinline__ int cell_row(int r) {   // r = x + 8 y + 64 z
+  return (r >> 6) * (B * B) + ((r >> 3) & 7) * B + (r & 7);
 }
 
 __device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
@@ -92,7 +107,7 @@ __device__ __forceinline__ float2 f2(float s) { return make_float2(s, s); }
 
 // ---------------------------------------------------------------------------
 // 16 vectors per CTA, 256 threads (64 lines x 4 lanes x float4).  Core by cp.async, the
-// halo rows of each line loaded from the neighbour bricks (L2) into the register window.
+// halo rows of each line loaded from the neighbour cells (L2) into the register window.
 namespace {
 __device__ __forceinline__ float4 f4_add(float4 a, float4 b) {
   const float2 lo = f2_add(make_float2(a.x, a.y), make_float2(b.x, b.y));
@@ -124,77 +139,80 @@ __device__ __forceinline__ bool finite4(float4 v) {
 }  // namespace
 
 // Shared memory of cm_step_ldg16 (bytes): core and accumulator (512 point slots x 16
-// floats each), the coefficients of the brick's KB atoms (KSCF_BRICK_ATOMS x 4 x 16
-// floats) and the first LDG_ENT entries of the brick (packed word + chi).
+// floats each), the coefficients of the cell's KB atoms (KSCF_BRICK_ATOMS x 4 x 16
+// floats) and the first LDG_ENT entries of the cell (packed word + chi).
 constexpr int LDG_ENT = 256;
 constexpr int LDG_CORE = 0, LDG_ACC = 32768, LDG_KBC = 65536, LDG_EW = LDG_KBC + KSCF_BRICK_ATOMS * 4 * 64,
               LDG_ECHI = LDG_EW + LDG_ENT * 4, LDG_PREV = LDG_ECHI + LDG_ENT * 16, LDG_KBP = LDG_PREV + 32768,
-              LDG_SMEM = LDG_KBP + 1040;   // + the brick's 513 entry offsets (uint16, from its first entry)
+              LDG_SMEM = LDG_KBP + 1040;   // + the cell's 513 entry offsets (uint16, from its first entry)
 
 // Lines of a pass that hold no domain point are skipped: each pass takes its lines from
-// the brick's compacted list of live lines, and the threads past the list's end idle
+// the cell's compacted list of live lines, and the threads past the list's end idle
 // (their points are padding and never stored).  The nonlocal gather of the z pass reads
-// the projection coefficients of the brick's KB atoms and the brick's entries from shared
+// the projection coefficients of the cell's KB atoms and the cell's entries from shared
 // memory, staged at the start together with the core (SMEM_KB; otherwise from global
-// memory).
-template <bool SMEM_KB>
+// memory).  B: brick edge (8 or 16), which sets the slot steps inside a cell.
+template <bool SMEM_KB, int B>
 __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t* __restrict__ lines,
                                                         const uint8_t* __restrict__ nlines,
                                                         const int32_t* __restrict__ batoms,
                                                         const int32_t* __restrict__ bnat,
                                                         const uint32_t* __restrict__ eword,
                                                         const float* __restrict__ zero) {
+  constexpr int SZ = B * B, SY = B;   // slot steps of z and y inside a brick
   extern __shared__ __align__(16) uint8_t smw[];
   float4* core4 = (float4*)(smw + LDG_CORE);   // [512][4]
   float4* acc4 = (float4*)(smw + LDG_ACC);     // [512][4]
   float4* kbc = (float4*)(smw + LDG_KBC);      // [atom][l][4]
   uint32_t* ew = (uint32_t*)(smw + LDG_EW);
   float4* echi = (float4*)(smw + LDG_ECHI);
-  const float4* prev4 = (const float4*)(smw + LDG_PREV);   // [512][4]: Y_{j-2} rows of this brick
-  uint16_t* kbp = (uint16_t*)(smw + LDG_KBP);              // [513]: first entry of each slot, from e0
+  const float4* prev4 = (const float4*)(smw + LDG_PREV);   // [512][4]: Y_{j-2} rows of this cell
+  uint16_t* kbp = (uint16_t*)(smw + LDG_KBP);              // [513]: first entry of each point, from e0
   auto sl = [](int x, int y, int z) { return (z * 8 + y) * 8 + (x ^ (y & 1)); };
-  int c, brick;
-  if (!cta_item(a, &c, &brick)) return;
+  int c, cell;
+  if (!cta_item(a, &c, &cell)) return;
   const int tid = threadIdx.x, vp = tid & 3, L = tid >> 2;
   const int vl = 4 * vp;
-  const int64_t b0 = (int64_t)brick * 512;
+  const int64_t b0 = cell_base<B>(cell);     // slot of the cell's first point
+  const int64_t k0 = (int64_t)cell * 512;    // its first cell-local point (KB tables)
   const float* inc = a.in + (int64_t)c * a.n_slots * 16 + vl;   // row stride 16 floats
   const float* own = inc + b0 * 16;
   const float* nbp[6];   // a missing neighbour reads the zero brick
 #pragma unroll
   for (int f = 0; f < 6; f++) {
-    const int q = __ldg(a.nbr + (int64_t)brick * 6 + f);
-    nbp[f] = q >= 0 ? inc + (int64_t)q * 512 * 16 : zero + vl;
+    const int q = __ldg(a.nbr + (int64_t)cell * 6 + f);
+    nbp[f] = q >= 0 ? inc + cell_base<B>(q) * 16 : zero + vl;
   }
-  const uint8_t* bl = lines + (int64_t)brick * 192;
-  const int nlx = __ldg(nlines + brick * 3), nly = __ldg(nlines + brick * 3 + 1), nlz = __ldg(nlines + brick * 3 + 2);
+  const uint8_t* bl = lines + (int64_t)cell * 192;
+  const int nlx = __ldg(nlines + cell * 3), nly = __ldg(nlines + cell * 3 + 1), nlz = __ldg(nlines + cell * 3 + 2);
   const int lx = L < nlx ? __ldg(bl + L) : -1;
   const int ly = L < nly ? __ldg(bl + 64 + L) : -1;
   const int lz = L < nlz ? __ldg(bl + 128 + L) : -1;
-  // core: 512 rows x 64 B, padding rows zero-filled without a read; with it the brick's
-  // Y_{j-2} rows (chunk-major, contiguous), so that the z pass finds them in shared memory
+  // core: 512 rows x 64 B, padding rows zero-filled without a read; with it the cell's
+  // Y_{j-2} rows, so that the z pass finds them in shared memory
   const bool prev_smem = a.prev != nullptr && a.ld_prev == 16;
   const float* psrc = prev_smem ? a.prev + (int64_t)c * a.cs_prev + b0 * 16 + vl : nullptr;
 #pragma unroll
   for (int i = 0; i < 8; i++) {
     const int r = L + 64 * i;
-    const uint32_t live = __ldg(a.mask + b0 + r);
+    const int ro = cell_row<B>(r);
+    const uint32_t live = __ldg(a.mask + b0 + ro);
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(&core4[sl(r & 7, (r >> 3) & 7, r >> 6) * 4 + vp]);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(own + r * 16), "r"(live ? 16 : 0)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(own + ro * 16), "r"(live ? 16 : 0)
                  : "memory");
     if (prev_smem) {
       const uint32_t dp = (uint32_t)__cvta_generic_to_shared(smw + LDG_PREV + (r * 4 + vp) * 16);
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dp), "l"(psrc + r * 16), "r"(live ? 16 : 0)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dp), "l"(psrc + ro * 16), "r"(live ? 16 : 0)
                    : "memory");
     }
   }
-  const int64_t e0 = __ldg(a.kb_ptr + b0), e1 = __ldg(a.kb_ptr + b0 + 512);
+  const int64_t e0 = __ldg(a.kb_ptr + k0), e1 = __ldg(a.kb_ptr + k0 + 512);
   const int ne = (int)(e1 - e0);
-  for (int t = tid; t <= 512; t += 256) kbp[t] = (uint16_t)(__ldg(a.kb_ptr + b0 + t) - e0);
+  for (int t = tid; t <= 512; t += 256) kbp[t] = (uint16_t)(__ldg(a.kb_ptr + k0 + t) - e0);
   if (SMEM_KB) {
-    const int nat = __ldg(bnat + brick);
+    const int nat = __ldg(bnat + cell);
     for (int t = tid; t < nat * 16; t += 256) {
-      const int at = __ldg(batoms + (int64_t)brick * KSCF_BRICK_ATOMS + (t >> 4));
+      const int at = __ldg(batoms + (int64_t)cell * KSCF_BRICK_ATOMS + (t >> 4));
       const int l = (t >> 2) & 3, q = t & 3;
       const float* src = a.coef + ((int64_t)at * 4 + l) * a.cld + c * 16 + 4 * q;
       const uint32_t d = (uint32_t)__cvta_generic_to_shared(&kbc[((t >> 4) * 4 + l) * 4 + q]);
@@ -210,10 +228,11 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
   asm volatile("cp.async.commit_group;" ::: "memory");
   float vv[8];
   uint32_t mk = 0;
+  const int zl = lz >= 0 ? (lz >> 3) * SY + (lz & 7) : 0;   // z line (x, y): slot offset of its z = 0 point
   if (lz >= 0) {
 #pragma unroll
     for (int z = 0; z < 8; z++) {
-      const int64_t s = b0 + z * 64 + lz;
+      const int64_t s = b0 + z * SZ + zl;
       mk |= (uint32_t)__ldg(a.mask + s) << z;
       vv[z] = __ldg(a.V + s);
     }
@@ -222,11 +241,10 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
   c2[0] = f2(3.0f * a.st[0]);
 #pragma unroll
   for (int k = 1; k < 7; k++) c2[k] = f2(a.st[k]);
-  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   // ---- x pass: line (y, z) ----
   {
     const int y = lx & 7, z = lx >> 3;
-    const int rb = (z * 8 + y) * 8 * 16;
+    const int rb = (z * SZ + y * SY) * 16;
     float4 w[20];
     if (lx >= 0) {
 #pragma unroll
@@ -251,8 +269,8 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
     if (ly >= 0) {
 #pragma unroll
       for (int yy = 0; yy < 6; yy++) {
-        w[yy] = ld4(nbp[2] + ((z * 8 + 2 + yy) * 8 + x) * 16);
-        w[14 + yy] = ld4(nbp[3] + ((z * 8 + yy) * 8 + x) * 16);
+        w[yy] = ld4(nbp[2] + (z * SZ + (2 + yy) * SY + x) * 16);
+        w[14 + yy] = ld4(nbp[3] + (z * SZ + yy * SY + x) * 16);
       }
 #pragma unroll
       for (int y = 0; y < 8; y++) w[6 + y] = core4[sl(x, y, z) * 4 + vp];
@@ -273,8 +291,8 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
     if (lz >= 0) {
 #pragma unroll
       for (int zz = 0; zz < 6; zz++) {
-        w[zz] = ld4(nbp[4] + ((2 + zz) * 64 + y * 8 + x) * 16);
-        w[14 + zz] = ld4(nbp[5] + (zz * 64 + y * 8 + x) * 16);
+        w[zz] = ld4(nbp[4] + ((2 + zz) * SZ + zl) * 16);
+        w[14 + zz] = ld4(nbp[5] + (zz * SZ + zl) * 16);
       }
 #pragma unroll
       for (int z = 0; z < 8; z++) w[6 + z] = core4[sl(x, y, z) * 4 + vp];
@@ -288,12 +306,12 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
       bool bad = false;
 #pragma unroll
       for (int z = 0; z < 8; z++) {
-        const int64_t s = b0 + z * 64 + lz;
+        const int64_t s = b0 + z * SZ + zl;
         if (!((mk >> z) & 1u)) continue;
         const float4 yc = w[6 + z];
         float4 hy = f4_add(acc4[sl(x, y, z) * 4 + vp], line4<false>(w, 6 + z, c2));
         hy = f4_fma(f2(vv[z]), yc, hy);
-        // nonlocal term of this point: sum over its KB entries (slot order) of
+        // nonlocal term of this point: sum over its KB entries (cell order) of
         // chi_l(e) * coef(atom(e), l), accumulated in registers
         const int sloc = z * 64 + lz;
         for (int i = kbp[sloc], i1 = kbp[sloc + 1]; i < i1; i++) {
@@ -399,7 +417,6 @@ __global__ void to_chunk_major(const float* __restrict__ X, int64_t ld, int w, i
 }
 
 namespace {
-bool g_ldg_attr[64] = {false};
 
 unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 }  // namespace
@@ -448,45 +465,38 @@ cudaError_t launch_cm_step(const Ham& H, const float* in, const float* prev, flo
   }
   a.w = w;
   a.nchunk = (w + cw - 1) / cw;
-  a.n_bricks = (int)H.grid.n_bricks;
-  // supertiles: the bricks of one chunk stay L2-resident (three buffers x 512 rows x cw x 4 B each)
-  const int64_t per_brick = 3LL * 512 * cw * 4;
-  a.super = (int)std::max<int64_t>(64, std::min<int64_t>(H.grid.n_bricks, (64LL << 20) / per_brick));
+  if (H.n_cells <= 0 || (H.grid.B != 8 && H.grid.B != 16)) return cudaErrorInvalidValue;
+  a.n_cells = (int)H.n_cells;
+  // supertiles: the cells of one chunk stay L2-resident (three buffers x 512 rows x cw x 4 B each)
+  const int64_t per_cell = 3LL * 512 * cw * 4;
+  a.super = (int)std::max<int64_t>(64, std::min<int64_t>(H.n_cells, (64LL << 20) / per_cell));
   a.alpha = (float)alpha;
   a.beta = (float)beta;
   a.c = (float)cshift;
   a.coef = coef;
   a.cld = cld;
   a.V = H.d_v32;
-  a.nbr = H.d_nbr;
+  a.nbr = H.d_cell_nbr;
   a.mask = H.d_mask;
-  a.kb_ptr = H.d_kb_slot_ptr;
-  a.kb_atom = H.d_kb_slot_atom;
-  a.kb_chi = H.d_kb_slot_chi32;
-  a.entry_lslot = H.d_kb_entry_lslot;
+  a.kb_ptr = H.d_cell_kb_ptr;
+  a.kb_atom = H.d_cell_kb_atom;
+  a.kb_chi = H.d_cell_kb_chi32;
   for (int k = 0; k < 7; k++) a.st[k] = (float)H.stencil[k];
   a.n_slots = H.grid.n_slots;
   a.check = check ? 1 : 0;
-  const int n_super = (int)((H.grid.n_bricks + a.super - 1) / a.super);
+  const int n_super = (int)((H.n_cells + a.super - 1) / a.super);
   const unsigned grid = (unsigned)((int64_t)n_super * a.super * a.nchunk);
-  int dev = 0;
-  cudaGetDevice(&dev);
-  {
-    if (dev >= 0 && dev < 64 && !g_ldg_attr[dev]) {
-      cudaError_t e = cudaFuncSetAttribute(cm_step_ldg16<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, LDG_SMEM);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(cm_step_ldg16<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, LDG_SMEM);
-      if (e != cudaSuccess) return e;
-      g_ldg_attr[dev] = true;
-    }
-    if (H.brick_atoms_ok)
-      cm_step_ldg16<true><<<grid, 256, LDG_SMEM, st>>>(a, H.d_lines, H.d_nlines, H.d_brick_atoms, H.d_brick_natoms,
-                                                       H.d_kb_entry_word, zero), count_launch();
-    else
-      cm_step_ldg16<false><<<grid, 256, LDG_SMEM, st>>>(a, H.d_lines, H.d_nlines, H.d_brick_atoms,
-                                                        H.d_brick_natoms, H.d_kb_entry_word, zero), count_launch();
-  }
-  return cudaGetLastError();
+  // the shared-memory size attribute belongs to the context: set on every call
+  auto run = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, LDG_SMEM);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 256, LDG_SMEM, st>>>(a, H.d_lines, H.d_nlines, H.d_brick_atoms, H.d_brick_natoms,
+                                      H.d_kb_entry_word, zero),
+        count_launch();
+    return cudaGetLastError();
+  };
+  if (H.grid.B == 8) return H.brick_atoms_ok ? run(cm_step_ldg16<true, 8>) : run(cm_step_ldg16<false, 8>);
+  return H.brick_atoms_ok ? run(cm_step_ldg16<true, 16>) : run(cm_step_ldg16<false, 16>);
 }
 
 unsigned int* nonfinite_flag() {

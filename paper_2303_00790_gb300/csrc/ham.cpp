@@ -38,6 +38,11 @@ static void free_ham(Ham& H) {
                   H.d_lines,         H.d_nlines,        H.d_brick_atoms, H.d_brick_natoms, H.d_kb_entry_word};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (H.cell_tables_own) {
+    void* cell[] = {H.d_cell_nbr, H.d_cell_kb_ptr, H.d_cell_kb_chi32, H.d_cell_kb_atom};
+    for (void* p : cell)
+      if (p) cudaFree(p);
+  }
 }
 
 extern "C" int kscf_ham_free(kscf_ham* ham) {
@@ -53,6 +58,15 @@ struct KBEntry {
   int32_t atom;
   double chi[4];
 };
+
+// slot of the cell-local point r = x + 8 y + 64 z of cell c (bricks of B = 8 or 16 points;
+// a 16^3 brick holds the cells brick * 8 + ox + 2 oy + 4 oz, points x-fastest in the brick)
+int64_t cell_slot(int B, int64_t c, int r) {
+  if (B == 8) return c * 512 + r;
+  const int o = (int)(c & 7);
+  const int x = (o & 1) * 8 + (r & 7), y = ((o >> 1) & 1) * 8 + ((r >> 3) & 7), z = (o >> 2) * 8 + (r >> 6);
+  return (c >> 3) * 4096 + ((int64_t)z * 16 + y) * 16 + x;
+}
 }  // namespace
 
 extern "C" int kscf_build_hamiltonian(const kscf_grid* grid, const kscf_atom* atoms, int n_atoms,
@@ -104,11 +118,33 @@ extern "C" int kscf_build_hamiltonian(const kscf_grid* grid, const kscf_atom* at
     if (e == cudaSuccess) e = upload(&H.d_mask, g.mask.data(), g.mask.size());
     if (e == cudaSuccess) e = upload(&H.d_lex, g.lex_of_slot.data(), g.lex_of_slot.size());
     if (e == cudaSuccess) e = upload(&H.d_pad, pad.data(), pad.size());
-    if (g.B == 8 && e == cudaSuccess) {
-      // live lines per brick and pass: x lines (y, z), y lines (x, z), z lines (x, y)
-      std::vector<uint8_t> lines((size_t)g.n_bricks * 3 * 64, 0), nlines((size_t)g.n_bricks * 3, 0);
-      for (int64_t b = 0; b < g.n_bricks; b++) {
-        const uint8_t* m = g.mask.data() + b * 512;
+    if ((g.B == 8 || g.B == 16) && e == cudaSuccess) {
+      // cells of the chunk-major filter: neighbours across the six faces (inside a 16^3
+      // brick the adjacent octant, else the octant of the neighbour brick that touches it)
+      const int per = g.B == 8 ? 1 : 8;
+      H.n_cells = g.n_bricks * per;
+      std::vector<int32_t> cnbr((size_t)H.n_cells * 6, -1);
+      for (int64_t c = 0; c < H.n_cells; c++) {
+        const int64_t b = c / per;
+        const int o = (int)(c % per);
+        for (int f = 0; f < 6; f++) {
+          if (per == 1) {
+            cnbr[c * 6 + f] = g.nbr[b * 6 + f];
+            continue;
+          }
+          const int ax = f >> 1, up = f & 1, oa = (o >> ax) & 1;
+          const int o2 = o ^ (1 << ax);
+          if (oa != up) {
+            cnbr[c * 6 + f] = (int32_t)(b * 8 + o2);
+          } else {
+            const int32_t nb = g.nbr[b * 6 + f];
+            cnbr[c * 6 + f] = nb < 0 ? -1 : (int32_t)((int64_t)nb * 8 + o2);
+          }
+        }
+      }
+      // live lines per cell and pass: x lines (y, z), y lines (x, z), z lines (x, y)
+      std::vector<uint8_t> lines((size_t)H.n_cells * 3 * 64, 0), nlines((size_t)H.n_cells * 3, 0);
+      for (int64_t c = 0; c < H.n_cells; c++) {
         for (int pass = 0; pass < 3; pass++) {
           int n = 0;
           for (int bb = 0; bb < 8; bb++)
@@ -119,15 +155,21 @@ extern "C" int kscf_build_hamiltonian(const kscf_grid* grid, const kscf_atom* at
                 if (pass == 0) { x = t; y = aa; z = bb; }
                 else if (pass == 1) { x = aa; y = t; z = bb; }
                 else { x = aa; y = bb; z = t; }
-                live |= m[(z * 8 + y) * 8 + x] != 0;
+                live |= g.mask[cell_slot(g.B, c, (z * 8 + y) * 8 + x)] != 0;
               }
-              if (live) lines[(b * 3 + pass) * 64 + n++] = (uint8_t)(aa + 8 * bb);
+              if (live) lines[(c * 3 + pass) * 64 + n++] = (uint8_t)(aa + 8 * bb);
             }
-          nlines[b * 3 + pass] = (uint8_t)n;
+          nlines[c * 3 + pass] = (uint8_t)n;
         }
       }
       e = upload(&H.d_lines, lines.data(), lines.size());
       if (e == cudaSuccess) e = upload(&H.d_nlines, nlines.data(), nlines.size());
+      if (per == 1) {
+        H.d_cell_nbr = H.d_nbr;
+      } else {
+        H.cell_tables_own = true;
+        if (e == cudaSuccess) e = upload(&H.d_cell_nbr, cnbr.data(), cnbr.size());
+      }
     }
     if (e == cudaSuccess) e = cudaMalloc((void**)&H.d_v64, sizeof(double) * g.n_slots);
     if (e == cudaSuccess) e = cudaMalloc((void**)&H.d_v32, sizeof(float) * g.n_slots);
@@ -317,33 +359,69 @@ extern "C" int kscf_build_hamiltonian(const kscf_grid* grid, const kscf_atom* at
       for (int64_t s2 = 0; s2 < g.n_slots; s2++)
         for (int64_t q = s_ptr[s2]; q < s_ptr[s2 + 1]; q++) lslot[q] = (uint16_t)(s2 % b3);
       if (e == cudaSuccess) e = upload(&H.d_kb_entry_lslot, lslot.data(), lslot.size());
-      if (g.B == 8 && e == cudaSuccess) {
-        // per-brick atom lists and packed entry words for the chunk-major filter kernels
-        const int64_t nb = g.n_bricks;
-        std::vector<int32_t> batoms((size_t)nb * KSCF_BRICK_ATOMS, -1), bnat(nb, 0);
+      if (H.n_cells > 0 && e == cudaSuccess) {
+        // the entries in cell order (the slot order itself for 8^3 bricks), per-cell atom
+        // lists and packed entry words for the chunk-major filter kernels
+        const bool own = g.B != 8;
+        std::vector<int64_t> cptr;
+        std::vector<float> cchi;
+        std::vector<int32_t> catom;
+        std::vector<uint16_t> clocal(ne);
+        if (own) {
+          cptr.assign((size_t)H.n_cells * 512 + 1, 0);
+          cchi.resize(4 * (size_t)ne);
+          catom.resize(ne);
+        }
+        int64_t q2 = 0;
+        for (int64_t c = 0; c < H.n_cells; c++)
+          for (int r = 0; r < 512; r++) {
+            const int64_t s2 = cell_slot(g.B, c, r);
+            if (own) cptr[c * 512 + r] = q2;
+            for (int64_t q = s_ptr[s2]; q < s_ptr[s2 + 1]; q++, q2++) {
+              clocal[q2] = (uint16_t)r;
+              if (own) {
+                catom[q2] = s_atom[q];
+                for (int l = 0; l < 4; l++) cchi[4 * q2 + l] = s_chi32[4 * q + l];
+              }
+            }
+          }
+        if (own) cptr[(size_t)H.n_cells * 512] = q2;
+        const std::vector<int64_t>& cp = own ? cptr : s_ptr;
+        const std::vector<int32_t>& ca = own ? catom : s_atom;
+        const int64_t nc = H.n_cells;
+        std::vector<int32_t> batoms((size_t)nc * KSCF_BRICK_ATOMS, -1), bnat(nc, 0);
         std::vector<uint32_t> word(ne);
         bool ok = true;
-        for (int64_t b = 0; b < nb; b++) {
-          for (int64_t q = s_ptr[b * 512]; q < s_ptr[(b + 1) * 512]; q++) {
-            const int32_t at = s_atom[q];
+        for (int64_t c = 0; c < nc; c++) {
+          for (int64_t q = cp[c * 512]; q < cp[(c + 1) * 512]; q++) {
+            const int32_t at = ca[q];
             int li = 0;
-            while (li < bnat[b] && batoms[b * KSCF_BRICK_ATOMS + li] != at) li++;
-            if (li == bnat[b]) {
-              if (bnat[b] == KSCF_BRICK_ATOMS) {
+            while (li < bnat[c] && batoms[c * KSCF_BRICK_ATOMS + li] != at) li++;
+            if (li == bnat[c]) {
+              if (bnat[c] == KSCF_BRICK_ATOMS) {
                 ok = false;
                 li = 0;
               } else {
-                batoms[b * KSCF_BRICK_ATOMS + li] = at;
-                bnat[b]++;
+                batoms[c * KSCF_BRICK_ATOMS + li] = at;
+                bnat[c]++;
               }
             }
-            word[q] = (uint32_t)lslot[q] | ((uint32_t)li << 16);
+            word[q] = (uint32_t)clocal[q] | ((uint32_t)li << 16);
           }
         }
         H.brick_atoms_ok = ok;
         if (e == cudaSuccess) e = upload(&H.d_brick_atoms, batoms.data(), batoms.size());
         if (e == cudaSuccess) e = upload(&H.d_brick_natoms, bnat.data(), bnat.size());
         if (e == cudaSuccess) e = upload(&H.d_kb_entry_word, word.data(), word.size());
+        if (own) {
+          if (e == cudaSuccess) e = upload(&H.d_cell_kb_ptr, cptr.data(), cptr.size());
+          if (e == cudaSuccess) e = upload(&H.d_cell_kb_chi32, cchi.data(), cchi.size());
+          if (e == cudaSuccess) e = upload(&H.d_cell_kb_atom, catom.data(), catom.size());
+        } else {
+          H.d_cell_kb_ptr = H.d_kb_slot_ptr;
+          H.d_cell_kb_chi32 = H.d_kb_slot_chi32;
+          H.d_cell_kb_atom = H.d_kb_slot_atom;
+        }
       }
     }
     if (e != cudaSuccess) {

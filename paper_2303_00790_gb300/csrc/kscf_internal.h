@@ -79,15 +79,27 @@ struct Ham {
   double* d_kb_energy = nullptr;      // n_kb*4: E_l * h^3
   double kb_upper = 0.0, kb_lower = 0.0;  // Gershgorin bounds of V_NL
   int max_slot_entries = 0;
-  // 8^3 bricks only (null otherwise): per brick and line pass (x, y, z) the lines holding
-  // at least one domain point, compacted (line = a + 8 b for the pass's two other axes)
-  uint8_t* d_lines = nullptr;          // n_bricks * 3 * 64
-  uint8_t* d_nlines = nullptr;         // n_bricks * 3
-  // per brick the KB atoms whose projectors reach into it (kb atom ids, at most
-  // KSCF_BRICK_ATOMS; brick_atoms_ok false when a brick has more), and per entry (slot
-  // order) the packed word  slot-in-brick | (index in its brick's atom list << 16)
-  int32_t* d_brick_atoms = nullptr;    // n_bricks * KSCF_BRICK_ATOMS, -1 padded
-  int32_t* d_brick_natoms = nullptr;   // n_bricks
+  // Cells of the chunk-major FP32 filter (bricks of 8^3 or 16^3, null otherwise): cubes of
+  // 8^3 points, the brick itself for 8^3 bricks, the eight octants of a 16^3 brick
+  // (cell = brick * 8 + ox + 2 oy + 4 oz).  Cell-local point r = x + 8 y + 64 z.
+  int64_t n_cells = 0;
+  int32_t* d_cell_nbr = nullptr;       // n_cells * 6: face neighbour cells (-x, +x, -y, +y, -z, +z), -1: none
+  // per cell and line pass (x, y, z) the lines holding at least one domain point,
+  // compacted (line = a + 8 b for the pass's two other axes)
+  uint8_t* d_lines = nullptr;          // n_cells * 3 * 64
+  uint8_t* d_nlines = nullptr;         // n_cells * 3
+  // the KB entries in cell order (cell, then cell-local point): CSR over the n_cells * 512
+  // cell-local points, chi (4 per entry) and atom; for 8^3 bricks these are the slot-order
+  // tables above (cell_tables_own false)
+  int64_t* d_cell_kb_ptr = nullptr;    // n_cells * 512 + 1
+  float* d_cell_kb_chi32 = nullptr;    // entry * 4
+  int32_t* d_cell_kb_atom = nullptr;   // entry -> kb atom
+  bool cell_tables_own = false;
+  // per cell the KB atoms whose projectors reach into it (kb atom ids, at most
+  // KSCF_BRICK_ATOMS; brick_atoms_ok false when a cell has more), and per entry (cell
+  // order) the packed word  cell-local point | (index in its cell's atom list << 16)
+  int32_t* d_brick_atoms = nullptr;    // n_cells * KSCF_BRICK_ATOMS, -1 padded
+  int32_t* d_brick_natoms = nullptr;   // n_cells
   uint32_t* d_kb_entry_word = nullptr;  // n_kb_entries
   bool brick_atoms_ok = false;
 };
@@ -110,7 +122,7 @@ cudaError_t launch_cheb_step(const Ham& H, const void* in, int64_t ld_in, const 
                              cudaStream_t st);
 inline int64_t coef_ld(int w) { return (int64_t)(w + 31) / 32 * 32; }
 
-// ---- chunk-major filter path (filter_cm.cu, FP32, 8^3 bricks) ----
+// ---- chunk-major filter path (filter_cm.cu, FP32, 8^3 and 16^3 bricks) ----
 // Working copies of a column block are chunk-major: element (c, s, v) at
 // buf[(c * n_slots + s) * cw + v], cw = cm_chunk_width().
 int cm_chunk_width();
@@ -126,7 +138,7 @@ cudaError_t launch_kb_gather_cm(const Ham& H, const float* Y, int cw, int w, flo
 cudaError_t launch_cm_step(const Ham& H, const float* in, const float* prev, float* out, int64_t out_ld, int w,
                            double alpha, double beta, double c, const float* coef, int64_t cld, bool check,
                            const float* zero, cudaStream_t st);
-constexpr size_t KSCF_CM_ZERO_BYTES = 512 * 16 * 4;
+constexpr size_t KSCF_CM_ZERO_BYTES = 4096 * 16 * 4;   // one 16^3 brick x 16 vectors
 // device address of the non-finite flag that kscf_check_status reports
 unsigned int* nonfinite_flag();
 // sets *flag when a domain row of X holds a NaN or Inf in its first k values
