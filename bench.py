@@ -586,10 +586,10 @@ def run_kscf(args):
     # end-to-end through the C ABI from pinned host buffers: the user's block has one row per
     # grid point (lexicographic order, k columns); every step uploads its input block,
     # converts it to the slot layout on the device (kscf_points_to_slots), runs the step,
-    # converts back (kscf_slots_to_points) and reads the result out.  The copies run on a
-    # second stream with double-buffered device blocks, so that step i's compute overlaps
-    # step i-1's read-out and step i+1's upload (the first upload and the last read-out are
-    # inside the timed region)
+    # converts back (kscf_slots_to_points) and reads the result out.  Uploads and read-outs
+    # run on two copy streams with double-buffered device blocks, so that step i's compute
+    # overlaps step i-1's read-out and step i+1's upload (the first upload and the last
+    # read-out are inside the timed region)
     e2e = None
     if not args.no_e2e:
         Pin = [torch.empty((n_points, k), dtype=dt, device="cuda") for _ in range(2)]
@@ -598,36 +598,44 @@ def run_kscf(args):
         Xh = torch.empty((n_points, k), dtype=dt, pin_memory=True)
         Xh.copy_(Pin[0])
         outh = torch.empty((n_points, k), dtype=dt, pin_memory=True)
-        cstream = torch.cuda.Stream()
+        up, down = torch.cuda.Stream(), torch.cuda.Stream()
         ev_copy = [torch.cuda.Event(), torch.cuda.Event()]
         ev_comp = [torch.cuda.Event(), torch.cuda.Event()]
+        ev_out = [torch.cuda.Event(), torch.cuda.Event()]
         torch.cuda.synchronize()
         barrier(world)
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
         nE = max(1, min(args.steps, 5))
-        s0.record(cstream)
-        with torch.cuda.stream(cstream):
+        s0.record(up)
+        with torch.cuda.stream(up):
             Pin[0].copy_(Xh, non_blocking=True)
-        ev_copy[0].record(cstream)
+        ev_copy[0].record(up)
         for i in range(nE):
             cur, nxt = i % 2, (i + 1) % 2
-            with torch.cuda.stream(cstream):
-                if i >= 1:
-                    cstream.wait_event(ev_comp[nxt])
+            if i >= 1:
+                down.wait_event(ev_comp[nxt])
+                with torch.cuda.stream(down):
                     outh.copy_(Pout[nxt], non_blocking=True)        # result of step i-1
-                if i + 1 < nE:
+                ev_out[nxt].record(down)
+            if i + 1 < nE:
+                if i >= 1:
+                    up.wait_event(ev_comp[nxt])                     # step i-1 has read Pin[nxt]
+                with torch.cuda.stream(up):
                     Pin[nxt].copy_(Xh, non_blocking=True)           # input of step i+1
-                    ev_copy[nxt].record(cstream)
+                ev_copy[nxt].record(up)
             stream.wait_event(ev_copy[cur])
+            if i >= 2:
+                stream.wait_event(ev_out[cur])                      # Pout[cur] read out
             kscf.kscf_points_to_slots(H, Pin[cur], X)
             step(False)
             kscf.kscf_slots_to_points(H, X, Pout[cur])
             ev_comp[cur].record(stream)
-        cstream.wait_event(ev_comp[(nE - 1) % 2])
-        with torch.cuda.stream(cstream):
+        down.wait_event(ev_comp[(nE - 1) % 2])
+        with torch.cuda.stream(down):
             outh.copy_(Pout[(nE - 1) % 2], non_blocking=True)       # result of the last step
-        s1.record(cstream)
+        up.wait_stream(down)
+        s1.record(up)
         torch.cuda.synchronize()
         e_ms = max_over_ranks(s0.elapsed_time(s1) / nE, world)
         del Pin, Pout
