@@ -11,12 +11,13 @@
 using namespace kscf;
 
 namespace kscf {
+// rowmap (device, may be null): row r of the operands (and of out) is row rowmap[r]
 cudaError_t launch_gram_tc(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t rows, int m, int n,
                            double scale, double* C, int64_t ldc, bool accumulate, void* work, size_t work_bytes,
-                           cudaStream_t st, bool symmetric_result = false);
+                           cudaStream_t st, bool symmetric_result = false, const int32_t* rowmap = nullptr);
 cudaError_t launch_rotate_tc(const float* A, int64_t lda, const double* Q, int64_t ldq, int64_t rows, int kin,
                              int kout, bool add_identity_input, float* out, int64_t ldo, void* work,
-                             size_t work_bytes, cudaStream_t st);
+                             size_t work_bytes, cudaStream_t st, const int32_t* rowmap = nullptr);
 size_t gram_tc_work_bytes(int64_t rows, int m, int n);
 size_t rotate_tc_work_bytes(int64_t rows, int kin, int kout);
 bool tc_available();
@@ -201,15 +202,23 @@ int check_mode(int dtype, int mode, const char* who) {
 // tensor path) in row panels.  The tensor path writes each panel in place (its product
 // reads the panel's bf16 pieces, made before the launch); the native path goes through
 // the panel buffer.
-int rotate_inplace(void* X, int64_t ld, int64_t rows, int k, int dtype, int mode, const void* Qm, const double* Q64,
-                   bool near_identity, void* panel, int64_t prows, void* tcwork, size_t tcbytes, cudaStream_t st) {
+int rotate_inplace(const Ham& H, void* X, int64_t ld, int k, int dtype, int mode, const void* Qm,
+                   const double* Q64, bool near_identity, void* panel, int64_t prows, void* tcwork, size_t tcbytes,
+                   cudaStream_t st) {
   const size_t es = esize(dtype);
+  // the tensor path rotates the domain rows only (through the grid's list of domain slots)
+  const bool live = mode == KSCF_GEMM_TENSOR && H.d_live;
+  const int64_t rows = live ? H.n_live : H.grid.n_slots;
   for (int64_t r0 = 0; r0 < rows; r0 += prows) {
     const int64_t nr = std::min(prows, rows - r0);
     char* Xr = (char*)X + (size_t)r0 * ld * es;
     if (mode == KSCF_GEMM_TENSOR) {
-      KSCF_CUDA_TRY(launch_rotate_tc((const float*)Xr, ld, Q64, k, nr, k, k, near_identity, (float*)Xr, ld, tcwork,
-                                     tcbytes, st));
+      if (live)
+        KSCF_CUDA_TRY(launch_rotate_tc((const float*)X, ld, Q64, k, nr, k, k, near_identity, (float*)X, ld, tcwork,
+                                       tcbytes, st, H.d_live + r0));
+      else
+        KSCF_CUDA_TRY(launch_rotate_tc((const float*)Xr, ld, Q64, k, nr, k, k, near_identity, (float*)Xr, ld, tcwork,
+                                       tcbytes, st));
     } else {
       KSCF_CUDA_TRY(launch_rotate_native(Xr, ld, Qm, k, nr, k, k, dtype, panel, k, st));
       KSCF_CUDA_TRY(launch_copy_cols(panel, k, Xr, ld, nr, k, dtype, st));
@@ -222,10 +231,10 @@ int rotate_inplace(void* X, int64_t ld, int64_t rows, int k, int dtype, int mode
 // the upper-triangle tiles only and mirrors them.
 int gram(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t rows, int m, int n, int dtype, int mode,
          double scale, double* C, int64_t ldc, void* tcwork, size_t tcbytes, cudaStream_t st,
-         bool symmetric_result = false) {
+         bool symmetric_result = false, const int32_t* rowmap = nullptr) {
   if (mode == KSCF_GEMM_TENSOR) {
     KSCF_CUDA_TRY(launch_gram_tc((const float*)A, lda, (const float*)B, ldb, rows, m, n, scale, C, ldc, false,
-                                 tcwork, tcbytes, st, symmetric_result && m == n));
+                                 tcwork, tcbytes, st, symmetric_result && m == n, rowmap));
   } else {
     KSCF_CUDA_TRY(launch_gram_native(A, lda, B, ldb, rows, m, n, dtype, scale, C, ldc, false, st));
   }
@@ -250,7 +259,9 @@ int cholqr_pass(const Ham& H, void* X, int64_t ld, int k, int dtype, int mode, c
   void* panel = c.take(p.panel);
   void* tcw = c.take(p.tc);
   const double h3 = H.grid.h * H.grid.h * H.grid.h;
-  const int64_t rows = H.grid.n_slots;
+  // the tensor path sums over the domain rows only (the padding rows are zero)
+  const int32_t* live = mode == KSCF_GEMM_TENSOR ? H.d_live : nullptr;
+  const int64_t rows = live ? H.n_live : H.grid.n_slots;
   const double u = dtype == KSCF_F64 ? 0x1.0p-53 : 0x1.0p-24;
   int hst[3] = {0, 0, 0};
   auto factor = [&](double floor_rel) -> int {
@@ -271,12 +282,12 @@ int cholqr_pass(const Ham& H, void* X, int64_t ld, int k, int dtype, int mode, c
     }
     return KSCF_OK;
   };
-  int rc = gram(X, ld, X, ld, rows, k, k, dtype, mode, h3, S, k, tcw, p.tc, st);
+  int rc = gram(X, ld, X, ld, rows, k, k, dtype, mode, h3, S, k, tcw, p.tc, st, false, live);
   if (rc) return rc;
   rc = factor(shifted ? 8.0 * u : 0.0);
   if (rc) return rc;
   if (hst[0] > 0 && shifted) {
-    rc = gram(X, ld, X, ld, rows, k, k, dtype, mode, h3, S, k, tcw, p.tc, st);
+    rc = gram(X, ld, X, ld, rows, k, k, dtype, mode, h3, S, k, tcw, p.tc, st, false, live);
     if (rc) return rc;
     KSCF_CUDA_TRY(launch_shift_diag(S, k, 16.0 * k * u, st));
     rc = factor(0.0);
@@ -290,7 +301,7 @@ int cholqr_pass(const Ham& H, void* X, int64_t ld, int k, int dtype, int mode, c
   }
   // S now holds R^-1 (upper triangular, zero below); the native path takes it in X's type
   if (mode != KSCF_GEMM_TENSOR) KSCF_CUDA_TRY(launch_upper_to_dtype(S, k, dtype, Rinv, st));
-  rc = rotate_inplace(X, ld, rows, k, dtype, mode, Rinv, S, second_pass, panel, p.prows, tcw, p.tc, st);
+  rc = rotate_inplace(H, X, ld, k, dtype, mode, Rinv, S, second_pass, panel, p.prows, tcw, p.tc, st);
   if (rc) return rc;
   KSCF_CUDA_TRY(cudaStreamSynchronize(st));
   return check_tc(mode, "Cholesky-QR");
@@ -516,7 +527,9 @@ extern "C" int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int 
   void* tcw = cv.take(p.tc);
   const size_t es = esize(dtype);
   const double h3 = H.grid.h * H.grid.h * H.grid.h;
-  const int64_t rows = H.grid.n_slots;
+  // the tensor path sums over the domain rows only (padding rows of X and H X are zero)
+  const int32_t* live = mode == KSCF_GEMM_TENSOR ? H.d_live : nullptr;
+  const int64_t rows = live ? H.n_live : H.grid.n_slots;
   KSCF_CUDA_TRY(launch_zero_rows(H, X, ld, k, dtype, st));
   for (int c0 = 0; c0 < k; c0 += p.w) {
     const int wb = std::min(p.w, k - c0);
@@ -527,7 +540,7 @@ extern "C" int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int 
     KSCF_CUDA_TRY(launch_cheb_step(H, Xb, ld, nullptr, 0, hxb, wpad, wb,
                                    (int)std::min<int64_t>(ld - c0, wpad), dtype, 1.0, 0.0, 0.0, coef, wpad, st));
     // Hs[:, c0:c0+wb] = h^3 X^T (H X_b); with a single block the product is symmetric (H is)
-    rc = gram(X, ld, hxb, wpad, rows, k, wb, dtype, mode, h3, Hs + (size_t)c0 * k, k, tcw, p.tc, st, wb == k);
+    rc = gram(X, ld, hxb, wpad, rows, k, wb, dtype, mode, h3, Hs + (size_t)c0 * k, k, tcw, p.tc, st, wb == k, live);
     if (rc) return rc;
   }
   KSCF_CUDA_TRY(launch_sym_eig(Hs, k, k, W, lwork, p.lwork_bytes, info, st));
@@ -549,8 +562,7 @@ extern "C" int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int 
       set_error("kscf_rayleigh_ritz: non-finite Ritz value");
       return KSCF_ERR_NONFINITE;
     }
-  return rotate_inplace(X, ld, rows, k, dtype, mode, Qm, Hs, mode == KSCF_GEMM_TENSOR, panel, p.prows, tcw, p.tc,
-                        st);
+  return rotate_inplace(H, X, ld, k, dtype, mode, Qm, Hs, mode == KSCF_GEMM_TENSOR, panel, p.prows, tcw, p.tc, st);
 }
 
 extern "C" int kscf_sym_eig_work_bytes(int n, size_t* bytes) {

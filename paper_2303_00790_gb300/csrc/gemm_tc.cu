@@ -2,6 +2,9 @@
 // Rayleigh-Ritz, arXiv 2303.00790 CheFSI paragraph):
 //   gram:   C (FP64) += scale * A^T B      A: rows x m, B: rows x n  (FP32)
 //   rotate: out (FP32) = A Q               A: rows x kin (FP32), Q: kin x kout (FP64)
+// With a row map, row r of A, B and out is row rowmap[r] of the stored matrix: the subspace
+// steps pass the grid's domain slots, so that the padding slots of the brick layout (zero
+// rows, 30 % of the slots of the 2.2 nm sphere) are neither split, multiplied nor written.
 //
 // Precision: each FP32 operand value x is split into three bf16 pieces
 // x = x1 + x2 + x3 (x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2)), and
@@ -143,6 +146,7 @@ struct TcArgs {
   int64_t rows;                    // valid rows of out
   const float* addsrc;             // if non-null: out = A Q + addsrc (same shape as out)
   int64_t ldadd;
+  const int32_t* rowmap;           // if non-null: row r of out and addsrc is row rowmap[r]
 };
 
 // products (A piece, B piece) kept: orders 2^0, 2^-8 (two), 2^-16 (three)
@@ -264,6 +268,16 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(TcArgs p) {
       const bool ok = __all_sync(0xffffffffu, mbar_wait(&tfull[b], (it >> 1) & 1));
       if (!ok) break;
       tc_fence_after();
+      // the output rows of this lane's sixteen tile rows (through the row map)
+      int64_t orow[16];
+      {
+        const int64_t ir0 = (int64_t)mt * TM + q * 32 + (lane >> 4);
+#pragma unroll
+        for (int r = 0; r < 16; r++) {
+          const int64_t ir = ir0 + 2 * r;
+          orow[r] = (p.rowmap && ir < p.rows) ? (int64_t)__ldg(p.rowmap + ir) : ir;
+        }
+      }
       for (int c0 = 0; c0 < TN; c0 += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + b * TN + c0, v);
@@ -280,14 +294,16 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(TcArgs p) {
           // the sixteen addends are loaded before any store (out may alias addsrc; each
           // element is read and written by this lane only), so their latencies overlap
 #pragma unroll
-          for (int r = 0; r < 16; r++)
-            add[r] = (p.addsrc && ir0 + 2 * r < p.rows) ? p.addsrc[(ir0 + 2 * r) * p.ldadd + j] : 0.0f;
+          for (int r = 0; r < 16; r++) {
+            const int64_t ir = ir0 + 2 * r;
+            add[r] = (p.addsrc && ir < p.rows) ? p.addsrc[orow[r] * p.ldadd + j] : 0.0f;
+          }
 #pragma unroll
           for (int r = 0; r < 16; r++) {
             const int64_t ir = ir0 + 2 * r;
             if (ir < p.rows) {
               const float v = tr[(2 * r + rh) * 17 + jj];
-              p.out[ir * p.ldo + j] = p.addsrc ? v + add[r] : v;
+              p.out[orow[r] * p.ldo + j] = p.addsrc ? v + add[r] : v;
             }
           }
         }
@@ -507,17 +523,19 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16&
   c = __float2bfloat16_rn(r2);
 }
 
-// Op[i][r] = X[r0 + r][c0 + i]  (gram operand: MN = columns, K = rows); one CTA per block
+// Op[i][r] = X[row(r0 + r)][c0 + i]  (gram operand: MN = columns, K = rows; row(r) = rowmap[r],
+// or r without a map); one CTA per block
 __global__ void __launch_bounds__(256) split_T_kernel(const float* __restrict__ X, int64_t ld, int64_t r0, int nr,
-                                                      int c0, int nc, int nkb, __nv_bfloat16* __restrict__ P0,
-                                                      __nv_bfloat16* __restrict__ P1, __nv_bfloat16* __restrict__ P2) {
+                                                      int c0, int nc, int nkb, const int32_t* __restrict__ rowmap,
+                                                      __nv_bfloat16* __restrict__ P0, __nv_bfloat16* __restrict__ P1,
+                                                      __nv_bfloat16* __restrict__ P2) {
   __shared__ __align__(16) __nv_bfloat16 sp[3][BLK_ELEMS];
   const int kb = blockIdx.x, mb = blockIdx.y;
   for (int e = threadIdx.x; e < BLK_ELEMS; e += 256) {
     const int i = e & 127, r = e >> 7;  // consecutive threads -> consecutive columns
     const int gi = mb * 128 + i, gr = kb * TK + r;
     float x = 0.f;
-    if (gi < nc && gr < nr) x = X[(r0 + gr) * ld + c0 + gi];
+    if (gi < nc && gr < nr) x = X[(rowmap ? (int64_t)rowmap[r0 + gr] : r0 + gr) * ld + c0 + gi];
     __nv_bfloat16 a, b, c;
     split3(x, a, b, c);
     const int o = tiled_off(i, r);
@@ -534,17 +552,18 @@ __global__ void __launch_bounds__(256) split_T_kernel(const float* __restrict__ 
   }
 }
 
-// Op[r][c] = X[r0 + r][c]  (rotation A operand: MN = rows, K = columns)
+// Op[r][c] = X[row(r0 + r)][c]  (rotation A operand: MN = rows, K = columns)
 __global__ void __launch_bounds__(256) split_N_kernel(const float* __restrict__ X, int64_t ld, int64_t r0, int nr,
-                                                      int nc, int nkb, __nv_bfloat16* __restrict__ P0,
-                                                      __nv_bfloat16* __restrict__ P1, __nv_bfloat16* __restrict__ P2) {
+                                                      int nc, int nkb, const int32_t* __restrict__ rowmap,
+                                                      __nv_bfloat16* __restrict__ P0, __nv_bfloat16* __restrict__ P1,
+                                                      __nv_bfloat16* __restrict__ P2) {
   __shared__ __align__(16) __nv_bfloat16 sp[3][BLK_ELEMS];
   const int kb = blockIdx.x, mb = blockIdx.y;
   for (int e = threadIdx.x; e < BLK_ELEMS; e += 256) {
     const int c = e & 31, r = e >> 5;  // consecutive threads -> consecutive columns of a row
     const int gr = mb * 128 + r, gc = kb * TK + c;
     float x = 0.f;
-    if (gr < nr && gc < nc) x = X[(r0 + gr) * ld + gc];
+    if (gr < nr && gc < nc) x = X[(rowmap ? (int64_t)rowmap[r0 + gr] : r0 + gr) * ld + gc];
     __nv_bfloat16 a, b, cc;
     split3(x, a, b, cc);
     const int o = tiled_off(r, c);
@@ -661,7 +680,7 @@ size_t rotate_tc_work_bytes(int64_t rows, int kin, int kout) {
 
 cudaError_t launch_gram_tc(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t rows, int m, int n,
                            double scale, double* C, int64_t ldc, bool accumulate, void* work, size_t work_bytes,
-                           cudaStream_t st, bool symmetric_result) {
+                           cudaStream_t st, bool symmetric_result, const int32_t* rowmap) {
   const int64_t chunk = gram_chunk_for_work(rows, m, n, work_bytes);
   if (chunk < TK && rows > 0) return cudaErrorInvalidValue;
   cudaError_t e = prepare_kernel();
@@ -702,12 +721,12 @@ cudaError_t launch_gram_tc(const float* A, int64_t lda, const float* B, int64_t 
   for (int64_t r0 = 0; r0 < rows; r0 += chunk) {
     const int nr = (int)std::min<int64_t>(chunk, rows - r0);
     const int nkb = cdiv(nr, TK);
-    split_T_kernel<<<dim3(nkb, cdiv(pad_to(m, TN), 128)), 256, 0, st>>>(A, lda, r0, nr, 0, m, nkb, Ap[0], Ap[1],
-                                                                         Ap[2]),
+    split_T_kernel<<<dim3(nkb, cdiv(pad_to(m, TN), 128)), 256, 0, st>>>(A, lda, r0, nr, 0, m, nkb, rowmap, Ap[0],
+                                                                         Ap[1], Ap[2]),
         count_launch();
     if (!same)
-      split_T_kernel<<<dim3(nkb, cdiv(pad_to(n, TN), 128)), 256, 0, st>>>(B, ldb, r0, nr, 0, n, nkb, Bp[0], Bp[1],
-                                                                           Bp[2]),
+      split_T_kernel<<<dim3(nkb, cdiv(pad_to(n, TN), 128)), 256, 0, st>>>(B, ldb, r0, nr, 0, n, nkb, rowmap, Bp[0],
+                                                                           Bp[1], Bp[2]),
           count_launch();
     a.nkb = nkb;
     // split the K range over CTAs: pick the split whose active CTAs fill whole waves
@@ -743,7 +762,7 @@ cudaError_t launch_gram_tc(const float* A, int64_t lda, const float* B, int64_t 
 
 cudaError_t launch_rotate_tc(const float* A, int64_t lda, const double* Q, int64_t ldq, int64_t rows, int kin,
                              int kout, bool add_identity_input, float* out, int64_t ldo, void* work,
-                             size_t work_bytes, cudaStream_t st) {
+                             size_t work_bytes, cudaStream_t st, const int32_t* rowmap) {
   if (work_bytes < rotate_tc_work_bytes(rows, kin, kout)) return cudaErrorInvalidValue;
   if (add_identity_input && kin != kout) return cudaErrorInvalidValue;
   cudaError_t e = prepare_kernel();
@@ -761,8 +780,8 @@ cudaError_t launch_rotate_tc(const float* A, int64_t lda, const double* Q, int64
     w += kscf_align256(piece_bytes(kout, kin));
   }
   const int nkb = cdiv(kin, TK);
-  split_N_kernel<<<dim3(nkb, cdiv(pad_to(rows, TN), 128)), 256, 0, st>>>(A, lda, 0, (int)rows, kin, nkb, Ap[0],
-                                                                           Ap[1], Ap[2]),
+  split_N_kernel<<<dim3(nkb, cdiv(pad_to(rows, TN), 128)), 256, 0, st>>>(A, lda, 0, (int)rows, kin, nkb, rowmap,
+                                                                           Ap[0], Ap[1], Ap[2]),
       count_launch();
   split_Q_kernel<<<dim3(nkb, cdiv(pad_to(kout, TN), 128)), 256, 0, st>>>(Q, ldq, kin, kout,
                                                                            add_identity_input ? 1 : 0, nkb, Bp[0],
@@ -786,6 +805,7 @@ cudaError_t launch_rotate_tc(const float* A, int64_t lda, const double* Q, int64
   // product reads only the bf16 pieces, which are complete before the kernel starts)
   a.addsrc = add_identity_input ? A : nullptr;
   a.ldadd = lda;
+  a.rowmap = rowmap;
   int sms = 152;
   {
     int dev = 0;

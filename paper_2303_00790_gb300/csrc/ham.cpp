@@ -31,7 +31,7 @@ static cudaError_t upload(T** dst, const T* src, size_t n) {
 }
 
 static void free_ham(Ham& H) {
-  void* ptrs[] = {H.d_nbr,           H.d_mask,         H.d_lex,          H.d_pad,
+  void* ptrs[] = {H.d_nbr,           H.d_mask,         H.d_lex,          H.d_pad,          H.d_live,
                   H.d_vion,          H.d_v64,           H.d_v32,          H.d_kb_atom_ptr,  H.d_kb_atom_slot,
                   H.d_kb_atom_chi64, H.d_kb_atom_chi32, H.d_kb_slot_ptr, H.d_kb_slot_atom,
                   H.d_kb_slot_chi64, H.d_kb_slot_chi32, H.d_kb_energy, H.d_kb_entry_lslot,
@@ -110,14 +110,19 @@ extern "C" int kscf_build_hamiltonian(const kscf_grid* grid, const kscf_atom* at
 
     // ---- geometry tables ----
     std::vector<int64_t> pad;
-    for (int64_t s = 0; s < g.n_slots; s++)
+    std::vector<int32_t> live;
+    for (int64_t s = 0; s < g.n_slots; s++) {
       if (!g.mask[s]) pad.push_back(s);
+      else live.push_back((int32_t)s);
+    }
     H.n_pad = (int64_t)pad.size();
+    H.n_live = (int64_t)live.size();
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = upload(&H.d_nbr, g.nbr.data(), g.nbr.size());
     if (e == cudaSuccess) e = upload(&H.d_mask, g.mask.data(), g.mask.size());
     if (e == cudaSuccess) e = upload(&H.d_lex, g.lex_of_slot.data(), g.lex_of_slot.size());
     if (e == cudaSuccess) e = upload(&H.d_pad, pad.data(), pad.size());
+    if (e == cudaSuccess) e = upload(&H.d_live, live.data(), live.size());
     if ((g.B == 8 || g.B == 16) && e == cudaSuccess) {
       // cells of the chunk-major filter: neighbours across the six faces (inside a 16^3
       // brick the adjacent octant, else the octant of the neighbour brick that touches it)

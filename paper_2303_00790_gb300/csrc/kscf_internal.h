@@ -61,6 +61,8 @@ struct Ham {
   int64_t* d_lex = nullptr;        // n_slots
   int64_t* d_pad = nullptr;        // padding slots
   int64_t n_pad = 0;
+  int32_t* d_live = nullptr;       // domain slots in slot order (n_live = number of grid points)
+  int64_t n_live = 0;
   double* d_v64 = nullptr;         // n_slots
   double* d_vion = nullptr;        // n_slots: V_loc as built (kept when the potential is replaced)
   float* d_v32 = nullptr;          // n_slots
