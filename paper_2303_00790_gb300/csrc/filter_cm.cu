@@ -368,52 +368,78 @@ __global__ void __launch_bounds__(256, 2) cm_step_ldg16(CmArgs a, const uint8_t*
 // ---------------------------------------------------------------------------
 // coef[(a*4+l)*cld + v] = E_l h^3 sum_{entries e of atom a} chi_l(e) Y(slot_e, v) for
 // v < w, and 0 for w <= v < cld (the padded columns of the last chunk then stay zero
-// through the recurrence).  Y chunk-major with chunk width cw.
-__global__ void __launch_bounds__(256) kb_gather_cm(const float* __restrict__ Y, int64_t n_slots, int cw, int w,
+// through the recurrence).  Y chunk-major with chunks of 16 columns.  A CTA takes one atom
+// and 128 columns (8 chunks); its 8 warps stride over the atom's entries, lane (chunk
+// lane / 4, quad lane % 4) reading its 4 columns of the entry's row as one float4; the
+// warps' sums meet in shared memory.
+__global__ void __launch_bounds__(256) kb_gather_cm(const float* __restrict__ Y, int64_t n_slots, int w, int nchunk,
                                                     int64_t cld, const int64_t* __restrict__ aptr,
                                                     const int64_t* __restrict__ aslot,
                                                     const float* __restrict__ achi,
                                                     const double* __restrict__ energy, float* __restrict__ coef) {
   const int at = blockIdx.x;
-  const int v = blockIdx.y * 32 + threadIdx.x;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  if (v < w) {
-    const float* base = Y + (int64_t)(v / cw) * n_slots * cw + (v % cw);
-    for (int64_t e = aptr[at] + threadIdx.y; e < aptr[at + 1]; e += 8) {
-      const float y = base[aslot[e] * cw];
-      const float4 ch = __ldg((const float4*)(achi + 4 * e));
-      acc[0] += ch.x * y;
-      acc[1] += ch.y * y;
-      acc[2] += ch.z * y;
-      acc[3] += ch.w * y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int chunk = blockIdx.y * 8 + (lane >> 2);
+  float acc[16];   // [l * 4 + column of the quad]
+#pragma unroll
+  for (int i = 0; i < 16; i++) acc[i] = 0.f;
+  if (chunk < nchunk) {
+    const float* base = Y + (int64_t)chunk * n_slots * 16 + (lane & 3) * 4;
+    const int64_t e1 = __ldg(aptr + at + 1);
+    int64_t e = __ldg(aptr + at) + warp;
+    auto add = [&](float4 c, float4 y) {
+      const float cl[4] = {c.x, c.y, c.z, c.w}, yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+      for (int l = 0; l < 4; l++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[l * 4 + q] = fmaf(cl[l], yv[q], acc[l * 4 + q]);
+    };
+    for (; e + 8 < e1; e += 16) {
+      const int64_t s0 = __ldg(aslot + e), s1 = __ldg(aslot + e + 8);
+      const float4 c0 = __ldg((const float4*)(achi + 4 * e)), c1 = __ldg((const float4*)(achi + 4 * (e + 8)));
+      const float4 y0 = __ldg((const float4*)(base + s0 * 16)), y1 = __ldg((const float4*)(base + s1 * 16));
+      add(c0, y0);
+      add(c1, y1);
     }
+    if (e < e1) add(__ldg((const float4*)(achi + 4 * e)), __ldg((const float4*)(base + __ldg(aslot + e) * 16)));
   }
-  __shared__ float red[8][4][32];
+  __shared__ float red[8][16][33];
 #pragma unroll
-  for (int l = 0; l < 4; l++) red[threadIdx.y][l][threadIdx.x] = acc[l];
+  for (int i = 0; i < 16; i++) red[warp][i][lane] = acc[i];
   __syncthreads();
-  if (threadIdx.y < 4 && v < cld) {
-    const int l = threadIdx.y;
-    float sum = 0.f;
+  // output element o = l * 128 + vv (vv: column inside the CTA's 128): contiguous stores
+  for (int o = threadIdx.x; o < 512; o += 256) {
+    const int l = o >> 7, vv = o & 127;
+    const int ln = (vv >> 4) * 4 + ((vv >> 2) & 3), i = l * 4 + (vv & 3);
+    const int64_t v = (int64_t)blockIdx.y * 128 + vv;
+    if (v < cld) {
+      float sum = 0.f;
 #pragma unroll
-    for (int q = 0; q < 8; q++) sum += red[q][l][threadIdx.x];
-    coef[((int64_t)at * 4 + l) * cld + v] = v < w ? (float)energy[4 * at + l] * sum : 0.f;
+      for (int q = 0; q < 8; q++) sum += red[q][i][ln];
+      coef[((int64_t)at * 4 + l) * cld + v] = v < w ? (float)energy[4 * at + l] * sum : 0.f;
+    }
   }
 }
 
-// chunk-major copy of w columns of a slot-major block (row stride ld), padded columns
-// zero; the padding rows of the second working buffer are zeroed too (the step kernels
-// never write padding rows, and they are read as halos)
-__global__ void to_chunk_major(const float* __restrict__ X, int64_t ld, int w, int cw, int wpad, int64_t n_slots,
-                               const uint8_t* __restrict__ mask, float* __restrict__ buf, float* __restrict__ buf2) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n_slots * wpad) return;
-  const int64_t s = t / wpad;
-  const int col = (int)(t - s * wpad);
-  const int c = col / cw, v = col - c * cw;
-  const int64_t o = ((int64_t)c * n_slots + s) * cw + v;
-  buf[o] = col < w ? X[s * ld + col] : 0.f;
-  if (!mask[s]) buf2[o] = 0.f;
+// chunk-major copy (chunks of 16 columns) of w columns of a slot-major block (row stride
+// ld), padded columns and padding rows zero (padding rows are not read); the padding rows
+// of the second working buffer are zeroed too (the step kernels never write padding rows,
+// and they are read as halos).  One warp per slot row, 32 consecutive columns per step.
+__global__ void __launch_bounds__(256) to_chunk_major(const float* __restrict__ X, int64_t ld, int w, int wpad,
+                                                      int64_t n_slots, const uint8_t* __restrict__ mask,
+                                                      float* __restrict__ buf, float* __restrict__ buf2) {
+  const int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (s >= n_slots) return;
+  const bool live = __ldg(mask + s) != 0;
+  const float* xr = X + s * ld;
+  float* br = buf + s * 16;
+  float* b2 = buf2 + s * 16;
+  const int64_t cstride = n_slots * 16;   // floats between chunks
+  for (int col = threadIdx.x & 31; col < wpad; col += 32) {
+    const int64_t o = (int64_t)(col >> 4) * cstride + (col & 15);
+    br[o] = (live && col < w) ? __ldg(xr + col) : 0.f;
+    if (!live) b2[o] = 0.f;
+  }
 }
 
 namespace {
@@ -425,9 +451,9 @@ int cm_chunk_width() { return 16; }
 
 cudaError_t launch_to_chunk_major(const Ham& H, const float* X, int64_t ld, int w, int cw, float* buf, float* buf2,
                                   cudaStream_t st) {
+  if (cw != 16) return cudaErrorInvalidValue;
   const int wpad = (w + cw - 1) / cw * cw;
-  const int64_t n = H.grid.n_slots * wpad;
-  to_chunk_major<<<blocks(n, 256), 256, 0, st>>>(X, ld, w, cw, wpad, H.grid.n_slots, H.d_mask, buf, buf2),
+  to_chunk_major<<<blocks(H.grid.n_slots, 8), 256, 0, st>>>(X, ld, w, wpad, H.grid.n_slots, H.d_mask, buf, buf2),
       count_launch();
   return cudaGetLastError();
 }
@@ -435,9 +461,10 @@ cudaError_t launch_to_chunk_major(const Ham& H, const float* X, int64_t ld, int 
 cudaError_t launch_kb_gather_cm(const Ham& H, const float* Y, int cw, int w, float* coef, int64_t cld,
                                 cudaStream_t st) {
   if (H.n_kb == 0 || w == 0) return cudaSuccess;
-  dim3 grid(H.n_kb, (unsigned)((cld + 31) / 32)), block(32, 8);
-  kb_gather_cm<<<grid, block, 0, st>>>(Y, H.grid.n_slots, cw, w, cld, H.d_kb_atom_ptr, H.d_kb_atom_slot,
-                                       H.d_kb_atom_chi32, H.d_kb_energy, coef),
+  if (cw != 16) return cudaErrorInvalidValue;
+  dim3 grid(H.n_kb, (unsigned)((cld + 127) / 128));
+  kb_gather_cm<<<grid, 256, 0, st>>>(Y, H.grid.n_slots, w, (w + 15) / 16, cld, H.d_kb_atom_ptr, H.d_kb_atom_slot,
+                                     H.d_kb_atom_chi32, H.d_kb_energy, coef),
       count_launch();
   return cudaGetLastError();
 }
