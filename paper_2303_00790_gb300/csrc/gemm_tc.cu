@@ -523,60 +523,72 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16&
   c = __float2bfloat16_rn(r2);
 }
 
+// Eight consecutive K values of one MN index form one 16-byte row of a core matrix in the
+// pre-tiled layout: split them and store the three pieces' rows directly.
+__device__ __forceinline__ void split8_store(const float* x, __nv_bfloat16* P0, __nv_bfloat16* P1,
+                                             __nv_bfloat16* P2, int64_t off) {
+  __align__(16) __nv_bfloat16 a[8], b[8], c[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) split3(x[i], a[i], b[i], c[i]);
+  *(uint4*)(P0 + off) = *(const uint4*)a;
+  *(uint4*)(P1 + off) = *(const uint4*)b;
+  *(uint4*)(P2 + off) = *(const uint4*)c;
+}
+
 // Op[i][r] = X[row(r0 + r)][c0 + i]  (gram operand: MN = columns, K = rows; row(r) = rowmap[r],
-// or r without a map); one CTA per block
+// or r without a map); one CTA per (128 x 32) block, a thread per (column, 8-row group):
+// eight row loads (coalesced over the warp's columns), one 16-byte store per piece
 __global__ void __launch_bounds__(256) split_T_kernel(const float* __restrict__ X, int64_t ld, int64_t r0, int nr,
                                                       int c0, int nc, int nkb, const int32_t* __restrict__ rowmap,
                                                       __nv_bfloat16* __restrict__ P0, __nv_bfloat16* __restrict__ P1,
                                                       __nv_bfloat16* __restrict__ P2) {
-  __shared__ __align__(16) __nv_bfloat16 sp[3][BLK_ELEMS];
   const int kb = blockIdx.x, mb = blockIdx.y;
-  for (int e = threadIdx.x; e < BLK_ELEMS; e += 256) {
-    const int i = e & 127, r = e >> 7;  // consecutive threads -> consecutive columns
-    const int gi = mb * 128 + i, gr = kb * TK + r;
-    float x = 0.f;
-    if (gi < nc && gr < nr) x = X[(rowmap ? (int64_t)rowmap[r0 + gr] : r0 + gr) * ld + c0 + gi];
-    __nv_bfloat16 a, b, c;
-    split3(x, a, b, c);
-    const int o = tiled_off(i, r);
-    sp[0][o] = a;
-    sp[1][o] = b;
-    sp[2][o] = c;
-  }
-  __syncthreads();
   const int64_t base = ((int64_t)mb * nkb + kb) * BLK_ELEMS;
-  for (int e = threadIdx.x; e < BLK_ELEMS / 8; e += 256) {
-    ((uint4*)(P0 + base))[e] = ((const uint4*)sp[0])[e];
-    ((uint4*)(P1 + base))[e] = ((const uint4*)sp[1])[e];
-    ((uint4*)(P2 + base))[e] = ((const uint4*)sp[2])[e];
+  const int i = threadIdx.x & 127, gi = mb * 128 + i;
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int ko = (threadIdx.x >> 7) + 2 * h;   // 8-row group 0..3 of the block
+    float x[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const int gr = kb * TK + ko * 8 + u;
+      x[u] = 0.f;
+      if (gi < nc && gr < nr) x[u] = X[(rowmap ? (int64_t)rowmap[r0 + gr] : r0 + gr) * ld + c0 + gi];
+    }
+    split8_store(x, P0, P1, P2, base + tiled_off(i, ko * 8));
   }
 }
 
-// Op[r][c] = X[row(r0 + r)][c]  (rotation A operand: MN = rows, K = columns)
+// Op[r][c] = X[row(r0 + r)][c]  (rotation A operand: MN = rows, K = columns); one CTA per
+// (128 x 32) block, a thread per (row, 8-column group): two float4 loads when the row
+// allows, one 16-byte store per piece
 __global__ void __launch_bounds__(256) split_N_kernel(const float* __restrict__ X, int64_t ld, int64_t r0, int nr,
                                                       int nc, int nkb, const int32_t* __restrict__ rowmap,
                                                       __nv_bfloat16* __restrict__ P0, __nv_bfloat16* __restrict__ P1,
                                                       __nv_bfloat16* __restrict__ P2) {
-  __shared__ __align__(16) __nv_bfloat16 sp[3][BLK_ELEMS];
   const int kb = blockIdx.x, mb = blockIdx.y;
-  for (int e = threadIdx.x; e < BLK_ELEMS; e += 256) {
-    const int c = e & 31, r = e >> 5;  // consecutive threads -> consecutive columns of a row
-    const int gr = mb * 128 + r, gc = kb * TK + c;
-    float x = 0.f;
-    if (gr < nr && gc < nc) x = X[(rowmap ? (int64_t)rowmap[r0 + gr] : r0 + gr) * ld + gc];
-    __nv_bfloat16 a, b, cc;
-    split3(x, a, b, cc);
-    const int o = tiled_off(r, c);
-    sp[0][o] = a;
-    sp[1][o] = b;
-    sp[2][o] = cc;
-  }
-  __syncthreads();
   const int64_t base = ((int64_t)mb * nkb + kb) * BLK_ELEMS;
-  for (int e = threadIdx.x; e < BLK_ELEMS / 8; e += 256) {
-    ((uint4*)(P0 + base))[e] = ((const uint4*)sp[0])[e];
-    ((uint4*)(P1 + base))[e] = ((const uint4*)sp[1])[e];
-    ((uint4*)(P2 + base))[e] = ((const uint4*)sp[2])[e];
+  const bool vec = (ld & 3) == 0 && (((uintptr_t)X) & 15) == 0;
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int r = (threadIdx.x >> 2) + 64 * h, ko = threadIdx.x & 3;
+    const int gr = mb * 128 + r, gc = kb * TK + ko * 8;
+    float x[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) x[u] = 0.f;
+    if (gr < nr) {
+      const float* row = X + (rowmap ? (int64_t)rowmap[r0 + gr] : r0 + gr) * ld;
+      if (vec && gc + 8 <= nc) {
+        const float4 lo = *(const float4*)(row + gc), hi = *(const float4*)(row + gc + 4);
+        x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
+        x[4] = hi.x; x[5] = hi.y; x[6] = hi.z; x[7] = hi.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+          if (gc + u < nc) x[u] = row[gc + u];
+      }
+    }
+    split8_store(x, P0, P1, P2, base + tiled_off(r, ko * 8));
   }
 }
 
@@ -721,12 +733,11 @@ cudaError_t launch_gram_tc(const float* A, int64_t lda, const float* B, int64_t 
   for (int64_t r0 = 0; r0 < rows; r0 += chunk) {
     const int nr = (int)std::min<int64_t>(chunk, rows - r0);
     const int nkb = cdiv(nr, TK);
-    split_T_kernel<<<dim3(nkb, cdiv(pad_to(m, TN), 128)), 256, 0, st>>>(A, lda, r0, nr, 0, m, nkb, rowmap, Ap[0],
-                                                                         Ap[1], Ap[2]),
+    // the Gram kernel reads the column blocks of its 128-wide tiles only
+    split_T_kernel<<<dim3(nkb, cdiv(m, TM)), 256, 0, st>>>(A, lda, r0, nr, 0, m, nkb, rowmap, Ap[0], Ap[1], Ap[2]),
         count_launch();
     if (!same)
-      split_T_kernel<<<dim3(nkb, cdiv(pad_to(n, TN), 128)), 256, 0, st>>>(B, ldb, r0, nr, 0, n, nkb, rowmap, Bp[0],
-                                                                           Bp[1], Bp[2]),
+      split_T_kernel<<<dim3(nkb, cdiv(n, GN)), 256, 0, st>>>(B, ldb, r0, nr, 0, n, nkb, rowmap, Bp[0], Bp[1], Bp[2]),
           count_launch();
     a.nkb = nkb;
     // split the K range over CTAs: pick the split whose active CTAs fill whole waves
