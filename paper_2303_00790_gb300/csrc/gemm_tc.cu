@@ -91,14 +91,20 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;                // base offset 0, absolute LBO mode, SWIZZLE_NONE
 }
 
-// instruction descriptor: D f32, A/B bf16, both K-major, M = 128, N = 256
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+// instruction descriptor: D f32, A/B bf16, both K-major, M = 128, N = n (a multiple of 16,
+// 16 <= n <= 256)
+__host__ __device__ constexpr uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+// N of a tile whose first `valid` columns are wanted: rounded up to 16, at most `full`
+__device__ __forceinline__ int tile_n(int valid, int full) { return min(full, max(16, (valid + 15) / 16 * 16)); }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
           tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -231,6 +237,8 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(TcArgs p) {
         if (it >= 2 && !mbar_wait(&tempty[b], ((it >> 1) - 1) & 1)) break;
         tc_fence_after();
         const uint32_t acc = tmem + b * TN;
+        // the last column tile multiplies only its valid columns (rounded up to 16)
+        const uint32_t idesc = idesc_n(tile_n(p.n - (t % p.n_tiles) * TN, TN));
         for (int kb = 0; kb < nk; kb++, g++) {
           const int s = g % STAGES;
           ok = mbar_wait(&full[s], (g / STAGES) & 1);
@@ -248,7 +256,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(TcArgs p) {
               // are 4 core matrices (512 B) apart
               const uint64_t ad = smem_desc(a_base + kk * 256, 128, 512);
               const uint64_t bd = smem_desc(b_base + kk * 256, 128, 512);
-              mma_bf16(acc, ad, bd, (kb > 0 || pr > 0 || kk > 0) ? 1u : 0u);
+              mma_bf16(acc, ad, bd, idesc, (kb > 0 || pr > 0 || kk > 0) ? 1u : 0u);
             }
           }
           mma_commit(&empty[s]);
@@ -336,14 +344,12 @@ constexpr int G_STAGES = 4;
 constexpr int G_A_BYTES = NPIECE * BLK_ELEMS * 2;        // 24 KB
 constexpr int G_STAGE_BYTES = 2 * G_A_BYTES;             // 48 KB
 constexpr int G_SMEM_BYTES = G_STAGES * G_STAGE_BYTES + 1024 + 512;
-constexpr uint32_t IDESC_N128 =
-    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16_n128(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16_n128(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                              uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
           tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(IDESC_N128), "r"(acc)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
       : "memory");
 }
 
@@ -420,6 +426,8 @@ __global__ void __launch_bounds__(320, 1) tc_gram_kernel(GramArgs p) {
   } else if (warp == 1) {
     if (lane == 0) {
       bool ok = true;
+      // the last column tile multiplies only its valid columns (rounded up to 16)
+      const uint32_t idesc = idesc_n(tile_n(p.n - nt * GN, GN));
       for (int c = 0; c < nsub && ok; c++) {
         const int b = c & 1;
         if (c >= 2 && !mbar_wait(&tempty[b], ((c >> 1) - 1) & 1)) break;
@@ -442,7 +450,7 @@ __global__ void __launch_bounds__(320, 1) tc_gram_kernel(GramArgs p) {
               const uint64_t ad = smem_desc(a_base + kk * 256, 128, 512);
               const uint64_t bd = smem_desc(b_base + kk * 256, 128, 512);
               const bool first = (it == it0) && (kk == 0) && (pr <= 1);
-              mma_bf16_n128(pr == 0 ? t_main : t_side, ad, bd, first ? 0u : 1u);
+              mma_bf16_n128(pr == 0 ? t_main : t_side, ad, bd, idesc, first ? 0u : 1u);
             }
           }
           mma_commit(&empty[s]);
