@@ -1045,12 +1045,17 @@ __global__ void __launch_bounds__(NT) dc_gemm_kernel(DcArgs a, int depth, int rt
       const int gr = row0 + rr, gk = k0 + kk;
       As[kk][rr] = gr < kd && gk < kd ? a.Z[(int64_t)(r0 + gr) + (int64_t)(r0 + gk) * ld] : 0.0;
     }
+    int nz = 0;
     for (int q = threadIdx.x; q < GTK * GTN; q += NT) {
       const int kk = q / GTN, cc = q % GTN;
       const int gk = k0 + kk, gc = col0 + cc;
-      Bs[kk][cc] = gk < kd && gc < N ? a.M[(int64_t)(r0 + gk) * ld + A0 + gc] : 0.0;
+      const double m = gk < kd && gc < N ? a.M[(int64_t)(r0 + gk) * ld + A0 + gc] : 0.0;
+      Bs[kk][cc] = m;
+      nz |= m != 0.0;
     }
-    __syncthreads();
+    // a slice of M without a nonzero adds nothing: deflated coordinates make most rows of
+    // M zero except for one unit entry, so heavily deflated merges skip most slices
+    if (!__syncthreads_or(nz)) continue;
 #pragma unroll
     for (int kk = 0; kk < GTK; kk++) {
       const double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
