@@ -5,12 +5,16 @@
 // Blocked right-looking algorithm over 32 x 32 tiles (tile (I, J) holds rows 32I..32I+31
 // and columns 32J..32J+31 of a column-major kp x kp matrix, kp = k rounded up to 32; the
 // padding is the identity).  For each block row j:
-//   phase B  R_jj = chol(S_jj)                    (every CTA factors the tile redundantly)
+//   phase B  R_jj = chol(S_jj)                    (factored ahead by CTA 0, see phase C)
 //            R_jm = R_jj^-T S_jm      for m > j   (forward substitution, one warp per tile)
 //            W_lj = B_lj R_jj^-1      for l <= j  (B_jj = I; B_lj accumulates below)
 //   phase C  S_ml -= R_jm^T R_jl      for j < m <= l    (trailing update)
 //            B_li -= W_lj R_ji        for l <= j < i    (right-looking R W = I)
-// with a grid-wide barrier after each phase.  The two triangular recurrences are those of
+// with a grid-wide barrier after each phase.  Look-ahead: in phase C of block row j, CTA 0
+// takes only the update of the next diagonal tile S_{j+1,j+1} and then factors it, while
+// the other CTAs apply the remaining updates, so that phase B of block row j+1 starts from
+// R_{j+1,j+1} instead of a 32-step pivot chain (block row 0 and one-CTA grids factor the
+// tile in phase B, in every CTA).  The two triangular recurrences are those of
 // the textbook blocked Cholesky and triangular inversion (Golub & Van Loan, Matrix
 // Computations, Sec. 4.2 and 3.1); every tile product is FP64 FMA.  On this part FP64
 // runs at ~1 TFLOP/s, so the kernel is FP64-ALU bound: 2 k^3 / 3 flop in total.
@@ -18,8 +22,8 @@
 // A pivot counts as failed when it is not above tau_c = S_cc * max((c + 8) u64, floor_rel)
 // (or is not finite): (c + 8) u64 S_cc is the rounding level of a Cholesky pivot, so an
 // exactly dependent column fails whatever the rounding order; floor_rel > 0 raises it to
-// the rounding level of the Gram matrix itself.  Every CTA computes the same pivots and
-// leaves at the same block row.  Barrier waits are bounded (about a second of clock
+// the rounding level of the Gram matrix itself.  Every CTA sees the same failed pivot (its
+// own in block row 0, CTA 0's published one after that) and leaves at the same block row.  Barrier waits are bounded (about a second of clock
 // cycles); a CTA that gives up sets the timeout word and the others follow.
 #include <cuda_runtime.h>
 
@@ -41,9 +45,10 @@ struct CholArgs {
   double* A;      // kp x kp: the working matrix, R in its upper triangle at the end
   double* W;      // kp x kp: B, then W = R^-1 (upper)
   double* D;      // kp: the diagonal of S before the factorisation
+  double* RC;     // kp: 1 / R_cc of the diagonal tiles factored ahead by CTA 0
   double* out;    // k x k output (may alias S): R^-1 upper, zero below
   int64_t ldo;
-  unsigned* bar;  // [0] arrival count, [1] generation
+  unsigned* bar;  // [0] arrival count, [1] generation, [2] failed pivot of a tile factored ahead (1-based) or 0
   int* status;    // [0] first failed pivot (1-based column) or 0, [1] barrier timeout
   double floor_rel;
   long long spin_limit;
@@ -245,20 +250,34 @@ __global__ void __launch_bounds__(NTHR) chol_inv_kernel(CholArgs a) {
   for (int64_t q = tid; q < kp; q += nth) a.D[q] = q < a.k ? a.S[q + q * a.lds] : 1.0;
   if (!grid_sync(a)) return;
   for (int j = 0; j < nt; j++) {
-    // phase B: every CTA factors the diagonal tile (the same arithmetic everywhere)
+    // phase B: the diagonal tile's factor.  Block row 0 (and a one-CTA grid): every CTA
+    // factors it (the same arithmetic everywhere); later block rows: CTA 0 factored it at
+    // the end of the previous phase C, as soon as its one update there was done, and every
+    // CTA loads R_jj and 1 / R_cc.
     const int r0 = j * TB;
+    const bool ahead_done = j > 0 && gridDim.x > 1;
     for (int q = threadIdx.x; q < TB * TB; q += NTHR) {
       const int r = q & (TB - 1), c = q >> 5;
       sm.T[r + c * LDT] = r <= c ? ld(a.A + at(kp, r0 + r, r0 + c)) : 0.0;
     }
-    if (threadIdx.x < TB) sm.dg[threadIdx.x] = ld(a.D + r0 + threadIdx.x);
-    if (threadIdx.x == 0) sm.fail = -1;
-    __syncthreads();
-    if (threadIdx.x < 128) factor_diag4(a, j, sm);
-    __syncthreads();
-    if (sm.fail >= 0) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) a.status[0] = j * TB + sm.fail + 1;
-      return;
+    if (ahead_done) {
+      if (threadIdx.x < TB) sm.rc[threadIdx.x] = ld(a.RC + r0 + threadIdx.x);
+      __syncthreads();
+      const int f = (int)__ldcg(a.bar + 2);
+      if (f > 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.status[0] = f;
+        return;
+      }
+    } else {
+      if (threadIdx.x < TB) sm.dg[threadIdx.x] = ld(a.D + r0 + threadIdx.x);
+      if (threadIdx.x == 0) sm.fail = -1;
+      __syncthreads();
+      if (threadIdx.x < 128) factor_diag4(a, j, sm);
+      __syncthreads();
+      if (sm.fail >= 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.status[0] = j * TB + sm.fail + 1;
+        return;
+      }
     }
     // items: m = j+1 .. nt-1 (panel tiles R_jm), then l = 0 .. j (inverse tiles W_lj)
     for (int it = blockIdx.x; it < nt; it += gridDim.x) {
@@ -279,10 +298,14 @@ __global__ void __launch_bounds__(NTHR) chol_inv_kernel(CholArgs a) {
       __syncthreads();
     }
     if (!grid_sync(a)) return;
-    // phase C
+    // phase C.  Item 0 is the next diagonal tile (j+1, j+1), whose only update this is: with
+    // more than one CTA, CTA 0 takes it alone and then factors the tile while the other CTAs
+    // work through items 1, 2, ...
     const int n = nt - 1 - j;
     const int n_trail = n * (n + 1) / 2, n_inv = (j + 1) * n;
-    for (int it = blockIdx.x; it < n_trail + n_inv; it += gridDim.x) {
+    const bool ahead = n >= 1 && gridDim.x > 1;
+    const int it_step = ahead ? (blockIdx.x == 0 ? n_trail + n_inv : (int)gridDim.x - 1) : (int)gridDim.x;
+    for (int it = blockIdx.x; it < n_trail + n_inv; it += it_step) {
       if (it < n_trail) {
         // it -> (m', l') with 0 <= m' <= l' < n, l'-major
         int lp = (int)((sqrt(8.0 * it + 1.0) - 1.0) * 0.5);
@@ -297,6 +320,30 @@ __global__ void __launch_bounds__(NTHR) chol_inv_kernel(CholArgs a) {
         const int l = q % (j + 1), i = j + 1 + q / (j + 1);
         tile_update(kp, a.W + at(kp, l * TB, i * TB), a.W + at(kp, l * TB, j * TB), false,
                     a.A + at(kp, j * TB, i * TB), Ps, Qs);
+      }
+    }
+    if (ahead && blockIdx.x == 0) {
+      // factor the updated tile (j+1, j+1) now; publish R (upper), 1 / R_cc and a failure
+      const int r1 = (j + 1) * TB;
+      __threadfence();   // the tile's update (item 0, this CTA) is read back through L2
+      __syncthreads();
+      for (int q = threadIdx.x; q < TB * TB; q += NTHR) {
+        const int r = q & (TB - 1), c = q >> 5;
+        sm.T[r + c * LDT] = r <= c ? ld(a.A + at(kp, r1 + r, r1 + c)) : 0.0;
+      }
+      if (threadIdx.x < TB) sm.dg[threadIdx.x] = ld(a.D + r1 + threadIdx.x);
+      if (threadIdx.x == 0) sm.fail = -1;
+      __syncthreads();
+      if (threadIdx.x < 128) factor_diag4(a, j + 1, sm);
+      __syncthreads();
+      if (sm.fail < 0) {
+        for (int q = threadIdx.x; q < TB * TB; q += NTHR) {
+          const int r = q & (TB - 1), c = q >> 5;
+          if (r <= c) a.A[at(kp, r1 + r, r1 + c)] = sm.T[r + c * LDT];
+        }
+        if (threadIdx.x < TB) a.RC[r1 + threadIdx.x] = sm.rc[threadIdx.x];
+      } else if (threadIdx.x == 0) {
+        a.bar[2] = (unsigned)((j + 1) * TB + sm.fail + 1);
       }
     }
     if (!grid_sync(a)) return;
@@ -331,7 +378,7 @@ int grid_for(int nt) {
 
 size_t chol_inv_work_bytes(int k) {
   const size_t kp = (size_t)((k + TB - 1) / TB) * TB;
-  return 2 * kscf_align256(kp * kp * 8) + kscf_align256(kp * 8) + 256;
+  return 2 * kscf_align256(kp * kp * 8) + 2 * kscf_align256(kp * 8) + 256;
 }
 
 cudaError_t launch_chol_inv(const double* S, int64_t lds, int k, double floor_rel, double* out, int64_t ldo,
@@ -347,14 +394,15 @@ cudaError_t launch_chol_inv(const double* S, int64_t lds, int k, double floor_re
   a.A = (double*)w;
   a.W = (double*)(w + mat);
   a.D = (double*)(w + 2 * mat);
-  a.bar = (unsigned*)(w + 2 * mat + kscf_align256((size_t)a.kp * 8));
+  a.RC = (double*)(w + 2 * mat + kscf_align256((size_t)a.kp * 8));
+  a.bar = (unsigned*)(w + 2 * mat + 2 * kscf_align256((size_t)a.kp * 8));
   a.out = out;
   a.ldo = ldo;
   a.status = status;
   a.floor_rel = floor_rel;
   a.spin_limit = spin_limit;
   a.leave_cta = leave_cta;
-  cudaError_t e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), st);
+  cudaError_t e = cudaMemsetAsync(a.bar, 0, 3 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(status, 0, 2 * sizeof(int), st);
   if (e != cudaSuccess) return e;
