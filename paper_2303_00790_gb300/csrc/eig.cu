@@ -1265,7 +1265,7 @@ cudaError_t launch_sym_eig(double* A, int64_t lda, int n, double* w, void* work,
   t.A = A;
   t.lda = lda;
   t.n = n;
-  t.P = std::max(1, std::min(std::min(nsm, MAX_P), (n - 1 + 7) / 8));
+  t.P = std::max(1, std::min(std::min(nsm, MAX_P), (n - 1 + 3) / 4));
   t.d = (double*)P_(L_D);
   t.e = (double*)P_(L_E);
   t.tau = (double*)P_(L_TAU);
