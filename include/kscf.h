@@ -254,7 +254,9 @@ int kscf_orthonormalize(const kscf_ham* ham, void* X, int64_t ld, int k, int dty
  * tiles are computed and mirrored), Hs = Q Lambda Q^T (FP64 symmetric eigensolver,
  * ascending), X <- X Q.  In tensor mode the eigenvector signs are chosen with
  * diag(Q) >= 0 and the rotation is applied as X + X (Q - I).  Requires h^3 X^T X = I on
- * entry.  eigvals_host (k doubles) receives Lambda; synchronous on `stream`. */
+ * entry.  HX is computed in column blocks as wide as the work buffer allows: all k columns
+ * with kscf_workspace_size(..., KSCF_OP_RR, ..., block = 0), halved (multiples of 32) for a
+ * smaller buffer.  eigvals_host (k doubles) receives Lambda; synchronous on `stream`. */
 int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int k, int dtype, int mode,
                        double* eigvals_host, void* work, size_t work_bytes, void* stream);
 

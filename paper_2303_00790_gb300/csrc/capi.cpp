@@ -502,16 +502,18 @@ extern "C" int kscf_rayleigh_ritz(const kscf_ham* ham, void* X, int64_t ld, int 
     return KSCF_ERR_INVALID;
   }
   const Ham& H = ham->h;
-  // block width of the H X stream: bounded so that the N x w buffer stays modest
+  // block width of the H X stream: the widest (k, then halving to multiples of 32) whose
+  // buffers fit the caller's work buffer, so that with the default workspace the projection
+  // is one symmetric Gram over one split of X
   int block = k;
-  {
-    const size_t cap = (size_t)1 << 30;
-    const size_t per_col = (size_t)H.grid.n_slots * esize(dtype);
-    if ((size_t)k * per_col > cap) block = std::max<int>(32, (int)(cap / per_col) / 32 * 32);
-  }
   RRPlan p;
   rc = rr_plan(H, k, dtype, mode, block, &p);
   if (rc) return rc;
+  while (rr_bytes(p) > work_bytes && block > 32) {
+    block = std::max(32, block / 2 / 32 * 32);
+    rc = rr_plan(H, k, dtype, mode, block, &p);
+    if (rc) return rc;
+  }
   rc = check_work(work, work_bytes, rr_bytes(p), "kscf_rayleigh_ritz");
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
