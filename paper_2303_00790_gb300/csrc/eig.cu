@@ -1106,17 +1106,23 @@ __global__ void dc_unscale_kernel(const double* lam, int n, const double* tscale
 // ------------------------------------------------------- back-transformation ----
 //
 // Z <- H_0 H_1 ... H_{n-2} Z: each CTA owns cw columns, g = (warps of the CTA) / cw warps
-// per column, the columns held in shared memory; reflectors from the last to the first,
-// each staged in shared memory (double-buffered, the next one loaded while the current one
-// is applied): s = tau_j v_j^T z, z <- z - s v_j.  Output into O (column-major, ldo).
+// per column, the columns held in shared memory; reflectors from the last to the first.
+// With `pairs`, two consecutive reflectors are applied at once: for a = j, b = j - 1,
+//   H_b H_a z = z - tau_a s_a v_a - tau_b (s_b - tau_a c s_a) v_b,
+// s_a = v_a^T z, s_b = v_b^T z (one pass over z), c = v_b^T v_a (cpair[j], computed
+// before); otherwise one at a time, s = tau_j v_j^T z, z <- z - s v_j.  The reflectors are
+// staged in shared memory, double-buffered (the next item loaded while the current one is
+// applied).  Output into O (column-major, ldo).
 constexpr int BT_THREADS = 384;   // largest CTA the kernel is compiled for
 __global__ void __launch_bounds__(BT_THREADS, 1) backtransform_kernel(const double* Z, int64_t ldz, const double* V,
-                                                                      int64_t ldv, const double* tau, int n, int cw,
+                                                                      int64_t ldv, const double* tau,
+                                                                      const double* cpair, int pairs, int n, int cw,
                                                                       double* O, int64_t ldo) {
   extern __shared__ __align__(16) double smz[];
+  const int per = pairs ? 2 : 1;          // vectors per item
   double* zc = smz;                       // cw x n
-  double* vb = smz + (int64_t)cw * n;     // 2 x n
-  __shared__ double part[BT_THREADS / 32];
+  double* vbase = smz + (int64_t)cw * n;  // 2 buffers x per x n
+  __shared__ double part[BT_THREADS / 32][2];
   const int nthr = blockDim.x, nwarp = nthr >> 5;
   const int g = nwarp / cw;               // warps per column
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1125,60 +1131,127 @@ __global__ void __launch_bounds__(BT_THREADS, 1) backtransform_kernel(const doub
   const int ncol = min(cw, n - col0);
   for (int c = 0; c < ncol; c++)
     for (int l = threadIdx.x; l < n; l += nthr) zc[(int64_t)c * n + l] = Z[l + (int64_t)(col0 + c) * ldz];
-  auto stage = [&](int j, int buf) {
-    double* dst = vb + (int64_t)buf * n;
+  // next item at or below j: the highest active reflector, paired with the one below it when
+  // that one is active too
+  auto next_item = [&](int j, int* jj, bool* pr) -> bool {
+    while (j >= 0 && tau[j] == 0.0) j--;
+    if (j < 0) return false;
+    *jj = j;
+    *pr = pairs && j >= 1 && tau[j - 1] != 0.0;
+    return true;
+  };
+  // buffer: v_j in [0, n) for rows l >= j+1 (and a zero at row j for a pair), v_{j-1} in
+  // [n, 2n) for rows l >= j
+  auto stage = [&](int j, bool pr, int buf) {
+    double* dst = vbase + (int64_t)buf * per * n;
     const double* src = V + (int64_t)j * ldv;
     for (int l = j + 1 + threadIdx.x; l < n; l += nthr) {
       const uint32_t da = (uint32_t)__cvta_generic_to_shared(dst + l);
       asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(da), "l"(src + l) : "memory");
     }
+    if (pr) {
+      if (threadIdx.x == 0) dst[j] = 0.0;
+      const double* srcb = V + (int64_t)(j - 1) * ldv;
+      for (int l = j + threadIdx.x; l < n; l += nthr) {
+        const uint32_t da = (uint32_t)__cvta_generic_to_shared(dst + n + l);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(da), "l"(srcb + l) : "memory");
+      }
+    }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  int jn = n - 2;
-  while (jn >= 0 && tau[jn] == 0.0) jn--;
-  if (jn >= 0) stage(jn, 0);
-  int buf = 0;
-  for (int j = jn; j >= 0;) {
-    int jnext = j - 1;
-    while (jnext >= 0 && tau[jnext] == 0.0) jnext--;
-    if (jnext >= 0) {
-      stage(jnext, buf ^ 1);
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
-    } else {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-    }
-    __syncthreads();
-    const double* v = vb + (int64_t)buf * n;
-    const double tj = tau[j];
-    double s = 0.0;
-    if (cl < ncol) {
-      const double* z = zc + (int64_t)cl * n;
-      double s1 = 0.0;
-      int l = j + 1 + gw * 32 + lane;
-      for (; l + 32 * g < n; l += 64 * g) {
-        s = fma(v[l], z[l], s);
-        s1 = fma(v[l + 32 * g], z[l + 32 * g], s1);
+  int j;
+  bool pr;
+  if (next_item(n - 2, &j, &pr)) {
+    stage(j, pr, 0);
+    int buf = 0;
+    for (;;) {
+      int jn;
+      bool prn;
+      const bool more = next_item(pr ? j - 2 : j - 1, &jn, &prn);
+      if (more) {
+        __syncthreads();   // the other buffer's last readers are done
+        stage(jn, prn, buf ^ 1);
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
       }
-      if (l < n) s = fma(v[l], z[l], s);
-      s = warp_sum(s + s1);
-    }
-    if (g > 1) {
-      if (lane == 0) part[warp] = s;
       __syncthreads();
-      s = 0.0;
-      for (int q = 0; q < g; q++) s += part[cl * g + q];
+      const double* va = vbase + (int64_t)buf * per * n;
+      const double* vb = va + n;
+      const int lo = pr ? j : j + 1;   // first row of the item's support
+      double sa = 0.0, sb = 0.0;
+      if (cl < ncol) {
+        const double* z = zc + (int64_t)cl * n;
+        double sa1 = 0.0, sb1 = 0.0;
+        int l = lo + gw * 32 + lane;
+        if (pr) {
+          for (; l + 32 * g < n; l += 64 * g) {
+            const double z0 = z[l], z1 = z[l + 32 * g];
+            sa = fma(va[l], z0, sa);
+            sb = fma(vb[l], z0, sb);
+            sa1 = fma(va[l + 32 * g], z1, sa1);
+            sb1 = fma(vb[l + 32 * g], z1, sb1);
+          }
+          if (l < n) {
+            sa = fma(va[l], z[l], sa);
+            sb = fma(vb[l], z[l], sb);
+          }
+          sa = warp_sum(sa + sa1);
+          sb = warp_sum(sb + sb1);
+        } else {
+          for (; l + 32 * g < n; l += 64 * g) {
+            sa = fma(va[l], z[l], sa);
+            sa1 = fma(va[l + 32 * g], z[l + 32 * g], sa1);
+          }
+          if (l < n) sa = fma(va[l], z[l], sa);
+          sa = warp_sum(sa + sa1);
+        }
+      }
+      if (g > 1) {
+        if (lane == 0) {
+          part[warp][0] = sa;
+          part[warp][1] = sb;
+        }
+        __syncthreads();
+        sa = 0.0;
+        sb = 0.0;
+        for (int q = 0; q < g; q++) {
+          sa += part[cl * g + q][0];
+          sb += part[cl * g + q][1];
+        }
+      }
+      if (cl < ncol) {
+        double* z = zc + (int64_t)cl * n;
+        const double ta = tau[j];
+        const double al = ta * sa;
+        if (pr) {
+          const double be = tau[j - 1] * fma(-ta * cpair[j], sa, sb);
+          for (int l = lo + gw * 32 + lane; l < n; l += 32 * g) z[l] = fma(-be, vb[l], fma(-al, va[l], z[l]));
+        } else {
+          for (int l = lo + gw * 32 + lane; l < n; l += 32 * g) z[l] = fma(-al, va[l], z[l]);
+        }
+      }
+      if (!more) break;
+      buf ^= 1;
+      j = jn;
+      pr = prn;
     }
-    if (cl < ncol) {
-      double* z = zc + (int64_t)cl * n;
-      const double st = s * tj;
-      for (int l = j + 1 + gw * 32 + lane; l < n; l += 32 * g) z[l] = fma(-st, v[l], z[l]);
-    }
-    __syncthreads();
-    buf ^= 1;
-    j = jnext;
   }
+  __syncthreads();
   for (int c = 0; c < ncol; c++)
     for (int l = threadIdx.x; l < n; l += nthr) O[l + (int64_t)(col0 + c) * ldo] = zc[(int64_t)c * n + l];
+}
+
+// cpair[j] = v_{j-1}^T v_j (rows l >= j+1, where v_j lives) for 1 <= j <= n-2: one warp per j
+__global__ void __launch_bounds__(NT) bt_pair_dot_kernel(const double* V, int64_t ldv, int n, double* cpair) {
+  const int j = 1 + (int)(blockIdx.x * (NT / 32) + (threadIdx.x >> 5)), lane = threadIdx.x & 31;
+  if (j > n - 2) return;
+  const double* va = V + (int64_t)j * ldv;
+  const double* vb = V + (int64_t)(j - 1) * ldv;
+  double s = 0.0;
+  for (int l = j + 1 + lane; l < n; l += 32) s = fma(vb[l], va[l], s);
+  s = warp_sum(s);
+  if (lane == 0) cpair[j] = s;
 }
 
 }  // namespace
@@ -1371,20 +1444,26 @@ cudaError_t launch_sym_eig(double* A, int64_t lda, int n, double* w, void* work,
   // One warp per column, ceil(n / SMs) columns per CTA (at most 8), so that every SM's FP64
   // pipes get a share; when 8 columns do not fit in shared memory, 8-warp CTAs of 4, 2, 1
   // columns of 2, 4, 8 warps (a 12-warp CTA with 6 two-warp columns was slower than one
-  // warp per column: the per-reflector cross-warp sum costs a CTA-wide barrier)
+  // warp per column: the per-reflector cross-warp sum costs a CTA-wide barrier).  Reflectors
+  // in pairs when two double-buffered pairs fit beside the columns, else one at a time.
   const int sms = sm_count();
   int cw = (int)std::min<int64_t>(8, ((int64_t)n + sms - 1) / sms);
   int bt_threads = 32 * cw;
-  if ((size_t)(cw + 2) * n * 8 > SMEM_CAP) {
+  int pairs = (size_t)(cw + 4) * n * 8 <= SMEM_CAP ? 1 : 0;
+  if (!pairs && (size_t)(cw + 2) * n * 8 > SMEM_CAP) {
     cw = 8;
     while (cw > 1 && (size_t)(cw + 2) * n * 8 > SMEM_CAP) cw /= 2;
     bt_threads = NT;
   }
-  const size_t bt_smem = (size_t)(cw + 2) * n * 8;
+  const size_t bt_smem = (size_t)(cw + 2 * (pairs ? 2 : 1)) * n * 8;
+  double* cpair = t.pbuf;   // free once the tridiagonalisation is done
+  if (pairs && n >= 3)
+    bt_pair_dot_kernel<<<(n - 2 + NT / 32 - 1) / (NT / 32), NT, 0, st>>>(t.V, n, n, cpair), count_launch();
   if ((e = cudaFuncSetAttribute(backtransform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt_smem)) !=
       cudaSuccess)
     return e;
-  backtransform_kernel<<<(n + cw - 1) / cw, bt_threads, bt_smem, st>>>(a.Z, n, t.V, n, t.tau, n, cw, A, lda),
+  backtransform_kernel<<<(n + cw - 1) / cw, bt_threads, bt_smem, st>>>(a.Z, n, t.V, n, t.tau, cpair, pairs, n, cw, A,
+                                                                      lda),
       count_launch();
   // non-finite input: report through info[2]
   info_nonfinite_kernel<<<1, 32, 0, st>>>(amax, info), count_launch();
