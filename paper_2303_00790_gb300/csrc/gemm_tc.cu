@@ -701,7 +701,9 @@ size_t rotate_tc_work_bytes(int64_t rows, int kin, int kout) {
 cudaError_t launch_gram_tc(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t rows, int m, int n,
                            double scale, double* C, int64_t ldc, bool accumulate, void* work, size_t work_bytes,
                            cudaStream_t st, bool symmetric_result, const int32_t* rowmap) {
-  const int64_t chunk = gram_chunk_for_work(rows, m, n, work_bytes);
+  // same operand: one set of split pieces (no B pieces), so a chunk twice as long fits
+  const bool same = (A == B && lda == ldb && m == n);
+  const int64_t chunk = gram_chunk_for_work(rows, m, same ? 0 : n, work_bytes);
   if (chunk < TK && rows > 0) return cudaErrorInvalidValue;
   cudaError_t e = prepare_kernel();
   if (e != cudaSuccess) return e;
@@ -709,9 +711,8 @@ cudaError_t launch_gram_tc(const float* A, int64_t lda, const float* B, int64_t 
     zero_f64_kernel<<<cdiv((int64_t)m * n, 256), 256, 0, st>>>(C, m, n, ldc), count_launch();
   }
   if (rows == 0 || m == 0 || n == 0) return cudaGetLastError();
-  // same operand: one set of split pieces; symmetric result (same operand, or a product
-  // the caller knows to be symmetric): upper-triangle tiles only, mirrored at the end
-  const bool same = (A == B && lda == ldb && m == n);
+  // symmetric result (same operand, or a product the caller knows to be symmetric):
+  // upper-triangle tiles only, mirrored at the end
   const bool sym = same || (symmetric_result && m == n && !accumulate);
   char* w = (char*)work;
   __nv_bfloat16* Ap[NPIECE];
@@ -722,7 +723,7 @@ cudaError_t launch_gram_tc(const float* A, int64_t lda, const float* B, int64_t 
   }
   for (int q = 0; q < NPIECE; q++) {
     Bp[q] = (__nv_bfloat16*)w;
-    w += kscf_align256(piece_bytes(n, chunk));
+    if (!same) w += kscf_align256(piece_bytes(n, chunk));
   }
   GramArgs a = {};
   for (int q = 0; q < NPIECE; q++) {
