@@ -231,7 +231,10 @@ int kscf_chebyshev_filter(const kscf_ham* ham, void* X, int64_t ld, int k, int d
 /* In place Cholesky-QR (orthonormalisation step of CheFSI):
  *   S = h^3 X^T X (k x k, FP64 sums), S = R^T R (FP64 Cholesky), X <- X R^-1,
  * so that h^3 X^T X = I.  For F32 X the step is repeated once (CholeskyQR2,
- * Yamamoto et al. 2015), the second rotation applied as X + X (R2^-1 - I).  Returns
+ * Yamamoto et al. 2015), the second rotation applied as X + X (R2^-1 - I); when the second
+ * pass's Gram matrix S = I + E has max_ij |E_ij| <= 1e-4, R2^-1 is replaced by the
+ * first-order inverse square root I - E/2 (no factorisation; the same span, and
+ * h^3 X^T X = I + O(E^2) with E^2 below the FP32 rounding of the rotation).  Returns
  * KSCF_ERR_NOT_SPD if the Cholesky factorisation fails, i.e. a pivot c (0-based) is not
  * above (c + 8) 2^-53 S_cc (X rank-deficient to working precision); X is then left
  * unchanged.  KSCF_ERR_TIMEOUT if a bounded grid barrier of the factorisation kernel

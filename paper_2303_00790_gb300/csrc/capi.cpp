@@ -4,6 +4,7 @@
 // k x k FP64 symmetric eigensolver from eig.cu.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "kscf_internal.h"
@@ -241,6 +242,13 @@ int gram(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t rows, i
   return KSCF_OK;
 }
 
+// Second FP32 pass: when the Gram matrix S = I + E is within this of I (max norm), X is
+// rotated by the first-order inverse square root W = I - E/2 instead of R^-1 from a
+// Cholesky factorisation: h^3 (XW)^T (XW) = I + O(E^2), and E^2 <= 1e-8 is below the FP32
+// rotation's own rounding (~3e-7), so the result is as orthonormal as after the factorised
+// pass, with the same span
+constexpr double kFp32PolarTol = 1e-4;
+
 // One Cholesky-QR pass: S = h^3 X^T X, S = R^T R, X <- X R^-1 (the factor and its inverse
 // from one FP64 kernel, chol.cu).  When the factorisation fails and `shifted` is non-null,
 // the Gram matrix is recomputed and its diagonal shifted by 16 k u max_i S_ii (u the unit
@@ -250,7 +258,7 @@ int gram(const void* A, int64_t lda, const void* B, int64_t ldb, int64_t rows, i
 // fails on a pivot at the Gram matrix's own rounding level (8 u S_cc), where the plain
 // factor would amplify rounding noise into the basis.
 int cholqr_pass(const Ham& H, void* X, int64_t ld, int k, int dtype, int mode, const OrthoPlan& p, Carver& cv,
-                bool second_pass, cudaStream_t st, bool* shifted = nullptr) {
+                bool second_pass, cudaStream_t st, bool* shifted = nullptr, double polar_tol = 0.0) {
   Carver c = cv;
   double* S = (double*)c.take(p.S);
   void* Rinv = c.take(p.Rinv);
@@ -284,6 +292,26 @@ int cholqr_pass(const Ham& H, void* X, int64_t ld, int k, int dtype, int mode, c
   };
   int rc = gram(X, ld, X, ld, rows, k, k, dtype, mode, h3, S, k, tcw, p.tc, st, false, live);
   if (rc) return rc;
+  if (polar_tol > 0.0) {
+    // S = I + E with |E| <= polar_tol: X <- X (I - E/2), no factorisation
+    unsigned long long* dv = (unsigned long long*)(status + 16);   // inside the status block
+    KSCF_CUDA_TRY(launch_dev_identity(S, k, k, dv, st));
+    unsigned long long bits = 0;
+    KSCF_CUDA_TRY(cudaMemcpyAsync(&bits, dv, sizeof(bits), cudaMemcpyDeviceToHost, st));
+    KSCF_CUDA_TRY(cudaStreamSynchronize(st));
+    rc = check_tc(mode, "Cholesky-QR");
+    if (rc) return rc;
+    double dev;
+    std::memcpy(&dev, &bits, sizeof(dev));
+    if (dev <= polar_tol) {
+      KSCF_CUDA_TRY(launch_polar_first_order(S, k, k, st));
+      if (mode != KSCF_GEMM_TENSOR) KSCF_CUDA_TRY(launch_f64_to_dtype(S, (int64_t)k * k, dtype, Rinv, st));
+      rc = rotate_inplace(H, X, ld, k, dtype, mode, Rinv, S, true, panel, p.prows, tcw, p.tc, st);
+      if (rc) return rc;
+      KSCF_CUDA_TRY(cudaStreamSynchronize(st));
+      return check_tc(mode, "Cholesky-QR");
+    }
+  }
   rc = factor(shifted ? 8.0 * u : 0.0);
   if (rc) return rc;
   if (hst[0] > 0 && shifted) {
@@ -487,7 +515,9 @@ extern "C" int kscf_orthonormalize(const kscf_ham* ham, void* X, int64_t ld, int
     rc = cholqr_pass(H, X, ld, k, dtype, mode, p, cv, false, st);
     if (rc) return rc;
   }
-  if (dtype == KSCF_F32) rc = cholqr_pass(H, X, ld, k, dtype, mode, p, cv, true, st);
+  // FP32: a second pass (its rotation by the first-order inverse square root of its Gram
+  // matrix when that is within kFp32PolarTol of I, else by a factorised R^-1)
+  if (dtype == KSCF_F32) rc = cholqr_pass(H, X, ld, k, dtype, mode, p, cv, true, st, nullptr, kFp32PolarTol);
   return rc;
 }
 

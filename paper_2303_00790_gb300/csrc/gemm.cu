@@ -6,6 +6,8 @@
 // gemm_tc.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "kscf_internal.h"
 
 namespace kscf {
@@ -269,6 +271,57 @@ __global__ void diag_finite_kernel(const double* S, int k, int64_t lds, int* sta
 
 cudaError_t launch_diag_finite(const double* S, int k, int64_t lds, int* status, cudaStream_t st) {
   diag_finite_kernel<<<1, 256, 0, st>>>(S, k, lds, status), count_launch();
+  return cudaGetLastError();
+}
+
+// *out = max_ij |S_ij - delta_ij| over the k x k matrix S (column-major, lds), as the bit
+// pattern of a non-negative double (a NaN or Inf element counts as +Inf); *out is 0 before
+__global__ void __launch_bounds__(256) dev_identity_kernel(const double* S, int k, int64_t lds,
+                                                           unsigned long long* out) {
+  double m = 0.0;
+  const int64_t total = (int64_t)k * k;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = q / k;
+    const int r = (int)(q - c * k);
+    double v = fabs(S[r + c * lds] - (r == c ? 1.0 : 0.0));
+    if (!(v <= 1.7976931348623157e308)) v = __longlong_as_double(0x7ff0000000000000LL);
+    m = fmax(m, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ double wm[8];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = fmax(m, wm[w]);
+    atomicMax(out, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// S <- (3 I - S) / 2 in place (k x k, column-major, lds): for S = I + E the first-order
+// inverse square root I - E / 2
+__global__ void polar_first_order_kernel(double* S, int k, int64_t lds) {
+  const int64_t total = (int64_t)k * k;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = q / k;
+    const int r = (int)(q - c * k);
+    double* x = S + r + c * lds;
+    *x = ((r == c ? 3.0 : 0.0) - *x) * 0.5;
+  }
+}
+
+cudaError_t launch_polar_first_order(double* S, int k, int64_t lds, cudaStream_t st) {
+  const int64_t total = (int64_t)k * k;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(304, (total + 255) / 256));
+  polar_first_order_kernel<<<grid, 256, 0, st>>>(S, k, lds), count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dev_identity(const double* S, int k, int64_t lds, unsigned long long* out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  const int64_t total = (int64_t)k * k;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(304, (total + 255) / 256));
+  dev_identity_kernel<<<grid, 256, 0, st>>>(S, k, lds, out), count_launch();
   return cudaGetLastError();
 }
 

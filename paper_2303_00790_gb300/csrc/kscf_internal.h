@@ -148,6 +148,10 @@ cudaError_t launch_finite_rows(const Ham& H, const void* X, int64_t ld, int k, i
                                cudaStream_t st);
 // *status = 1 if a diagonal element of S is NaN or Inf, else 0
 cudaError_t launch_diag_finite(const double* S, int k, int64_t lds, int* status, cudaStream_t st);
+// *out = max_ij |S_ij - delta_ij| as the bits of a non-negative double (NaN or Inf: +Inf)
+cudaError_t launch_dev_identity(const double* S, int k, int64_t lds, unsigned long long* out, cudaStream_t st);
+// S <- (3 I - S) / 2 in place: the first-order inverse square root of S = I + E
+cudaError_t launch_polar_first_order(double* S, int k, int64_t lds, cudaStream_t st);
 // device status words of the chunk-major path: a timed-out wait, non-finite output
 cudaError_t cm_status(bool reset, unsigned int* timeout, unsigned int* nonfinite);
 cudaError_t launch_copy_cols(const void* src, int64_t ld_src, void* dst, int64_t ld_dst, int64_t rows,
