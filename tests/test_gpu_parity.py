@@ -274,6 +274,26 @@ def test_orthonormalize_tensor_mode(kscf, system):
 
 
 @pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("log_cond", [0.5, 3.0])
+def test_orthonormalize_f32_second_pass_paths(kscf, system, mode, log_cond):
+    """The second FP32 pass rotates by I - E/2 when its Gram matrix I + E is within 1e-4 of I
+    and by a factorised R^-1 otherwise.  Columns scaled over 10^log_cond: at 10^0.5 the first
+    pass leaves |E| ~ 1e-6 (first-order path); at 10^3 it leaves |E| ~ kappa^2 u ~ 1e-2
+    (factorised path).  Both must give h^3 X^T X = I to the FP32 level and the oracle's
+    span."""
+    from workloads import random_block_lex
+    k = 40
+    X = random_block_lex(21, system["n"], k) * np.logspace(0.0, -log_cond, k)[None, :]
+    Xd = dev(to_slots(X, system["lex"]), torch.float32)
+    kscf.kscf_orthonormalize(system["H"], Xd, mode=mode)
+    got = from_slots(Xd.double().cpu().numpy(), system["lex"], system["n"])
+    h3 = system["OH"].h3
+    assert np.max(np.abs(h3 * got.T @ got - np.eye(k))) < 2e-6
+    Xr = X.astype(np.float32).astype(np.float64)   # the span of the block as passed in
+    assert subspace_gap(got, Xr, h3) < 1e-4
+
+
+@pytest.mark.parametrize("mode", [0, 1])
 def test_rayleigh_ritz_f32_modes(kscf, system, mode):
     from oracle.chefsi import cholesky_qr, rayleigh_ritz
     from workloads import random_block_lex
