@@ -161,12 +161,20 @@ size_t rr_bytes(const RRPlan& p) {
 // FP32 on 8^3 bricks: the filter runs on two chunk-major working copies of the block
 bool filter_chunk_major(const Ham& H, int dtype) { return dtype == KSCF_F32 && H.n_cells > 0; }
 
+// The chunk-major filter runs each column block as two halves of whole 16-column chunks
+// (the first with the odd chunk), one per stream: columns are filtered independently, so
+// one half's projection gathers overlap the other half's degree steps.
+int cm_first_half_cols(int wb) { return std::min(wb, ((wb + 15) / 16 + 1) / 2 * 16); }
+
 size_t filter_bytes(const Ham& H, int k, int dtype, int block) {
   const int w = block_width(k, block);
   const size_t coef = kscf_align256((size_t)std::max(H.n_kb, 1) * 4 * coef_ld(w) * esize(dtype));
   if (filter_chunk_major(H, dtype)) {
     const size_t wpad = (size_t)(w + 15) / 16 * 16;   // covers chunk widths 8 and 16
-    return 2 * kscf_align256((size_t)H.grid.n_slots * wpad * 4) + coef + kscf_align256(KSCF_CM_ZERO_BYTES);
+    const int w0 = cm_first_half_cols(w), w1 = std::max(1, w - w0);
+    const size_t coefs = kscf_align256((size_t)std::max(H.n_kb, 1) * 4 * coef_ld(w0) * 4) +
+                         kscf_align256((size_t)std::max(H.n_kb, 1) * 4 * coef_ld(w1) * 4);
+    return 2 * kscf_align256((size_t)H.grid.n_slots * wpad * 4) + coefs + kscf_align256(KSCF_CM_ZERO_BYTES);
   }
   return kscf_align256((size_t)H.grid.n_slots * coef_ld(w) * esize(dtype)) + coef;
 }
@@ -421,39 +429,81 @@ extern "C" int kscf_chebyshev_filter(const kscf_ham* ham, void* X, int64_t ld, i
   const double e = (b - a) / 2.0, c = (b + a) / 2.0;
   const double sigma1 = e / (a0 - c), tau = 2.0 / sigma1;
   if (filter_chunk_major(H, dtype)) {
-    // two chunk-major working copies A, B: A = Y_0 (converted block), B = Y_1, then Y_j
-    // overwrites Y_{j-2}; the last step writes Y_m straight into the caller's block
+    // two chunk-major working copies A, B per half: A = Y_0 (converted block), B = Y_1, then
+    // Y_j overwrites Y_{j-2}; the last step writes Y_m straight into the caller's block
     const int cw = cm_chunk_width();
     const size_t wpad16 = (size_t)(w + 15) / 16 * 16;
     float* A = (float*)cv.take((size_t)H.grid.n_slots * wpad16 * 4);
     float* B = (float*)cv.take((size_t)H.grid.n_slots * wpad16 * 4);
-    float* coef = (float*)cv.take((size_t)std::max(H.n_kb, 1) * 4 * coef_ld(w) * 4);
+    const int w0max = cm_first_half_cols(w), w1max = std::max(1, w - w0max);
+    float* coefh[2];
+    coefh[0] = (float*)cv.take((size_t)std::max(H.n_kb, 1) * 4 * coef_ld(w0max) * 4);
+    coefh[1] = (float*)cv.take((size_t)std::max(H.n_kb, 1) * 4 * coef_ld(w1max) * 4);
     float* zero = (float*)cv.take(KSCF_CM_ZERO_BYTES);
-    const int64_t cld = coef_ld(w);
     KSCF_CUDA_TRY(cudaMemsetAsync(zero, 0, KSCF_CM_ZERO_BYTES, st));
     KSCF_CUDA_TRY(launch_zero_rows(H, X, ld, k, dtype, st));
-    for (int c0 = 0; c0 < k; c0 += w) {
-      const int wb = std::min(w, k - c0);
-      float* Xb = (float*)X + c0;
-      KSCF_CUDA_TRY(launch_to_chunk_major(H, Xb, ld, wb, cw, A, B, st));
-      KSCF_CUDA_TRY(launch_kb_gather_cm(H, A, cw, wb, coef, cld, st));
+    // the second half's stream and the fork/join events, released once enqueued (CUDA
+    // frees them when their work is done)
+    cudaStream_t st1 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    const bool split = w > cw;
+    auto release = [&]() {
+      if (ev_fork) cudaEventDestroy(ev_fork);
+      if (ev_join) cudaEventDestroy(ev_join);
+      if (st1) cudaStreamDestroy(st1);
+    };
+    if (split) {
+      cudaError_t ce = cudaStreamCreateWithFlags(&st1, cudaStreamNonBlocking);
+      if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
+      if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming);
+      if (ce != cudaSuccess) {
+        release();
+        KSCF_CUDA_TRY(ce);
+      }
+    }
+    auto run = [&](float* Xb, int wb, float* Ah, float* Bh, float* coef, cudaStream_t sh) -> cudaError_t {
+      const int64_t cld = coef_ld(wb);
+      cudaError_t e2 = launch_to_chunk_major(H, Xb, ld, wb, cw, Ah, Bh, sh);
+      if (e2 == cudaSuccess) e2 = launch_kb_gather_cm(H, Ah, cw, wb, coef, cld, sh);
       // Y_1 = (sigma_1/e)(H X - c X)
-      KSCF_CUDA_TRY(launch_cm_step(H, A, nullptr, degree == 1 ? Xb : B, degree == 1 ? ld : -1, wb, sigma1 / e, 0.0,
-                                   c, coef, cld, degree == 1, zero, st));
-      float* cur = B;
-      float* prv = A;
+      if (e2 == cudaSuccess)
+        e2 = launch_cm_step(H, Ah, nullptr, degree == 1 ? Xb : Bh, degree == 1 ? ld : -1, wb, sigma1 / e, 0.0, c,
+                            coef, cld, degree == 1, zero, sh);
+      float* cur = Bh;
+      float* prv = Ah;
       double sigma = sigma1;
-      for (int j = 2; j <= degree; j++) {
+      for (int j = 2; j <= degree && e2 == cudaSuccess; j++) {
         const double sigma_new = 1.0 / (tau - sigma);
         const bool last = j == degree;
-        KSCF_CUDA_TRY(launch_kb_gather_cm(H, cur, cw, wb, coef, cld, st));
+        e2 = launch_kb_gather_cm(H, cur, cw, wb, coef, cld, sh);
         // Y_j overwrites Y_{j-2} (each element read before it is written)
-        KSCF_CUDA_TRY(launch_cm_step(H, cur, prv, last ? Xb : prv, last ? ld : -1, wb, 2.0 * sigma_new / e,
-                                     -sigma * sigma_new, c, coef, cld, last, zero, st));
+        if (e2 == cudaSuccess)
+          e2 = launch_cm_step(H, cur, prv, last ? Xb : prv, last ? ld : -1, wb, 2.0 * sigma_new / e, -sigma * sigma_new,
+                              c, coef, cld, last, zero, sh);
         std::swap(cur, prv);
         sigma = sigma_new;
       }
+      return e2;
+    };
+    cudaError_t err = cudaSuccess;
+    for (int c0 = 0; c0 < k && err == cudaSuccess; c0 += w) {
+      const int wb = std::min(w, k - c0);
+      float* Xb = (float*)X + c0;
+      const int wb0 = split ? cm_first_half_cols(wb) : wb, wb1 = wb - wb0;
+      if (wb1 > 0) {
+        err = cudaEventRecord(ev_fork, st);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(st1, ev_fork, 0);
+      }
+      if (err == cudaSuccess) err = run(Xb, wb0, A, B, coefh[0], st);
+      if (err == cudaSuccess && wb1 > 0) {
+        const size_t off = (size_t)H.grid.n_slots * wb0;   // wb0 is a multiple of 16
+        err = run(Xb + wb0, wb1, A + off, B + off, coefh[1], st1);
+        if (err == cudaSuccess) err = cudaEventRecord(ev_join, st1);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(st, ev_join, 0);
+      }
     }
+    release();
+    KSCF_CUDA_TRY(err);
     return KSCF_OK;
   }
   const int64_t wpad = coef_ld(w);
