@@ -204,11 +204,11 @@ int kscf_hamiltonian_apply(const kscf_ham* ham, void* Y, int64_t ld_y, void* HY,
  *     bytes (n_kb = atoms with projectors); larger k is rejected with
  *     KSCF_ERR_INVALID and a message giving the largest k that fits -- call it on
  *     column blocks of Y instead.
- *   - Allocates nothing and calls no allocating routine.  The first call on each
- *     device looks up the array's device address (cudaGetSymbolAddress) with that
- *     device current; make that first call before any stream capture.  The address is
- *     kept for the life of the process: do not use this entry point on a device after
- *     cudaDeviceReset (or any reset of its primary context) in the same process.
+ *   - Allocates nothing and calls no allocating routine.  Every call looks up the
+ *     array's device address (cudaGetSymbolAddress, with the device current), so the
+ *     entry point stays usable after cudaDeviceReset or a reset of the primary context;
+ *     make the first call on each device before any stream capture (the first lookup
+ *     may load the library's device code).
  *   - All calls share the one array and it keeps the last call's contents; calls whose
  *     work overlaps on the GPU (different streams, or threads without ordering) race
  *     on it and give wrong results.  Serialise them (e.g. one stream).
@@ -223,7 +223,10 @@ int kscf_hamiltonian_apply_noalloc(const kscf_ham* ham, void* Y, int64_t ld_y, v
  *   Y_j = (2 sigma_j/e)(H Y_{j-1} - c Y_{j-1}) - sigma_{j-1} sigma_j Y_{j-2},
  *   sigma_j = 1/(tau - sigma_{j-1}),  j = 2..m;   X <- Y_m.
  * Requires a0 < a < b, degree >= 1.  Columns are processed `block` at a time
- * (0 = all k); the result does not depend on block. */
+ * (0 = all k); the result does not depend on block.  F32 on bricks of 8^3 or 16^3: each
+ * block runs as two halves of whole 16-column chunks, the second on a stream the call
+ * creates and releases; both halves are ordered after the work already on `stream`, and
+ * the work enqueued on `stream` after the call waits for both. */
 int kscf_chebyshev_filter(const kscf_ham* ham, void* X, int64_t ld, int k, int degree,
                           double a, double b, double a0, int dtype, int block,
                           void* work, size_t work_bytes, void* stream);
