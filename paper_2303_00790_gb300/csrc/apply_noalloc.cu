@@ -10,8 +10,8 @@
 // The array is a file-scope __device__ variable of KSCF_NOALLOC_SCRATCH_BYTES bytes; every
 // GPU that loads this library holds it until the process exits.  Host code may not
 // use the array's name as a device address (on the host it is only a stand-in), so
-// the device address is looked up once per device with cudaGetSymbolAddress, with
-// that device current, on the first call made on that device.
+// the device address is looked up with cudaGetSymbolAddress, with the device current,
+// on every call.
 #include <cuda_runtime.h>
 
 #include "kscf_internal.h"
