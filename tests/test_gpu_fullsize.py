@@ -32,13 +32,17 @@ def device_block(kscf, H, n_slots, k, seed):
     return full, X
 
 
-def test_filter_fullsize_bench_config(kscf, species):
+@pytest.mark.parametrize("brick", [8, 16])
+def test_filter_fullsize_bench_config(kscf, species, brick):
+    """Bricks of 8^3 (the benchmark's layout) and 16^3 (the chunk-major kernel on the
+    octants of each brick): the same filter, compared with the oracle on sampled columns
+    over all points."""
     from oracle.chefsi import chebyshev_filter
     from oracle.system import cluster_hamiltonian
     from workloads import random_block_lex, workload
     w = workload("si353h196")
     pos, z = w.atoms()
-    g, H = kscf.build_cluster(pos, z, species, w.radius, w.h)
+    g, H = kscf.build_cluster(pos, z, species, w.radius, w.h, brick=brick)
     lex, _ = g.slots()
     n, n_slots, k = g.info["n_points"], g.info["n_slots"], w.k
     full, X = device_block(kscf, H, n_slots, k, seed=3)
