@@ -679,7 +679,7 @@ def run_kscf(args):
                 "step_breakdown_ms": breakdown,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
-                             "kernel": "cm_step_ldg16 (fused stencil + V + KB scatter + recurrence) with its kb_gather_cm, per degree step",
+                             "kernel": "cm_step_ldg16 (fused stencil + V + KB gather + recurrence; the block's two column halves) with its kb_gather_cm, per degree step of the block",
                              "alg_bytes_per_launch": alg_bytes, "launch_ms": step_ms},
                 "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": int(launches), "clocks": clocks, "scf": scf,
                 "learned_start": learned_start}
