@@ -565,11 +565,11 @@ def run_kscf(args):
     units = n_points * k * m
     value = world * units / (ms * 1e-3) / 1e9
 
-    # roofline of the dominant kernel: the fused filter step (one launch = one degree
-    # step of one column block); algorithmic bytes = 12 B per point*vec (read Y_{j-1},
-    # read Y_{j-2}, write Y_j in FP32).  Its duration is the filter time over its
-    # m * ceil(k/block) degree-step launches (the small projector-gather launches
-    # inside are counted in the time).
+    # roofline of the dominant kernel: the fused filter step (one degree step of one column
+    # block = its two half launches on two streams); algorithmic bytes = 12 B per point*vec
+    # (read Y_{j-1}, read Y_{j-2}, write Y_j in FP32).  Its duration is the filter time over
+    # its m * ceil(k/block) degree steps (the projection-gather launches and the chunk-major
+    # conversion inside are counted in the time).
     n_launch_steps = m * ((k + block - 1) // block)
     step_ms = filt_ms / n_launch_steps
     alg_bytes = 12.0 * n_points * block
